@@ -1,0 +1,184 @@
+/*
+ * lx_eri.h -- C ABI of a GB300 (sm_103a) library that evaluates batches of 4-center
+ * 2-electron repulsion integrals (ab|cd) over contracted Cartesian Gaussian shells by
+ * the matrix form of the McMurchie-Davidson (MD) recurrences (Asadchev & Valeev,
+ * "High-performance evaluation of high angular momentum 4-center Gaussian integrals on
+ * modern accelerated processors", arXiv:2307.03452).
+ *
+ * What is computed (paper, Section 2 "Formalism"):
+ *   (ab|cd) = sum_{p,q} H_ab^p [p|q] H_cd^q   over all primitive quartets,
+ *   [p|q]   = (-1)^{l_q} [p+q]^(0)                                     (Eq. pq)
+ *   [r+1_i]^(m) = r_i [r-1_i]^(m+1) + (P_i - Q_i) [r]^(m+1)             (Eq. md1)
+ *   [0]^(m) = (-2 rho)^m 2 pi^{5/2} / (zeta_p zeta_q sqrt(zeta_p+zeta_q)) F_m(rho |PQ|^2)
+ *   F_m(T)  = int_0^1 y^{2m} exp(-T y^2) dy                             (Eq. boys)
+ *   H_ab^p  = sum_{a,b} C^a_{l_a m_a} C^b_{l_b m_b} E_ab^p  (solid) or E_ab^p (Cartesian),
+ *   with E from the recursions after Eq. cart2herm-2, evaluated as the two transforms
+ *   Eq. ab_to_hermite / Eq. make-abq and Eq. cd_to_hermite / Eq. make-abcd.
+ *
+ * Conventions (the paper leaves them open):
+ *   - Cartesian components of a shell l in the order: for i = 0..l, j = 0..i:
+ *     (l-i, i-j, j).  Every component carries the normaliser of x^l exp(-zeta r^2).
+ *   - Raw contraction coefficients are normalised inside the library: c_i times the
+ *     primitive normaliser, rescaled so that the contracted x^l function has unit norm.
+ *   - Real solid harmonics are unit-normalised, ordered m = -l..l (Schlegel & Frisch).
+ *   - A quartet's output block is row-major over (a, b, c, d) components, written at
+ *     out + out_offset (in doubles).
+ *   - No screening is done (the paper's Section 3: the caller screens).
+ *
+ * Threading: every entry point is thread-safe; the first call on a device uploads
+ * constant tables to that device (synchronously), so make it before any stream capture.
+ */
+#ifndef LX_ERI_H
+#define LX_ERI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LX_LMAX 6  /* largest shell angular momentum (i shells) */
+#define LX_KMAX 16 /* largest contraction degree of one shell */
+
+/* One shell: angular momentum l (0..LX_LMAX), nprim primitives whose exponents and raw
+   contraction coefficients start at exps[prim_offset] / coefs[prim_offset], center in bohr. */
+typedef struct {
+    int32_t l;
+    int32_t nprim;
+    int32_t prim_offset;
+    int32_t reserved; /* must be 0 */
+    double center[3];
+} lx_shell;
+
+/* One shell quartet (ab|cd): shell indices s[0..3] = a, b, c, d and the offset (in doubles)
+   of its output block in the caller's output buffer. */
+typedef struct {
+    int32_t s[4];
+    int64_t out_offset;
+} lx_quartet;
+
+/* flags */
+#define LX_CART 0x0        /* Cartesian output, ncart(l) = (l+1)(l+2)/2 per shell */
+#define LX_SOLID 0x1       /* real solid-harmonic output, 2l+1 per shell */
+#define LX_PATH_FP64 0x0   /* every step in FP64 */
+#define LX_TIME_STAGES 0x200 /* record CUDA events around each stage (see lx_eri_stage_times) */
+
+/* stages timed with LX_TIME_STAGES */
+#define LX_STAGE_NORM 0   /* contraction normalisation */
+#define LX_STAGE_PAIR 1   /* pair scalars and H matrices */
+#define LX_STAGE_BOYS_R 2 /* Boys function and [r]^(0) */
+#define LX_STAGE_GEMM1 3  /* [ab|q] = H_ab [p|q] */
+#define LX_STAGE_GEMM2 4  /* (ab|cd) = [ab|q] H_cd^T */
+#define LX_NSTAGE 5
+
+/* error codes (0 = success) */
+#define LX_OK 0
+#define LX_ERR_NULL (-1)          /* a required pointer is NULL */
+#define LX_ERR_SHELL (-2)         /* l outside 0..LX_LMAX, nprim outside 1..LX_KMAX, reserved != 0,
+                                     primitive range outside the arrays, or non-finite center */
+#define LX_ERR_PRIMITIVE (-3)     /* exponent not finite and > 0, or coefficient not finite */
+#define LX_ERR_QUARTET (-4)       /* shell index out of range or negative out_offset */
+#define LX_ERR_FLAGS (-5)         /* unknown flag bits */
+#define LX_ERR_WORKSPACE (-6)     /* workspace NULL or smaller than lx_eri_workspace_min */
+#define LX_ERR_CUDA (-7)          /* a CUDA runtime call failed (see lx_last_cuda_error) */
+#define LX_ERR_ARCH (-8)          /* current device is not compute capability 10.3 */
+#define LX_ERR_DEVICE_STATUS (-9) /* a kernel reported a bad index or an exhausted wait */
+#define LX_ERR_SIZE (-10)         /* a size argument is negative or too large */
+
+/*
+ * Number of doubles the output buffer needs: max over quartets of out_offset + block size.
+ * Host pointers.  Returns a negative error code on invalid input.
+ */
+int64_t lx_eri_out_size(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
+                        int32_t flags);
+
+/*
+ * Device workspace (bytes) to evaluate the whole batch in one pass.  A smaller workspace
+ * (at least lx_eri_workspace_min) also works: the batch is then processed in chunks.
+ */
+int64_t lx_eri_workspace_size(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets,
+                              int64_t nquartet, int32_t flags);
+
+/* Smallest workspace (bytes) with which lx_eri_batch accepts this batch (one quartet at a time). */
+int64_t lx_eri_workspace_min(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets,
+                             int64_t nquartet, int32_t flags);
+
+/*
+ * Evaluate (ab|cd) for every quartet.
+ *   shells[nshell], exps[nprim_total], coefs[nprim_total], quartets[nquartet]: HOST memory,
+ *     read during the call only.
+ *   out: DEVICE memory (current device), caller-owned, at least lx_eri_out_size doubles;
+ *     only the quartets' blocks are written.
+ *   workspace: DEVICE memory, caller-owned, workspace_bytes long, 256-byte aligned; it
+ *     holds the per-call descriptors, the H matrices, the [r]^(0) vectors and the
+ *     intermediate [ab|q] blocks.  It must not be reused until the stream has passed the work.
+ *   cuda_stream: a cudaStream_t of the current device (NULL = legacy default stream).
+ * The call validates every input on the host, enqueues the kernels and returns without
+ * waiting for them.  Errors found on the device are reported by lx_eri_sync_status.
+ */
+int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
+                 int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags, double* out,
+                 void* workspace, size_t workspace_bytes, void* cuda_stream);
+
+/*
+ * Wait for cuda_stream, then read and clear the device status word of the current device.
+ * Returns LX_OK, LX_ERR_DEVICE_STATUS if a kernel flagged an error since the last call,
+ * or LX_ERR_CUDA if the stream reported a CUDA error.
+ */
+int lx_eri_sync_status(void* cuda_stream);
+
+/*
+ * Milliseconds spent in each stage (ms[LX_STAGE_*], nstage <= LX_NSTAGE) and the number of
+ * kernel launches per stage (launches[], may be NULL), summed over every lx_eri_batch call
+ * made with LX_TIME_STAGES on cuda_stream since the previous call of this function; the
+ * accumulators are then cleared.  Waits for cuda_stream.  The events are recorded on the
+ * stream the kernels run on, so each figure is the stage's device time.
+ */
+int lx_eri_stage_times(double* ms, int64_t* launches, int32_t nstage, void* cuda_stream);
+
+/* Human-readable text of an error code (static storage). */
+const char* lx_strerror(int code);
+
+/* Text of the last CUDA error seen by this thread (static thread-local storage). */
+const char* lx_last_cuda_error(void);
+
+/* ---------------------------------------------------------------- stage entry points
+ * The same device routines the batch path uses, exposed one stage at a time so that each
+ * stage can be checked on its own.  All array arguments are DEVICE pointers. */
+
+/*
+ * Boys function, Eq. boys: F[i*(mmax+1) + m] = F_m(T[i]) for m = 0..mmax, i < n.
+ * mmax <= 4*LX_LMAX; T[i] >= 0 and finite (a negative or non-finite T sets the device
+ * status word and yields NaN).  Tabulated Taylor expansion plus downward recursion for
+ * T < 36, erf-free asymptotic F_0 plus upward recursion above.
+ */
+int lx_boys(int32_t mmax, const double* T, int64_t n, double* F, void* cuda_stream);
+
+/*
+ * Auxiliary Hermite integrals [r]^(0), |r| <= L, by Eq. md1 in place with descending m.
+ * Item i: params[5i..5i+4] = (rho, PQx, PQy, PQz, pref) with pref the prefactor
+ * 2 pi^{5/2}/(zeta_p zeta_q sqrt(zeta_p+zeta_q)); output R[i*pyr(L) + idx(t,u,v)] with the
+ * pyramidal index idx(t,u,v) = n(n+1)(n+2)/6 + i'(i'+1)/2 + v, n = t+u+v, i' = u+v,
+ * pyr(L) = (L+1)(L+2)(L+3)/6.  L <= 4*LX_LMAX.
+ */
+int lx_hermite_R(int32_t L, const double* params, int64_t n, double* R, void* cuda_stream);
+
+/*
+ * Hermite-to-Cartesian/solid matrices H (Section 2, definition of H) of shell pairs.
+ * pairs[2k], pairs[2k+1]: shell indices (a, b) of pair k (HOST memory, like shells, exps,
+ * coefs).  Output H (DEVICE) for pair k starts at H + k*stride with
+ * stride = max over pairs of nfun(l_a) nfun(l_b) K_a K_b pyr(l_a+l_b), laid out as
+ * [a b][kp * pyr(l_a+l_b) + idx(p)] with kp = i_a K_b + i_b the primitive pair; each row
+ * carries exp(-mu |AB|^2) and the normalised coefficients of both primitives.  flags:
+ * LX_SOLID selects solid output; bit 0x100 multiplies column p by (-1)^{|p|} (ket side).
+ */
+int lx_hermite_H(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
+                 int32_t nprim_total, const int32_t* pairs, int32_t npair, int32_t flags, double* H,
+                 int64_t stride, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LX_ERI_H */

@@ -1,0 +1,630 @@
+// C ABI of the library: input validation, batch planning and the launch sequence of the
+// matrix form of MD4 (paper, Section 2, pseudocode "md4"; Section 3):
+//   norm    -> normalised contraction coefficients
+//   pair_h  -> per primitive pair: zeta_p, P and the H matrix (E recursions, solid fold)
+//   boys_r  -> per primitive quartet: Boys function and [r]^(0) by Eq. md1
+//   gemm1   -> [ab|q] = H_ab [p|q]                                  (Eq. make-abq)
+//   gemm2   -> (ab|cd) = [ab|q] H_cd^T                              (Eq. make-abcd)
+// The host side only validates, deduplicates shell pairs, lays out the caller's workspace
+// and builds work lists; every arithmetic step of the method runs in the kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "lx_internal.cuh"
+
+namespace lx {
+namespace {
+
+__device__ unsigned g_status_word;
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_init_mutex;
+bool g_dev_ready[MAX_DEVICES];
+unsigned* g_status_ptr[MAX_DEVICES];
+
+thread_local char t_cuda_msg[256] = "no error";
+
+// Stage timing (LX_TIME_STAGES): events recorded around each stage, read back by
+// lx_eri_stage_times.
+struct PendingTiming {
+    cudaStream_t stream;
+    cudaEvent_t begin, end;
+    int stage;
+    int launches;
+};
+std::mutex g_timing_mutex;
+std::vector<PendingTiming> g_pending;
+
+struct StageTimer {
+    bool on;
+    cudaStream_t st;
+    cudaEvent_t cur = nullptr;
+    cudaError_t begin() {
+        if (!on) return cudaSuccess;
+        cudaError_t e = cudaEventCreate(&cur);
+        if (e != cudaSuccess) return e;
+        return cudaEventRecord(cur, st);
+    }
+    cudaError_t end(int stage, int launches) {
+        if (!on) return cudaSuccess;
+        cudaEvent_t e1;
+        cudaError_t e = cudaEventCreate(&e1);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaEventRecord(e1, st)) != cudaSuccess) return e;
+        std::lock_guard<std::mutex> lock(g_timing_mutex);
+        g_pending.push_back({st, cur, e1, stage, launches});
+        cur = nullptr;
+        return cudaSuccess;
+    }
+};
+
+int cuda_fail(cudaError_t e) {
+    std::snprintf(t_cuda_msg, sizeof(t_cuda_msg), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return LX_ERR_CUDA;
+}
+
+// Once per device, with that device current: check the architecture, upload the tables,
+// look up the status word.  Returns LX_OK or an error code; *status receives the word.
+int ensure_device(unsigned** status) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= MAX_DEVICES) return LX_ERR_ARCH;
+    std::lock_guard<std::mutex> lock(g_init_mutex);
+    if (!g_dev_ready[dev]) {
+        int major = 0, minor = 0;
+        e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+        if (e != cudaSuccess) return cuda_fail(e);
+        e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (major != 10 || minor != 3) return LX_ERR_ARCH;
+        std::vector<double> boys(BOYS_NROW * BOYS_NPT);
+        make_boys_table(boys.data());
+        std::vector<double> solid(840);
+        make_solid_coefs(solid.data());
+        std::vector<int> tuv(NHERM_TOT);
+        make_tuv_table(tuv.data());
+        if ((e = init_boys_table(boys.data())) != cudaSuccess) return cuda_fail(e);
+        if ((e = init_prep_tables(solid.data(), tuv.data())) != cudaSuccess) return cuda_fail(e);
+        if ((e = init_tuv_table(tuv.data())) != cudaSuccess) return cuda_fail(e);
+        void* p = nullptr;
+        if ((e = cudaGetSymbolAddress(&p, g_status_word)) != cudaSuccess) return cuda_fail(e);
+        const unsigned zero = 0;
+        if ((e = cudaMemcpyToSymbol(g_status_word, &zero, sizeof(zero))) != cudaSuccess) return cuda_fail(e);
+        g_status_ptr[dev] = static_cast<unsigned*>(p);
+        g_dev_ready[dev] = true;
+    }
+    *status = g_status_ptr[dev];
+    return LX_OK;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct QuartetShape {
+    int la, lb, lc, ld, Ka, Kb, Kc, Kd;
+};
+
+int validate(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs, int32_t nprim_total,
+             const lx_quartet* quartets, int64_t nquartet, int32_t flags, bool need_prims) {
+    if (nshell < 0 || nquartet < 0 || nprim_total < 0) return LX_ERR_SIZE;
+    if ((nshell > 0 && !shells) || (nquartet > 0 && !quartets)) return LX_ERR_NULL;
+    if (need_prims && nprim_total > 0 && (!exps || !coefs)) return LX_ERR_NULL;
+    if (flags & ~(LX_SOLID | LX_TIME_STAGES)) return LX_ERR_FLAGS;
+    for (int32_t s = 0; s < nshell; ++s) {
+        const lx_shell& d = shells[s];
+        if (d.l < 0 || d.l > LX_LMAX || d.nprim < 1 || d.nprim > LX_KMAX || d.reserved != 0) return LX_ERR_SHELL;
+        if (!std::isfinite(d.center[0]) || !std::isfinite(d.center[1]) || !std::isfinite(d.center[2]))
+            return LX_ERR_SHELL;
+        if (need_prims) {
+            if (d.prim_offset < 0 || (int64_t)d.prim_offset + d.nprim > nprim_total) return LX_ERR_SHELL;
+            for (int k = 0; k < d.nprim; ++k) {
+                const double z = exps[d.prim_offset + k], c = coefs[d.prim_offset + k];
+                if (!(std::isfinite(z) && z > 0.0) || !std::isfinite(c)) return LX_ERR_PRIMITIVE;
+            }
+        }
+    }
+    for (int64_t q = 0; q < nquartet; ++q) {
+        for (int k = 0; k < 4; ++k)
+            if (quartets[q].s[k] < 0 || quartets[q].s[k] >= nshell) return LX_ERR_QUARTET;
+        if (quartets[q].out_offset < 0) return LX_ERR_QUARTET;
+    }
+    return LX_OK;
+}
+
+// ------------------------------------------------------------------ planning
+
+struct PairKey {
+    int64_t v;
+    bool operator==(const PairKey& o) const { return v == o.v; }
+};
+struct PairKeyHash {
+    size_t operator()(const PairKey& k) const { return std::hash<int64_t>()(k.v); }
+};
+
+struct Chunk {
+    int64_t q_begin = 0, q_end = 0;
+};
+
+// Workspace bytes of one quartet's own data (without its pairs).
+size_t quartet_bytes(const lx_shell* sh, const lx_quartet& q, bool solid) {
+    const lx_shell &a = sh[q.s[0]], &b = sh[q.s[1]], &c = sh[q.s[2]], &d = sh[q.s[3]];
+    const int L = a.l + b.l + c.l + d.l, nq = pyr(c.l + d.l);
+    const int64_t kbra = (int64_t)a.nprim * b.nprim, kket = (int64_t)c.nprim * d.nprim;
+    const int64_t nab = (int64_t)nfun(a.l, solid) * nfun(b.l, solid), ncd = (int64_t)nfun(c.l, solid) * nfun(d.l, solid);
+    const int64_t n1 = kket * nq;
+    int64_t items = (kbra * kket + 3) / 4;
+    items += ((nab + GEMM_BM - 1) / GEMM_BM) * ((n1 + GEMM_BN - 1) / GEMM_BN);
+    items += ((nab + GEMM_BM - 1) / GEMM_BM) * ((ncd + GEMM_BN - 1) / GEMM_BN);
+    // + 2 x 256 bytes: each of the two data blocks starts on a 256-byte boundary
+    return sizeof(DQuartet) + items * sizeof(WorkItem) + 8 * (size_t)(kbra * kket * pyr(L) + nab * n1) + 512;
+}
+
+size_t pair_bytes(const lx_shell* sh, int sa, int sb, bool solid) {
+    const lx_shell &a = sh[sa], &b = sh[sb];
+    const int64_t kab = (int64_t)a.nprim * b.nprim;
+    const int64_t rows = (int64_t)nfun(a.l, solid) * nfun(b.l, solid);
+    return sizeof(DPair) + kab * sizeof(WorkItem) + 8 * (size_t)(kab * 4 + rows * kab * pyr(a.l + b.l)) + 512;
+}
+
+constexpr size_t CHUNK_SLACK = 16 * 256;  // alignment padding of the chunk's regions
+
+size_t head_bytes(int nshell, int nprim) {
+    return align256(sizeof(DShell) * (size_t)nshell) + 3 * align256(sizeof(double) * (size_t)nprim);
+}
+
+// Greedy chunking of the quartet list so that each chunk fits `budget` bytes.
+int plan_chunks(const lx_shell* sh, const lx_quartet* qs, int64_t nq, bool solid, size_t budget,
+                std::vector<Chunk>& chunks) {
+    chunks.clear();
+    std::unordered_map<PairKey, int, PairKeyHash> seen;
+    size_t used = CHUNK_SLACK;
+    Chunk cur;
+    cur.q_begin = 0;
+    for (int64_t i = 0; i < nq; ++i) {
+        const lx_quartet& q = qs[i];
+        size_t add = quartet_bytes(sh, q, solid);
+        const PairKey kb{((int64_t)q.s[0] << 32 | (uint32_t)q.s[1]) * 2};
+        const PairKey kk{((int64_t)q.s[2] << 32 | (uint32_t)q.s[3]) * 2 + 1};
+        const bool nb = !seen.count(kb), nk = !seen.count(kk);
+        if (nb) add += pair_bytes(sh, q.s[0], q.s[1], solid);
+        if (nk && !(kk == kb)) add += pair_bytes(sh, q.s[2], q.s[3], solid);
+        if (used + add > budget) {
+            if (i == cur.q_begin) return LX_ERR_WORKSPACE;  // one quartet does not fit
+            cur.q_end = i;
+            chunks.push_back(cur);
+            cur.q_begin = i;
+            seen.clear();
+            used = CHUNK_SLACK;
+            --i;  // retry this quartet in the new chunk
+            continue;
+        }
+        used += add;
+        seen[kb] = 1;
+        seen[kk] = 1;
+    }
+    cur.q_end = nq;
+    if (nq > 0) chunks.push_back(cur);
+    return LX_OK;
+}
+
+// Layout of one chunk inside the workspace, built on the host.
+struct ChunkPlan {
+    std::vector<DPair> pairs;
+    std::vector<DQuartet> quartets;
+    std::vector<WorkItem> items_h, items_br, items_g1, items_g2;
+    size_t off_pairs = 0, off_quartets = 0, off_h = 0, off_br = 0, off_g1 = 0, off_g2 = 0, off_data = 0;
+    size_t total = 0;         // bytes from the chunk base
+    std::vector<char> blob;   // descriptor bytes [0, off_data)
+};
+
+void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, bool solid, size_t chunk_base,
+                 ChunkPlan& P) {
+    P.pairs.clear();
+    P.quartets.clear();
+    P.items_h.clear();
+    P.items_br.clear();
+    P.items_g1.clear();
+    P.items_g2.clear();
+    std::unordered_map<PairKey, int, PairKeyHash> pid;
+    auto get_pair = [&](int sa, int sb, int side) {
+        const PairKey k{((int64_t)sa << 32 | (uint32_t)sb) * 2 + side};
+        auto f = pid.find(k);
+        if (f != pid.end()) return f->second;
+        DPair p{};
+        p.sa = sa;
+        p.sb = sb;
+        p.Kab = sh[sa].nprim * sh[sb].nprim;
+        p.nrow = nfun(sh[sa].l, solid) * nfun(sh[sb].l, solid);
+        p.np = pyr(sh[sa].l + sh[sb].l);
+        p.sign = side;
+        p.solid = solid ? 1 : 0;
+        const int id = (int)P.pairs.size();
+        P.pairs.push_back(p);
+        pid.emplace(k, id);
+        return id;
+    };
+    for (int64_t i = ch.q_begin; i < ch.q_end; ++i) {
+        const lx_quartet& q = qs[i];
+        DQuartet d{};
+        d.pb = get_pair(q.s[0], q.s[1], 0);
+        d.pk = get_pair(q.s[2], q.s[3], 1);
+        const lx_shell &a = sh[q.s[0]], &b = sh[q.s[1]], &c = sh[q.s[2]], &dd = sh[q.s[3]];
+        d.L = a.l + b.l + c.l + dd.l;
+        d.np = pyr(a.l + b.l);
+        d.nq = pyr(c.l + dd.l);
+        d.nab = nfun(a.l, solid) * nfun(b.l, solid);
+        d.ncd = nfun(c.l, solid) * nfun(dd.l, solid);
+        d.kbra = a.nprim * b.nprim;
+        d.kket = c.nprim * dd.nprim;
+        d.nr = pyr(d.L);
+        d.out_off = q.out_offset;
+        P.quartets.push_back(d);
+    }
+    // work lists
+    for (int i = 0; i < (int)P.pairs.size(); ++i)
+        for (int kp = 0; kp < P.pairs[i].Kab; ++kp) P.items_h.push_back({i, kp, 0, 0});
+    for (int i = 0; i < (int)P.quartets.size(); ++i) {
+        const DQuartet& d = P.quartets[i];
+        for (int k = 0; k < d.kbra * d.kket; k += 4) P.items_br.push_back({i, k, 0, 0});
+        const int mt = (d.nab + GEMM_BM - 1) / GEMM_BM;
+        const int nt1 = (d.kket * d.nq + GEMM_BN - 1) / GEMM_BN, nt2 = (d.ncd + GEMM_BN - 1) / GEMM_BN;
+        for (int m = 0; m < mt; ++m)
+            for (int n = 0; n < nt1; ++n) P.items_g1.push_back({i, m, n, 0});
+        for (int m = 0; m < mt; ++m)
+            for (int n = 0; n < nt2; ++n) P.items_g2.push_back({i, m, n, 0});
+    }
+    // byte layout from the chunk base
+    size_t o = 0;
+    P.off_pairs = o;
+    o = align256(o + sizeof(DPair) * P.pairs.size());
+    P.off_quartets = o;
+    o = align256(o + sizeof(DQuartet) * P.quartets.size());
+    P.off_h = o;
+    o = align256(o + sizeof(WorkItem) * P.items_h.size());
+    P.off_br = o;
+    o = align256(o + sizeof(WorkItem) * P.items_br.size());
+    P.off_g1 = o;
+    o = align256(o + sizeof(WorkItem) * P.items_g1.size());
+    P.off_g2 = o;
+    o = align256(o + sizeof(WorkItem) * P.items_g2.size());
+    P.off_data = o;
+    // data regions, offsets in doubles from the workspace base
+    int64_t dw = (int64_t)((chunk_base + o) / 8);
+    for (auto& p : P.pairs) {
+        p.info_off = dw;
+        dw += 4 * (int64_t)p.Kab;
+        dw = (dw + 31) & ~int64_t(31);
+    }
+    for (auto& p : P.pairs) {
+        p.h_off = dw;
+        dw += (int64_t)p.nrow * p.Kab * p.np;
+        dw = (dw + 31) & ~int64_t(31);
+    }
+    for (auto& d : P.quartets) {
+        d.rr_off = dw;
+        dw += (int64_t)d.kbra * d.kket * d.nr;
+        dw = (dw + 31) & ~int64_t(31);
+        d.x_off = dw;
+        dw += (int64_t)d.nab * d.kket * d.nq;
+        dw = (dw + 31) & ~int64_t(31);
+    }
+    P.total = (size_t)dw * 8 - chunk_base;
+    P.blob.assign(P.off_data, 0);
+    std::memcpy(P.blob.data() + P.off_pairs, P.pairs.data(), sizeof(DPair) * P.pairs.size());
+    std::memcpy(P.blob.data() + P.off_quartets, P.quartets.data(), sizeof(DQuartet) * P.quartets.size());
+    std::memcpy(P.blob.data() + P.off_h, P.items_h.data(), sizeof(WorkItem) * P.items_h.size());
+    std::memcpy(P.blob.data() + P.off_br, P.items_br.data(), sizeof(WorkItem) * P.items_br.size());
+    std::memcpy(P.blob.data() + P.off_g1, P.items_g1.data(), sizeof(WorkItem) * P.items_g1.size());
+    std::memcpy(P.blob.data() + P.off_g2, P.items_g2.data(), sizeof(WorkItem) * P.items_g2.size());
+}
+
+// Workspace bytes that plan_chunks needs to keep quartets [b, e) in one chunk (an upper
+// bound of the exact layout built by build_chunk).
+size_t chunk_estimate(const lx_shell* sh, const lx_quartet* qs, int64_t b, int64_t e, bool solid) {
+    std::unordered_map<PairKey, int, PairKeyHash> seen;
+    size_t used = CHUNK_SLACK;
+    for (int64_t i = b; i < e; ++i) {
+        const lx_quartet& q = qs[i];
+        used += quartet_bytes(sh, q, solid);
+        const PairKey kb{((int64_t)q.s[0] << 32 | (uint32_t)q.s[1]) * 2};
+        const PairKey kk{((int64_t)q.s[2] << 32 | (uint32_t)q.s[3]) * 2 + 1};
+        if (!seen.count(kb)) used += pair_bytes(sh, q.s[0], q.s[1], solid);
+        if (!seen.count(kk)) used += pair_bytes(sh, q.s[2], q.s[3], solid);
+        seen[kb] = 1;
+        seen[kk] = 1;
+    }
+    return used;
+}
+
+int64_t prim_count(const lx_shell* sh, int32_t nshell) {
+    int64_t n = 0;
+    for (int32_t s = 0; s < nshell; ++s) n = std::max<int64_t>(n, (int64_t)sh[s].prim_offset + sh[s].nprim);
+    return n;
+}
+
+}  // namespace
+}  // namespace lx
+
+using namespace lx;
+
+extern "C" {
+
+int64_t lx_eri_out_size(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
+                        int32_t flags) {
+    const int v = validate(shells, nshell, nullptr, nullptr, 0, quartets, nquartet, flags, false);
+    if (v != LX_OK) return v;
+    const bool solid = flags & LX_SOLID;
+    int64_t n = 0;
+    for (int64_t i = 0; i < nquartet; ++i) {
+        int64_t sz = 1;
+        for (int k = 0; k < 4; ++k) sz *= nfun(shells[quartets[i].s[k]].l, solid);
+        n = std::max(n, quartets[i].out_offset + sz);
+    }
+    return n;
+}
+
+int64_t lx_eri_workspace_size(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
+                              int32_t flags) {
+    const int v = validate(shells, nshell, nullptr, nullptr, 0, quartets, nquartet, flags, false);
+    if (v != LX_OK) return v;
+    return (int64_t)(head_bytes(nshell, (int32_t)prim_count(shells, nshell)) +
+                     chunk_estimate(shells, quartets, 0, nquartet, flags & LX_SOLID));
+}
+
+int64_t lx_eri_workspace_min(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
+                             int32_t flags) {
+    const int v = validate(shells, nshell, nullptr, nullptr, 0, quartets, nquartet, flags, false);
+    if (v != LX_OK) return v;
+    size_t mx = CHUNK_SLACK;
+    for (int64_t i = 0; i < nquartet; ++i) mx = std::max(mx, chunk_estimate(shells, quartets, i, i + 1, flags & LX_SOLID));
+    return (int64_t)(head_bytes(nshell, (int32_t)prim_count(shells, nshell)) + mx);
+}
+
+int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
+                 int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags, double* out,
+                 void* workspace, size_t workspace_bytes, void* cuda_stream) {
+    int v = validate(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, true);
+    if (v != LX_OK) return v;
+    if (nquartet == 0) return LX_OK;
+    if (!out) return LX_ERR_NULL;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return LX_ERR_WORKSPACE;
+    unsigned* status = nullptr;
+    if ((v = ensure_device(&status)) != LX_OK) return v;
+    const bool solid = flags & LX_SOLID;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const size_t head = head_bytes(nshell, nprim_total);
+    if (workspace_bytes < head + CHUNK_SLACK) return LX_ERR_WORKSPACE;
+    std::vector<Chunk> chunks;
+    if ((v = plan_chunks(shells, quartets, nquartet, solid, workspace_bytes - head, chunks)) != LX_OK) return v;
+
+    char* wsb = static_cast<char*>(workspace);
+    double* ws = static_cast<double*>(workspace);
+    // head: shells, exponents, raw and normalised coefficients
+    std::vector<char> hb(head, 0);
+    DShell* dsh = reinterpret_cast<DShell*>(hb.data());
+    for (int32_t s = 0; s < nshell; ++s) {
+        dsh[s].l = shells[s].l;
+        dsh[s].K = shells[s].nprim;
+        dsh[s].prim_off = shells[s].prim_offset;
+        for (int k = 0; k < 3; ++k) dsh[s].A[k] = shells[s].center[k];
+    }
+    const size_t o_exps = align256(sizeof(DShell) * (size_t)nshell);
+    const size_t o_coefs = o_exps + align256(sizeof(double) * (size_t)nprim_total);
+    const size_t o_ncoef = o_coefs + align256(sizeof(double) * (size_t)nprim_total);
+    std::memcpy(hb.data() + o_exps, exps, sizeof(double) * (size_t)nprim_total);
+    std::memcpy(hb.data() + o_coefs, coefs, sizeof(double) * (size_t)nprim_total);
+    cudaError_t e = cudaMemcpyAsync(wsb, hb.data(), o_ncoef, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const DShell* d_sh = reinterpret_cast<const DShell*>(wsb);
+    const double* d_exps = reinterpret_cast<const double*>(wsb + o_exps);
+    const double* d_coefs = reinterpret_cast<const double*>(wsb + o_coefs);
+    double* d_ncoef = reinterpret_cast<double*>(wsb + o_ncoef);
+    StageTimer tm{(flags & LX_TIME_STAGES) != 0, st};
+    if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
+    if ((e = launch_norm(d_sh, nshell, d_exps, d_coefs, d_ncoef, status, st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = tm.end(LX_STAGE_NORM, 1)) != cudaSuccess) return cuda_fail(e);
+
+    ChunkPlan P;
+    for (const auto& ch : chunks) {
+        build_chunk(shells, quartets, ch, solid, head, P);
+        if (head + P.total > workspace_bytes) return LX_ERR_WORKSPACE;
+        char* base = wsb + head;
+        e = cudaMemcpyAsync(base, P.blob.data(), P.off_data, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+        const DPair* d_pairs = reinterpret_cast<const DPair*>(base + P.off_pairs);
+        const DQuartet* d_q = reinterpret_cast<const DQuartet*>(base + P.off_quartets);
+        const WorkItem* d_ih = reinterpret_cast<const WorkItem*>(base + P.off_h);
+        const WorkItem* d_ibr = reinterpret_cast<const WorkItem*>(base + P.off_br);
+        const WorkItem* d_ig1 = reinterpret_cast<const WorkItem*>(base + P.off_g1);
+        const WorkItem* d_ig2 = reinterpret_cast<const WorkItem*>(base + P.off_g2);
+        if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
+        if ((e = launch_pair_h(d_pairs, d_ih, (int)P.items_h.size(), d_sh, d_exps, d_ncoef, ws, ws, status, st)) !=
+            cudaSuccess)
+            return cuda_fail(e);
+        if ((e = tm.end(LX_STAGE_PAIR, 1)) != cudaSuccess) return cuda_fail(e);
+        if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
+        if ((e = launch_boys_r(d_q, d_pairs, d_ibr, (int)P.items_br.size(), ws, status, st)) != cudaSuccess)
+            return cuda_fail(e);
+        if ((e = tm.end(LX_STAGE_BOYS_R, 1)) != cudaSuccess) return cuda_fail(e);
+        if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
+        if ((e = launch_gemm1(d_q, d_pairs, d_ig1, (int)P.items_g1.size(), ws, status, st)) != cudaSuccess)
+            return cuda_fail(e);
+        if ((e = tm.end(LX_STAGE_GEMM1, 1)) != cudaSuccess) return cuda_fail(e);
+        if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
+        if ((e = launch_gemm2(d_q, d_pairs, d_ig2, (int)P.items_g2.size(), ws, out, status, st)) != cudaSuccess)
+            return cuda_fail(e);
+        if ((e = tm.end(LX_STAGE_GEMM2, 1)) != cudaSuccess) return cuda_fail(e);
+    }
+    return LX_OK;
+}
+
+int lx_eri_sync_status(void* cuda_stream) {
+    unsigned* status = nullptr;
+    int v = ensure_device(&status);
+    if (v != LX_OK) return v;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(e);
+    unsigned word = 0;
+    if ((e = cudaMemcpyFromSymbol(&word, g_status_word, sizeof(word))) != cudaSuccess) return cuda_fail(e);
+    if (word) {
+        const unsigned zero = 0;
+        if ((e = cudaMemcpyToSymbol(g_status_word, &zero, sizeof(zero))) != cudaSuccess) return cuda_fail(e);
+        return LX_ERR_DEVICE_STATUS;
+    }
+    return LX_OK;
+}
+
+int lx_eri_stage_times(double* ms, int64_t* launches, int32_t nstage, void* cuda_stream) {
+    if (nstage < 0 || nstage > LX_NSTAGE) return LX_ERR_SIZE;
+    if (nstage > 0 && !ms) return LX_ERR_NULL;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int i = 0; i < nstage; ++i) {
+        ms[i] = 0.0;
+        if (launches) launches[i] = 0;
+    }
+    std::lock_guard<std::mutex> lock(g_timing_mutex);
+    std::vector<PendingTiming> keep;
+    int rc = LX_OK;
+    for (const auto& p : g_pending) {
+        if (p.stream != st) {
+            keep.push_back(p);
+            continue;
+        }
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, p.begin, p.end);
+        if (e != cudaSuccess) rc = cuda_fail(e);
+        if (p.stage < nstage) {
+            ms[p.stage] += t;
+            if (launches) launches[p.stage] += p.launches;
+        }
+        cudaEventDestroy(p.begin);
+        cudaEventDestroy(p.end);
+    }
+    g_pending.swap(keep);
+    return rc;
+}
+
+const char* lx_strerror(int code) {
+    switch (code) {
+        case LX_OK: return "success";
+        case LX_ERR_NULL: return "a required pointer is NULL";
+        case LX_ERR_SHELL: return "invalid shell (l, nprim, reserved field, primitive range or center)";
+        case LX_ERR_PRIMITIVE: return "invalid primitive (exponent must be finite and > 0, coefficient finite)";
+        case LX_ERR_QUARTET: return "invalid quartet (shell index out of range or negative out_offset)";
+        case LX_ERR_FLAGS: return "unknown flag bits";
+        case LX_ERR_WORKSPACE: return "workspace NULL, misaligned or too small";
+        case LX_ERR_CUDA: return "CUDA runtime error";
+        case LX_ERR_ARCH: return "current device is not compute capability 10.3 (GB300)";
+        case LX_ERR_DEVICE_STATUS: return "a kernel reported a bad index or input";
+        case LX_ERR_SIZE: return "a size argument is negative or too large";
+        default: return "unknown error code";
+    }
+}
+
+const char* lx_last_cuda_error(void) { return t_cuda_msg; }
+
+int lx_boys(int32_t mmax, const double* T, int64_t n, double* F, void* cuda_stream) {
+    if (mmax < 0 || mmax > LTOT || n < 0) return LX_ERR_SIZE;
+    if (n > 0 && (!T || !F)) return LX_ERR_NULL;
+    unsigned* status = nullptr;
+    int v = ensure_device(&status);
+    if (v != LX_OK) return v;
+    cudaError_t e = launch_boys(mmax, T, n, F, status, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? LX_OK : cuda_fail(e);
+}
+
+int lx_hermite_R(int32_t L, const double* params, int64_t n, double* R, void* cuda_stream) {
+    if (L < 0 || L > LTOT || n < 0) return LX_ERR_SIZE;
+    if (n > 0 && (!params || !R)) return LX_ERR_NULL;
+    unsigned* status = nullptr;
+    int v = ensure_device(&status);
+    if (v != LX_OK) return v;
+    cudaError_t e = launch_hermite_r(L, params, n, R, status, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? LX_OK : cuda_fail(e);
+}
+
+int lx_hermite_H(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
+                 int32_t nprim_total, const int32_t* pairs, int32_t npair, int32_t flags, double* H, int64_t stride,
+                 void* cuda_stream) {
+    const int32_t side = (flags & 0x100) ? 1 : 0;
+    const int32_t f = flags & ~0x100;
+    int v = validate(shells, nshell, exps, coefs, nprim_total, nullptr, 0, f, true);
+    if (v != LX_OK) return v;
+    if (npair < 0 || stride < 0) return LX_ERR_SIZE;
+    if (npair == 0) return LX_OK;
+    if (!pairs || !H) return LX_ERR_NULL;
+    const bool solid = f & LX_SOLID;
+    int64_t need = 0;
+    for (int32_t k = 0; k < npair; ++k) {
+        const int sa = pairs[2 * k], sb = pairs[2 * k + 1];
+        if (sa < 0 || sa >= nshell || sb < 0 || sb >= nshell) return LX_ERR_QUARTET;
+        need = std::max<int64_t>(need, (int64_t)nfun(shells[sa].l, solid) * nfun(shells[sb].l, solid) *
+                                           shells[sa].nprim * shells[sb].nprim * pyr(shells[sa].l + shells[sb].l));
+    }
+    if (stride < need) return LX_ERR_SIZE;
+    unsigned* status = nullptr;
+    if ((v = ensure_device(&status)) != LX_OK) return v;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // Scratch for descriptors and pair scalars, stream-ordered.
+    std::vector<DPair> dp(npair);
+    std::vector<WorkItem> items;
+    int64_t info_total = 0;
+    for (int32_t k = 0; k < npair; ++k) {
+        const int sa = pairs[2 * k], sb = pairs[2 * k + 1];
+        DPair& p = dp[k];
+        p.sa = sa;
+        p.sb = sb;
+        p.Kab = shells[sa].nprim * shells[sb].nprim;
+        p.nrow = nfun(shells[sa].l, solid) * nfun(shells[sb].l, solid);
+        p.np = pyr(shells[sa].l + shells[sb].l);
+        p.sign = side;
+        p.solid = solid ? 1 : 0;
+        p.info_off = info_total;
+        info_total += 4 * (int64_t)p.Kab;
+        for (int kp = 0; kp < p.Kab; ++kp) items.push_back({k, kp, 0, 0});
+    }
+    const size_t o_sh = 0, o_exps = align256(sizeof(DShell) * (size_t)nshell);
+    const size_t o_coefs = o_exps + align256(8 * (size_t)nprim_total);
+    const size_t o_ncoef = o_coefs + align256(8 * (size_t)nprim_total);
+    const size_t o_pairs = o_ncoef + align256(8 * (size_t)nprim_total);
+    const size_t o_items = o_pairs + align256(sizeof(DPair) * (size_t)npair);
+    const size_t o_info = o_items + align256(sizeof(WorkItem) * items.size());
+    const size_t scratch_bytes = o_info + align256(8 * (size_t)info_total);
+    char* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), scratch_bytes, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int32_t k = 0; k < npair; ++k) dp[k].h_off = (int64_t)k * stride;
+    std::vector<char> blob(o_info, 0);
+    DShell* dsh = reinterpret_cast<DShell*>(blob.data() + o_sh);
+    for (int32_t s = 0; s < nshell; ++s) {
+        dsh[s].l = shells[s].l;
+        dsh[s].K = shells[s].nprim;
+        dsh[s].prim_off = shells[s].prim_offset;
+        for (int k = 0; k < 3; ++k) dsh[s].A[k] = shells[s].center[k];
+    }
+    std::memcpy(blob.data() + o_exps, exps, 8 * (size_t)nprim_total);
+    std::memcpy(blob.data() + o_coefs, coefs, 8 * (size_t)nprim_total);
+    std::memcpy(blob.data() + o_pairs, dp.data(), sizeof(DPair) * dp.size());
+    std::memcpy(blob.data() + o_items, items.data(), sizeof(WorkItem) * items.size());
+    if ((e = cudaMemcpyAsync(scratch, blob.data(), o_info, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e);
+    const DShell* d_sh = reinterpret_cast<const DShell*>(scratch + o_sh);
+    const double* d_exps = reinterpret_cast<const double*>(scratch + o_exps);
+    const double* d_coefs = reinterpret_cast<const double*>(scratch + o_coefs);
+    double* d_ncoef = reinterpret_cast<double*>(scratch + o_ncoef);
+    if ((e = launch_norm(d_sh, nshell, d_exps, d_coefs, d_ncoef, status, st)) != cudaSuccess) return cuda_fail(e);
+    if ((e = launch_pair_h(reinterpret_cast<const DPair*>(scratch + o_pairs),
+                           reinterpret_cast<const WorkItem*>(scratch + o_items), (int)items.size(), d_sh, d_exps,
+                           d_ncoef, H, reinterpret_cast<double*>(scratch + o_info), status, st)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaFreeAsync(scratch, st)) != cudaSuccess) return cuda_fail(e);
+    return LX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,213 @@
+// Boys function (Eq. boys) and the auxiliary Hermite integrals [r]^(m) (Eq. md1).
+//
+// Boys: for T < 36, F_mmax(T) from an 8-term Taylor expansion around the nearest point
+// of a 0.1-spaced table of F_n(T_k), then the downward recursion
+// F_m = (2T F_{m+1} + exp(-T)) / (2m+1); for T >= 36, F_0 = (1/2) sqrt(pi/T) (erf(sqrt T)
+// differs from 1 by < 3e-17) and the upward recursion F_{m+1} = ((2m+1) F_m - exp(-T))/(2T).
+//
+// R: one warp per primitive quartet evaluates [r]^(m) for m = L-1 down to 0 in one shared
+// array of pyr(L) doubles, overwriting [r]^(m+1) with [r]^(m) (the paper's in-place
+// scheme, Section 3): within level m the totals n = |r| are processed from L-m down
+// to 1, so the inputs at totals n-1 and n-2 still hold level m+1 when they are read.
+#include <cmath>
+
+#include "lx_internal.cuh"
+
+namespace lx {
+
+namespace {
+
+__device__ double g_boys[BOYS_NROW * BOYS_NPT];
+
+constexpr double PI = 3.141592653589793238462643383279502884;
+
+__device__ inline void set_status(unsigned* st, unsigned bit) { atomicOr(st, bit); }
+
+// F_m(T) for m = 0..mmax (mmax <= LTOT) into F (any memory), one thread.
+__device__ void boys_eval(int mmax, double T, double* F) {
+    if (T < BOYS_TMAX) {
+        const int k = __double2int_rn(T * (1.0 / BOYS_DT));
+        const double d = k * BOYS_DT - T;  // -(T - T_k)
+        // F_mmax(T) = sum_j F_{mmax+j}(T_k) (-(T - T_k))^j / j!
+        const double* col = g_boys + k;
+        double f = 0.0, pw = 1.0;
+#pragma unroll
+        for (int j = 0; j < BOYS_ORDER; ++j) {
+            f += __ldg(col + (mmax + j) * BOYS_NPT) * pw;
+            pw *= d / (j + 1);
+        }
+        F[mmax] = f;
+        const double e = exp(-T), twoT = 2.0 * T;
+        for (int m = mmax - 1; m >= 0; --m) {
+            f = (twoT * f + e) / (2 * m + 1);
+            F[m] = f;
+        }
+    } else {
+        double f = 0.5 * sqrt(PI / T);
+        F[0] = f;
+        const double e = exp(-T), oo2T = 0.5 / T;
+        for (int m = 0; m < mmax; ++m) {
+            f = ((2 * m + 1) * f - e) * oo2T;
+            F[m + 1] = f;
+        }
+    }
+}
+
+// Within-total position s (0 <= s < (n+1)(n+2)/2) -> (i, v) with s = i(i+1)/2 + v.
+__device__ inline void split_pos(int s, int& i, int& v) {
+    i = (int)((sqrtf(8.0f * s + 1.0f) - 1.0f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= s) ++i;
+    while (i * (i + 1) / 2 > s) --i;
+    v = s - i * (i + 1) / 2;
+}
+
+// In-place Eq. md1 on R[pyr(L)] (shared memory), by one warp.  B[m] = [0]^(m), m = 0..L.
+// On return R holds [r]^(0).
+__device__ void hermite_r_warp(int L, double X, double Y, double Z, const double* B, double* R, int lane) {
+    if (lane == 0) R[0] = B[L];
+    __syncwarp();
+    for (int m = L - 1; m >= 0; --m) {
+        for (int n = L - m; n >= 1; --n) {
+            const int base = n * (n + 1) * (n + 2) / 6;  // pyr(n-1)
+            const int cnt = (n + 1) * (n + 2) / 2;
+            for (int s = lane; s < cnt; s += 32) {
+                int i, v;
+                split_pos(s, i, v);
+                const int u = i - v, t = n - i;
+                double val;
+                // [r + 1_d]^(m) = r_d [r - 1_d]^(m+1) + X_d [r]^(m+1), lowering the first
+                // nonzero direction of the target triplet
+                if (t > 0) {
+                    val = X * R[hidx(t - 1, u, v)];
+                    if (t > 1) val += (t - 1) * R[hidx(t - 2, u, v)];
+                } else if (u > 0) {
+                    val = Y * R[hidx(0, u - 1, v)];
+                    if (u > 1) val += (u - 1) * R[hidx(0, u - 2, v)];
+                } else {
+                    val = Z * R[hidx(0, 0, v - 1)];
+                    if (v > 1) val += (v - 1) * R[hidx(0, 0, v - 2)];
+                }
+                R[base + s] = val;
+            }
+            __syncwarp();
+        }
+        if (lane == 0) R[0] = B[m];
+        __syncwarp();
+    }
+}
+
+constexpr int BR_WARPS = 4;
+
+// One warp per primitive quartet: item.q = quartet, item.a = first primitive quartet of the
+// CTA's group of BR_WARPS (kpq = kp * kket + kq).
+__global__ void __launch_bounds__(BR_WARPS * 32) boys_r_kernel(const DQuartet* __restrict__ qd,
+                                                               const DPair* __restrict__ pairs,
+                                                               const WorkItem* __restrict__ items,
+                                                               double* __restrict__ ws, unsigned* status) {
+    extern __shared__ double smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const WorkItem it = items[blockIdx.x];
+    const DQuartet q = qd[it.q];
+    const int kpq = it.a + warp;
+    if (kpq >= q.kbra * q.kket) return;
+    const int nr = q.nr;
+    double* R = smem + warp * (nr + LTOT + 1);
+    double* B = R + nr;
+    const int kp = kpq / q.kket, kq = kpq - kp * q.kket;
+    const DPair pb = pairs[q.pb], pk = pairs[q.pk];
+    const double* ib = ws + pb.info_off + 4 * (int64_t)kp;
+    const double* ik = ws + pk.info_off + 4 * (int64_t)kq;
+    const double zp = ib[0], zq = ik[0];
+    const double X = ib[1] - ik[1], Y = ib[2] - ik[2], Z = ib[3] - ik[3];
+    const double rho = zp * zq / (zp + zq);
+    const double T = rho * (X * X + Y * Y + Z * Z);
+    if (lane == 0) {
+        boys_eval(q.L, T, B);
+        // [0]^(m) = (-2 rho)^m 2 pi^{5/2} / (zeta_p zeta_q sqrt(zeta_p + zeta_q)) F_m(T)
+        double f = 2.0 * PI * PI * sqrt(PI) / (zp * zq * sqrt(zp + zq));
+        for (int m = 0; m <= q.L; ++m) {
+            B[m] *= f;
+            f *= -2.0 * rho;
+        }
+    }
+    __syncwarp();
+    hermite_r_warp(q.L, X, Y, Z, B, R, lane);
+    double* out = ws + q.rr_off + (int64_t)kpq * nr;
+    for (int r = lane; r < nr; r += 32) out[r] = R[r];
+}
+
+__global__ void boys_stage_kernel(int mmax, const double* __restrict__ T, int64_t n, double* __restrict__ F,
+                                  unsigned* status) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double t = T[i];
+    double buf[LTOT + 1];
+    if (!(t >= 0.0) || !isfinite(t)) {
+        set_status(status, ST_BAD_INPUT);
+        for (int m = 0; m <= mmax; ++m) F[i * (mmax + 1) + m] = nan("");
+        return;
+    }
+    boys_eval(mmax, t, buf);
+    for (int m = 0; m <= mmax; ++m) F[i * (mmax + 1) + m] = buf[m];
+}
+
+// Stage entry: params[5i..] = (rho, X, Y, Z, pref) -> R[i * pyr(L) ..].
+__global__ void __launch_bounds__(BR_WARPS * 32) hermite_r_stage_kernel(int L, const double* __restrict__ params,
+                                                                        int64_t n, double* __restrict__ Rout) {
+    extern __shared__ double smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t item = (int64_t)blockIdx.x * BR_WARPS + warp;
+    if (item >= n) return;
+    const int nr = pyr(L);
+    double* R = smem + warp * (nr + LTOT + 1);
+    double* B = R + nr;
+    const double rho = params[5 * item], X = params[5 * item + 1], Y = params[5 * item + 2],
+                 Z = params[5 * item + 3], pref = params[5 * item + 4];
+    if (lane == 0) {
+        boys_eval(L, rho * (X * X + Y * Y + Z * Z), B);
+        double f = pref;
+        for (int m = 0; m <= L; ++m) {
+            B[m] *= f;
+            f *= -2.0 * rho;
+        }
+    }
+    __syncwarp();
+    hermite_r_warp(L, X, Y, Z, B, R, lane);
+    for (int r = lane; r < nr; r += 32) Rout[item * nr + r] = R[r];
+}
+
+size_t br_smem(int L) { return sizeof(double) * BR_WARPS * (size_t)(pyr(L) + LTOT + 1); }
+
+}  // namespace
+
+cudaError_t init_boys_table(const double* host_table) {
+    cudaError_t e = cudaMemcpyToSymbol(g_boys, host_table, sizeof(double) * BOYS_NROW * BOYS_NPT);
+    if (e != cudaSuccess) return e;
+    const size_t maxsm = br_smem(LTOT);
+    e = cudaFuncSetAttribute(boys_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxsm);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(hermite_r_stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxsm);
+}
+
+cudaError_t launch_boys_r(const DQuartet* qd, const DPair* pairs, const WorkItem* items, int nitems, double* ws,
+                          unsigned* status, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    boys_r_kernel<<<nitems, BR_WARPS * 32, br_smem(LTOT), st>>>(qd, pairs, items, ws, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_boys(int mmax, const double* T, int64_t n, double* F, unsigned* status, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    boys_stage_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(mmax, T, n, F, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hermite_r(int L, const double* params, int64_t n, double* R, unsigned* status, cudaStream_t st) {
+    (void)status;
+    if (n <= 0) return cudaSuccess;
+    hermite_r_stage_kernel<<<(unsigned)((n + BR_WARPS - 1) / BR_WARPS), BR_WARPS * 32, br_smem(L), st>>>(L, params,
+                                                                                                          n, R);
+    return cudaGetLastError();
+}
+
+}  // namespace lx

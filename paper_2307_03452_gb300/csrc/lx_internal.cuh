@@ -1,0 +1,102 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lx_eri.h"
+
+namespace lx {
+
+constexpr int LMAX = LX_LMAX;                       // largest shell l
+constexpr int LTOT = 4 * LMAX;                      // largest total L of a quartet (24)
+constexpr int NCART_MAX = (LMAX + 1) * (LMAX + 2) / 2;  // 28
+constexpr int NSOL_MAX = 2 * LMAX + 1;              // 13
+constexpr int NHERM_TOT = (LTOT + 1) * (LTOT + 2) * (LTOT + 3) / 6;  // pyr(24) = 2925
+
+// Boys table: F_n(T_k), n = 0..BOYS_NROW-1, T_k = k * BOYS_DT for k = 0..BOYS_NPT-1.
+// Taylor expansion of order BOYS_ORDER-1 around the nearest grid point covers T < BOYS_TMAX.
+constexpr int BOYS_ORDER = 8;
+constexpr int BOYS_NROW = LTOT + BOYS_ORDER;        // 32
+constexpr int BOYS_NPT = 361;
+constexpr double BOYS_DT = 0.1;
+constexpr double BOYS_TMAX = 36.0;
+
+__host__ __device__ inline int pyr(int n) { return (n + 1) * (n + 2) * (n + 3) / 6; }
+__host__ __device__ inline int ncart(int l) { return (l + 1) * (l + 2) / 2; }
+__host__ __device__ inline int nfun(int l, bool solid) { return solid ? 2 * l + 1 : (l + 1) * (l + 2) / 2; }
+// Pyramidal ordinal of a Hermite triplet (t,u,v): lower totals first; within total n,
+// i = u+v ascending, then v ascending.  Within one total this is the Cartesian order.
+__host__ __device__ inline int hidx(int t, int u, int v) {
+    int n = t + u + v, i = u + v;
+    return n * (n + 1) * (n + 2) / 6 + i * (i + 1) / 2 + v;
+}
+
+// Device status word bits (see lx_eri_sync_status).
+enum : unsigned { ST_BAD_INDEX = 1u, ST_BAD_INPUT = 2u, ST_TIMEOUT = 4u };
+
+struct DShell {  // 48 bytes
+    int l, K, prim_off, pad;
+    double A[3];
+    double pad2;
+};
+
+struct DPair {  // one shell pair on one side of the quartet
+    int sa, sb;     // shells
+    int Kab;        // K_a * K_b primitive pairs
+    int nrow;       // nfun(l_a) nfun(l_b)
+    int np;         // pyr(l_a + l_b)
+    int sign;       // 1: ket side, columns carry (-1)^{|p|}
+    int solid;      // 1: solid-harmonic rows
+    int pad;
+    int64_t h_off;     // H block (doubles): [nrow][Kab*np]
+    int64_t info_off;  // pair scalars (doubles): [Kab][4] = zeta_p, P
+};
+
+struct DQuartet {
+    int pb, pk;          // bra / ket pair ids
+    int L, np, nq;       // L = l_bra + l_ket, Hermite counts
+    int nab, ncd;        // output rows / columns
+    int kbra, kket;      // primitive-pair counts
+    int nr;              // pyr(L)
+    int64_t rr_off;      // [kbra][kket][nr] doubles
+    int64_t x_off;       // [nab][kket*nq] doubles
+    int64_t out_off;     // output block in the caller's buffer
+};
+
+struct WorkItem {  // generic work descriptor: owner + two tile indices
+    int q, a, b, c;
+};
+
+// ----------------------------------------------------------------- per-TU launchers
+// Tables (called once per device with that device current).
+cudaError_t init_boys_table(const double* host_table);      // lx_boys_r.cu
+cudaError_t init_prep_tables(const double* host_coefs, const int* host_tuv);  // lx_prep.cu
+cudaError_t init_tuv_table(const int* host_tuv);           // lx_gemm.cu
+
+cudaError_t launch_norm(const DShell* sh, int nshell, const double* exps, const double* coefs, double* ncoef,
+                        unsigned* status, cudaStream_t st);
+// H blocks at ws + h_off, pair scalars at ws_info + info_off.
+cudaError_t launch_pair_h(const DPair* pairs, const WorkItem* items, int nitems, const DShell* sh,
+                          const double* exps, const double* ncoef, double* ws, double* ws_info, unsigned* status,
+                          cudaStream_t st);
+cudaError_t launch_boys_r(const DQuartet* qd, const DPair* pairs, const WorkItem* items, int nitems, double* ws,
+                          unsigned* status, cudaStream_t st);
+cudaError_t launch_gemm1(const DQuartet* qd, const DPair* pairs, const WorkItem* items, int nitems, double* ws,
+                         unsigned* status, cudaStream_t st);
+cudaError_t launch_gemm2(const DQuartet* qd, const DPair* pairs, const WorkItem* items, int nitems,
+                         const double* ws_in, double* out, unsigned* status, cudaStream_t st);
+cudaError_t launch_boys(int mmax, const double* T, int64_t n, double* F, unsigned* status, cudaStream_t st);
+cudaError_t launch_hermite_r(int L, const double* params, int64_t n, double* R, unsigned* status, cudaStream_t st);
+
+// GEMM tiling (shared by the planner and the kernels).
+constexpr int GEMM_BM = 32;
+constexpr int GEMM_BN = 64;
+constexpr int GEMM_BK = 16;
+
+// Host-side table generators (lx_tables.cpp).
+void make_boys_table(double* table);        // BOYS_NROW * BOYS_NPT
+void make_solid_coefs(double* coefs);       // packed: l = 0..LMAX, (2l+1) x ncart(l) each
+int solid_offset(int l);                    // offset of shell l's block in the packed array
+void make_tuv_table(int* tuv);              // NHERM_TOT entries: t | u << 8 | v << 16
+
+}  // namespace lx

@@ -1,0 +1,276 @@
+"""Python binding of the C ABI in ``include/lx_eri.h`` (argument marshalling only).
+
+Every arithmetic step runs in the CUDA library ``liblx_eri.so``; this module packs the
+host descriptors, passes device pointers taken from torch tensors, and raises if the
+library cannot be loaded.  There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SHELL_DTYPE = np.dtype([("l", "<i4"), ("nprim", "<i4"), ("prim_offset", "<i4"), ("reserved", "<i4"),
+                        ("center", "<f8", (3,))])
+QUARTET_DTYPE = np.dtype([("s", "<i4", (4,)), ("out_offset", "<i8")])
+assert SHELL_DTYPE.itemsize == 40 and QUARTET_DTYPE.itemsize == 24
+
+LX_CART = 0x0
+LX_SOLID = 0x1
+LX_KET_SIGN = 0x100  # lx_hermite_H: multiply column p by (-1)^|p|
+LMAX = 6
+KMAX = 16
+
+_lock = threading.Lock()
+_lib = None
+
+#: every symbol the header declares
+EXPORTS = sorted(["lx_eri_out_size", "lx_eri_workspace_size", "lx_eri_workspace_min", "lx_eri_batch",
+                  "lx_eri_sync_status", "lx_eri_stage_times", "lx_strerror", "lx_last_cuda_error", "lx_boys",
+                  "lx_hermite_R", "lx_hermite_H"])
+LX_TIME_STAGES = 0x200
+STAGES = ["norm", "pair_h", "boys_r", "gemm1", "gemm2"]
+
+
+class LxError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        lib = load()
+        msg = lib.lx_strerror(code).decode()
+        if code == -7:
+            msg += f" ({lib.lx_last_cuda_error().decode()})"
+        super().__init__(f"{where}: error {code}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblx_eri.so (building it first if it is missing and nvcc is present)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        c_i32, c_i64, c_vp, c_sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t
+        lib.lx_eri_out_size.argtypes = [c_vp, c_i32, c_vp, c_i64, c_i32]
+        lib.lx_eri_out_size.restype = c_i64
+        lib.lx_eri_workspace_size.argtypes = [c_vp, c_i32, c_vp, c_i64, c_i32]
+        lib.lx_eri_workspace_size.restype = c_i64
+        lib.lx_eri_workspace_min.argtypes = [c_vp, c_i32, c_vp, c_i64, c_i32]
+        lib.lx_eri_workspace_min.restype = c_i64
+        lib.lx_eri_batch.argtypes = [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_i64, c_i32, c_vp, c_vp, c_sz, c_vp]
+        lib.lx_eri_batch.restype = ctypes.c_int
+        lib.lx_eri_sync_status.argtypes = [c_vp]
+        lib.lx_eri_sync_status.restype = ctypes.c_int
+        lib.lx_eri_stage_times.argtypes = [c_vp, c_vp, c_i32, c_vp]
+        lib.lx_eri_stage_times.restype = ctypes.c_int
+        lib.lx_strerror.argtypes = [ctypes.c_int]
+        lib.lx_strerror.restype = ctypes.c_char_p
+        lib.lx_last_cuda_error.argtypes = []
+        lib.lx_last_cuda_error.restype = ctypes.c_char_p
+        lib.lx_boys.argtypes = [c_i32, c_vp, c_i64, c_vp, c_vp]
+        lib.lx_boys.restype = ctypes.c_int
+        lib.lx_hermite_R.argtypes = [c_i32, c_vp, c_i64, c_vp, c_vp]
+        lib.lx_hermite_R.restype = ctypes.c_int
+        lib.lx_hermite_H.argtypes = [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_i32, c_i32, c_vp, c_i64, c_vp]
+        lib.lx_hermite_H.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise LxError(code, where)
+
+
+def nfun(l: int, solid: bool) -> int:
+    return 2 * l + 1 if solid else (l + 1) * (l + 2) // 2
+
+
+def pack_shells(basis: dict) -> np.ndarray:
+    n = len(basis["l"])
+    sh = np.zeros(n, dtype=SHELL_DTYPE)
+    sh["l"] = basis["l"]
+    sh["nprim"] = basis["nprim"]
+    sh["prim_offset"] = basis["prim_off"]
+    sh["center"] = np.asarray(basis["center"], dtype=np.float64).reshape(n, 3)
+    return sh
+
+
+def pack_quartets(basis: dict, quartets, solid: bool, out_off=None) -> tuple[np.ndarray, np.ndarray]:
+    qs = np.asarray(quartets, dtype=np.int32).reshape(-1, 4)
+    l = np.asarray(basis["l"])
+    nf = (2 * l + 1) if solid else (l + 1) * (l + 2) // 2
+    sizes = nf[qs[:, 0]].astype(np.int64) * nf[qs[:, 1]] * nf[qs[:, 2]] * nf[qs[:, 3]]
+    if out_off is None:
+        out_off = np.zeros(len(qs), dtype=np.int64)
+        if len(qs):
+            out_off[1:] = np.cumsum(sizes)[:-1]
+    q = np.zeros(len(qs), dtype=QUARTET_DTYPE)
+    q["s"] = qs
+    q["out_offset"] = out_off
+    return q, sizes
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Batch:
+    """Host descriptors of one batch, packed once (the planner's input)."""
+
+    def __init__(self, basis: dict, quartets, solid: bool, out_off=None):
+        self.solid = bool(solid)
+        self.flags = LX_SOLID if solid else LX_CART
+        self.shells = pack_shells(basis)
+        self.exps = np.ascontiguousarray(basis["exps"], dtype=np.float64)
+        self.coefs = np.ascontiguousarray(basis["coefs"], dtype=np.float64)
+        self.quartets, self.sizes = pack_quartets(basis, quartets, solid, out_off)
+        lib = load()
+        n = lib.lx_eri_out_size(_ptr(self.shells), len(self.shells), _ptr(self.quartets), len(self.quartets), self.flags)
+        if n < 0:
+            raise LxError(int(n), "lx_eri_out_size")
+        self.out_size = int(n)
+
+    def pin(self):
+        """Move the host descriptors into pinned (page-locked) memory, so that the library's
+        uploads are asynchronous DMA copies."""
+        import torch
+        self._pinned = []
+
+        def to_pinned(a):
+            t = torch.empty(max(a.nbytes, 1), dtype=torch.uint8, pin_memory=True)
+            v = t.numpy()[: a.nbytes].view(a.dtype).reshape(a.shape)
+            v[...] = a
+            self._pinned.append(t)
+            return v
+
+        self.shells = to_pinned(self.shells)
+        self.exps = to_pinned(self.exps)
+        self.coefs = to_pinned(self.coefs)
+        self.quartets = to_pinned(self.quartets)
+        return self
+
+    def host_bytes(self) -> int:
+        """Bytes of host descriptors passed per call (shells, exponents, coefficients, quartets)."""
+        return int(self.shells.nbytes + self.exps.nbytes + self.coefs.nbytes + self.quartets.nbytes)
+
+    @property
+    def nquartet(self) -> int:
+        return len(self.quartets)
+
+    def workspace_size(self) -> int:
+        n = load().lx_eri_workspace_size(_ptr(self.shells), len(self.shells), _ptr(self.quartets),
+                                         len(self.quartets), self.flags)
+        if n < 0:
+            raise LxError(int(n), "lx_eri_workspace_size")
+        return int(n)
+
+    def workspace_min(self) -> int:
+        n = load().lx_eri_workspace_min(_ptr(self.shells), len(self.shells), _ptr(self.quartets),
+                                        len(self.quartets), self.flags)
+        if n < 0:
+            raise LxError(int(n), "lx_eri_workspace_min")
+        return int(n)
+
+    def run(self, out, workspace, stream=None, time_stages: bool = False):
+        """Enqueue lx_eri_batch; out and workspace are CUDA tensors (float64 / uint8)."""
+        flags = self.flags | (LX_TIME_STAGES if time_stages else 0)
+        rc = load().lx_eri_batch(_ptr(self.shells), len(self.shells), _ptr(self.exps), _ptr(self.coefs),
+                                 len(self.exps), _ptr(self.quartets), len(self.quartets), flags,
+                                 ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(workspace.data_ptr()),
+                                 workspace.numel() * workspace.element_size(), ctypes.c_void_p(_stream_ptr(stream)))
+        _check(rc, "lx_eri_batch")
+
+
+def stage_times(stream=None) -> tuple[dict, dict]:
+    """Per-stage device milliseconds and launch counts of the LX_TIME_STAGES calls on `stream`
+    since the last read (waits for the stream)."""
+    ms = np.zeros(len(STAGES))
+    n = np.zeros(len(STAGES), dtype=np.int64)
+    _check(load().lx_eri_stage_times(_ptr(ms), _ptr(n), len(STAGES), ctypes.c_void_p(_stream_ptr(stream))),
+           "lx_eri_stage_times")
+    return dict(zip(STAGES, ms.tolist())), dict(zip(STAGES, n.tolist()))
+
+
+def sync_status(stream=None):
+    _check(load().lx_eri_sync_status(ctypes.c_void_p(_stream_ptr(stream))), "lx_eri_sync_status")
+
+
+def alloc_workspace(nbytes: int, device="cuda"):
+    import torch
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def eri(basis: dict, quartets, solid: bool = True, device="cuda", workspace_limit: int | None = None,
+        stream=None):
+    """Evaluate (ab|cd) for every quartet on the GPU; returns (out, out_offsets) with out a
+    float64 CUDA tensor holding each quartet's row-major (a,b,c,d) block."""
+    import torch
+    b = Batch(basis, quartets, solid)
+    need = b.workspace_size()
+    if workspace_limit is not None:
+        need = max(min(need, int(workspace_limit)), b.workspace_min())
+    out = torch.empty(max(b.out_size, 1), dtype=torch.float64, device=device)
+    ws = alloc_workspace(need, device)
+    b.run(out, ws, stream)
+    sync_status(stream)
+    return out[: b.out_size], b.quartets["out_offset"].copy()
+
+
+def boys(mmax: int, T, stream=None):
+    """F_m(T) (Eq. boys) for a float64 CUDA tensor T: returns (len(T), mmax+1)."""
+    import torch
+    T = T.contiguous()
+    F = torch.empty((T.numel(), mmax + 1), dtype=torch.float64, device=T.device)
+    _check(load().lx_boys(mmax, ctypes.c_void_p(T.data_ptr()), T.numel(), ctypes.c_void_p(F.data_ptr()),
+                          ctypes.c_void_p(_stream_ptr(stream))), "lx_boys")
+    return F
+
+
+def hermite_R(L: int, params, stream=None):
+    """[r]^(0) (Eq. md1) for params (n, 5) = (rho, PQx, PQy, PQz, pref): returns (n, pyr(L))."""
+    import torch
+    params = params.contiguous()
+    n = params.shape[0]
+    npyr = (L + 1) * (L + 2) * (L + 3) // 6
+    R = torch.empty((n, npyr), dtype=torch.float64, device=params.device)
+    _check(load().lx_hermite_R(L, ctypes.c_void_p(params.data_ptr()), n, ctypes.c_void_p(R.data_ptr()),
+                               ctypes.c_void_p(_stream_ptr(stream))), "lx_hermite_R")
+    return R
+
+
+def hermite_H(basis: dict, pairs, solid: bool, ket_sign: bool = False, device="cuda", stream=None):
+    """H matrices of shell pairs: returns (npair, stride) float64 CUDA tensor and the stride."""
+    import torch
+    sh = pack_shells(basis)
+    ex = np.ascontiguousarray(basis["exps"], dtype=np.float64)
+    co = np.ascontiguousarray(basis["coefs"], dtype=np.float64)
+    pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+    l, K = np.asarray(basis["l"]), np.asarray(basis["nprim"])
+    pyr = lambda n: (n + 1) * (n + 2) * (n + 3) // 6
+    stride = max(nfun(l[a], solid) * nfun(l[b], solid) * K[a] * K[b] * pyr(l[a] + l[b]) for a, b in pr)
+    H = torch.empty((len(pr), stride), dtype=torch.float64, device=device)
+    flags = (LX_SOLID if solid else LX_CART) | (LX_KET_SIGN if ket_sign else 0)
+    _check(load().lx_hermite_H(_ptr(sh), len(sh), _ptr(ex), _ptr(co), len(ex), _ptr(pr), len(pr), flags,
+                               ctypes.c_void_p(H.data_ptr()), stride, ctypes.c_void_p(_stream_ptr(stream))),
+           "lx_hermite_H")
+    return H, stride

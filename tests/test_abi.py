@@ -1,0 +1,147 @@
+"""The C-ABI library loads, exports every symbol include/lx_eri.h declares, and its host
+side rejects invalid input with the documented error codes (no GPU needed: validation
+precedes any device work)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2307_03452_gb300 import inputs, lx
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "lx_eri.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lx_[a-zA-Z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = lx.load()
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), f"missing export {name}"
+    assert sorted(lx.EXPORTS) == names
+
+
+def test_error_strings():
+    lib = lx.load()
+    for code in [0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10]:
+        s = lib.lx_strerror(code).decode()
+        assert s and s != "unknown error code"
+    assert lib.lx_strerror(12345).decode() == "unknown error code"
+
+
+def _batch(nq=2, l=(4, 4, 4, 4)):
+    b, q = inputs.uniform_class(l, nq, 3)
+    return b, q
+
+
+def _call_batch(b, q, flags=lx.LX_SOLID, shells=None, exps=None, coefs=None, quartets=None, out=1, ws=256,
+                nprim=None):
+    lib = lx.load()
+    sh = lx.pack_shells(b) if shells is None else shells
+    ex = np.ascontiguousarray(b["exps"]) if exps is None else exps
+    co = np.ascontiguousarray(b["coefs"]) if coefs is None else coefs
+    qs = lx.pack_quartets(b, q, True)[0] if quartets is None else quartets
+    npr = len(ex) if nprim is None else nprim
+    # fake non-null device pointers: validation rejects the input before they are touched
+    return lib.lx_eri_batch(sh.ctypes.data_as(ctypes.c_void_p), len(sh), ex.ctypes.data_as(ctypes.c_void_p),
+                            co.ctypes.data_as(ctypes.c_void_p), npr, qs.ctypes.data_as(ctypes.c_void_p), len(qs),
+                            flags, ctypes.c_void_p(out), ctypes.c_void_p(ws), 1 << 20, None)
+
+
+def test_rejects_bad_angular_momentum():
+    b, q = _batch()
+    sh = lx.pack_shells(b)
+    sh["l"][1] = 7
+    assert _call_batch(b, q, shells=sh) == -2
+    sh["l"][1] = -1
+    assert _call_batch(b, q, shells=sh) == -2
+
+
+def test_rejects_bad_contraction_degree_and_reserved():
+    b, q = _batch()
+    sh = lx.pack_shells(b)
+    sh["nprim"][0] = 0
+    assert _call_batch(b, q, shells=sh) == -2
+    sh = lx.pack_shells(b)
+    sh["nprim"][0] = 17
+    assert _call_batch(b, q, shells=sh) == -2
+    sh = lx.pack_shells(b)
+    sh["reserved"][2] = 1
+    assert _call_batch(b, q, shells=sh) == -2
+
+
+def test_rejects_nonfinite_center_and_primitive_range():
+    b, q = _batch()
+    sh = lx.pack_shells(b)
+    sh["center"][3, 1] = np.nan
+    assert _call_batch(b, q, shells=sh) == -2
+    sh = lx.pack_shells(b)
+    sh["prim_offset"][0] = len(b["exps"])
+    assert _call_batch(b, q, shells=sh) == -2
+
+
+@pytest.mark.parametrize("bad", [0.0, -1.0, np.inf, np.nan])
+def test_rejects_bad_exponent(bad):
+    b, q = _batch()
+    ex = np.ascontiguousarray(b["exps"]).copy()
+    ex[2] = bad
+    assert _call_batch(b, q, exps=ex) == -3
+
+
+def test_rejects_bad_coefficient():
+    b, q = _batch()
+    co = np.ascontiguousarray(b["coefs"]).copy()
+    co[0] = np.inf
+    assert _call_batch(b, q, coefs=co) == -3
+
+
+def test_rejects_bad_quartets_and_flags():
+    b, q = _batch()
+    qs = lx.pack_quartets(b, q, True)[0]
+    qs["s"][1, 2] = 999
+    assert _call_batch(b, q, quartets=qs) == -4
+    qs = lx.pack_quartets(b, q, True)[0]
+    qs["out_offset"][0] = -5
+    assert _call_batch(b, q, quartets=qs) == -4
+    assert _call_batch(b, q, flags=0x40) == -5
+
+
+def test_rejects_null_and_workspace():
+    b, q = _batch()
+    assert _call_batch(b, q, out=0) == -1
+    assert _call_batch(b, q, ws=0) == -6
+    assert _call_batch(b, q, ws=8) == -6  # not 256-byte aligned
+
+
+def test_empty_batch_is_a_noop():
+    b, q = _batch()
+    lib = lx.load()
+    sh = lx.pack_shells(b)
+    rc = lib.lx_eri_batch(sh.ctypes.data_as(ctypes.c_void_p), len(sh), b["exps"].ctypes.data_as(ctypes.c_void_p),
+                          b["coefs"].ctypes.data_as(ctypes.c_void_p), len(b["exps"]), None, 0, 1, None, None, 0,
+                          None)
+    assert rc == 0
+
+
+def test_sizes():
+    b, q = inputs.iiii_fp64(8)
+    bs = lx.Batch(b, q, True)
+    assert bs.out_size == 8 * 13 ** 4
+    bc = lx.Batch(b, q, False)
+    assert bc.out_size == 8 * 28 ** 4
+    # workspace: at least H (both sides), [r]^(0) and [ab|q] of every quartet
+    per_q = 8 * (2 * 169 * 455 + 2925 + 169 * 455)
+    assert bs.workspace_size() >= 8 * per_q
+    assert bs.workspace_min() < bs.workspace_size()
+    # custom offsets: out size follows the largest block end
+    qs = np.asarray(q)
+    off = np.arange(8, dtype=np.int64) * 13 ** 4 * 2
+    b2 = lx.Batch(b, qs, True, out_off=off)
+    assert b2.out_size == off[-1] + 13 ** 4

@@ -1,0 +1,296 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: the plain FP64 path must match the oracle within 1e-11 of the largest |integral|
+of each quartet class in the batch; the Boys function, the [r]^(0) vectors and the H
+matrices are compared stage by stage, each relative to its own magnitude.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_03452_gb300 import inputs, lx
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_ERI = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    torch.cuda.set_device(0)
+
+
+def pyr(n):
+    return (n + 1) * (n + 2) * (n + 3) // 6
+
+
+def tuv_list(L):
+    out = []
+    for n in range(L + 1):
+        for i in range(n + 1):
+            for v in range(i + 1):
+                out.append((n - i, i - v, v))
+    return out
+
+
+def assert_eri_close(basis, quartets, got, ref, off, solid, tol=TOL_ERI):
+    """Per class: max |got - ref| <= tol * max |ref| over that class."""
+    l = np.asarray(basis["l"])
+    qs = np.asarray(quartets)
+    classes = {}
+    for i, q in enumerate(qs):
+        cls = tuple(int(l[s]) for s in q)
+        n = int(np.prod([2 * x + 1 if solid else (x + 1) * (x + 2) // 2 for x in cls]))
+        classes.setdefault(cls, []).append((off[i], n))
+    for cls, blocks in classes.items():
+        idx = np.concatenate([np.arange(o, o + n) for o, n in blocks])
+        scale = np.abs(ref[idx]).max()
+        err = np.abs(got[idx] - ref[idx]).max()
+        assert np.all(np.isfinite(got[idx])), f"non-finite output for class {cls}"
+        assert err <= tol * scale, f"class {cls}: max err {err:.3e} > {tol:.0e} * {scale:.3e}"
+
+
+def run_and_check(basis, quartets, solid, **kw):
+    out, off = lx.eri(basis, quartets, solid=solid, **kw)
+    ref, roff = oracle.eri(basis, quartets, solid=solid)
+    assert np.array_equal(off, roff)
+    got = out.cpu().numpy()
+    assert_eri_close(basis, quartets, got, ref, off, solid)
+    return got, ref
+
+
+# ---------------------------------------------------------------- stage: Boys
+
+def test_boys_stage_matches_oracle():
+    T = np.concatenate([[0.0, 1e-14, 1e-9], np.logspace(-6, 4.7, 400), np.arange(0, 36.05, 0.1),
+                        np.arange(0.05, 36, 0.1), np.linspace(35.9, 36.1, 41), [36.0, 80.0, 80.5, 1e5]])
+    mmax = 24
+    F = lx.boys(mmax, torch.tensor(T, dtype=torch.float64, device="cuda")).cpu().numpy()
+    ref = np.stack([oracle.boys(mmax, t) for t in T])
+    rel = np.abs(F - ref) / np.abs(ref)
+    assert rel.max() <= 5e-14, f"max rel err {rel.max():.3e} at T={T[np.unravel_index(rel.argmax(), rel.shape)[0]]}"
+
+
+def test_boys_stage_small_mmax_and_empty():
+    T = torch.tensor([0.5, 40.0], dtype=torch.float64, device="cuda")
+    F = lx.boys(0, T).cpu().numpy()
+    assert F.shape == (2, 1)
+    assert F[0, 0] == pytest.approx(math.sqrt(math.pi / (4 * 0.5)) * math.erf(math.sqrt(0.5)), rel=1e-14)
+    assert lx.boys(4, torch.zeros(0, dtype=torch.float64, device="cuda")).shape == (0, 5)
+
+
+# ---------------------------------------------------------------- stage: R
+
+@pytest.mark.parametrize("L", [0, 1, 2, 5, 8, 12, 16, 20, 24])
+def test_hermite_R_stage_matches_oracle(L):
+    rng = np.random.default_rng(L)
+    n = 37  # several CTAs and a ragged tail
+    rho = np.exp(rng.uniform(np.log(0.02), np.log(40), n))
+    PQ = rng.uniform(-4, 4, (n, 3))
+    PQ[0] = 0.0  # T = 0
+    pref = np.exp(rng.uniform(-2, 2, n))
+    params = np.column_stack([rho, PQ, pref])
+    R = lx.hermite_R(L, torch.tensor(params, device="cuda")).cpu().numpy()
+    idx = tuv_list(L)
+    for i in range(n):
+        box = oracle.hermite_R(L, rho[i], PQ[i], pref[i])
+        ref = np.array([box[t, u, v] for t, u, v in idx])
+        scale = np.abs(ref).max()
+        # Eq. md1 is ill-conditioned at high L and large T: its FP64 result moves by up to
+        # ~1e-9 of the largest entry when rho or PQ changes by one ulp.  The bound is
+        # 2e-12 of the largest entry plus 4x that one-ulp sensitivity, measured on the oracle.
+        ulp = 2.3e-16
+        s1 = oracle.hermite_R(L, rho[i] * (1 + ulp), PQ[i], pref[i])
+        s2 = oracle.hermite_R(L, rho[i], PQ[i] * (1 + ulp), pref[i])
+        sens = max(np.abs(s1 - box).max(), np.abs(s2 - box).max())
+        assert np.abs(R[i] - ref).max() <= 2e-12 * scale + 4 * sens, f"item {i}"
+
+
+# ---------------------------------------------------------------- stage: H
+
+def oracle_H(basis, sa, sb, solid, ket_sign):
+    """H of one shell pair from the oracle's building blocks (E, solid coefficients,
+    contraction normalisation), laid out [ab][kp * pyr(la+lb) + idx(p)]."""
+    la, lb = int(basis["l"][sa]), int(basis["l"][sb])
+    oa, ob = int(basis["prim_off"][sa]), int(basis["prim_off"][sb])
+    Ka, Kb = int(basis["nprim"][sa]), int(basis["nprim"][sb])
+    za, zb = basis["exps"][oa:oa + Ka], basis["exps"][ob:ob + Kb]
+    ca = oracle.contract_norm(la, za, basis["coefs"][oa:oa + Ka])
+    cb = oracle.contract_norm(lb, zb, basis["coefs"][ob:ob + Kb])
+    A, B = basis["center"][sa], basis["center"][sb]
+    comps_a = [(la - i, i - j, j) for i in range(la + 1) for j in range(i + 1)]
+    comps_b = [(lb - i, i - j, j) for i in range(lb + 1) for j in range(i + 1)]
+    herm = tuv_list(la + lb)
+    np_ = len(herm)
+    blocks = []
+    for i in range(Ka):
+        for j in range(Kb):
+            E = [oracle.hermite_E(la, lb, za[i], zb[j], A[d], B[d]) for d in range(3)]
+            zp = za[i] + zb[j]
+            K = math.exp(-za[i] * zb[j] / zp * np.sum((A - B) ** 2)) * ca[i] * cb[j]
+            Ecart = np.zeros((len(comps_a), len(comps_b), np_))
+            for ia, a in enumerate(comps_a):
+                for ib, b in enumerate(comps_b):
+                    for ip, p in enumerate(herm):
+                        Ecart[ia, ib, ip] = E[0][a[0], b[0], p[0]] * E[1][a[1], b[1], p[1]] * E[2][a[2], b[2], p[2]]
+            if solid:
+                Ecart = np.einsum("ma,nb,abp->mnp", oracle.solid_coefs(la), oracle.solid_coefs(lb), Ecart)
+            if ket_sign:
+                Ecart = Ecart * np.array([(-1) ** sum(p) for p in herm])
+            blocks.append(K * Ecart.reshape(-1, np_))
+    return np.concatenate(blocks, axis=1)
+
+
+@pytest.mark.parametrize("solid", [False, True])
+@pytest.mark.parametrize("ket_sign", [False, True])
+def test_hermite_H_stage_matches_oracle(solid, ket_sign):
+    pairs_l = [(0, 0), (1, 0), (2, 3), (4, 4), (6, 6), (5, 4), (4, 6), (6, 0)]
+    ls = [x for pr in pairs_l for x in pr]
+    rng = np.random.default_rng(4)
+    K = rng.integers(1, 4, len(ls)).astype(np.int32)
+    off = np.concatenate([[0], np.cumsum(K)[:-1]]).astype(np.int32)
+    basis = {"l": np.asarray(ls, np.int32), "nprim": K, "prim_off": off, "center": rng.uniform(0, 3, (len(ls), 3)),
+             "exps": np.exp(rng.uniform(np.log(0.05), np.log(50), K.sum())), "coefs": 1 - rng.uniform(0, 1, K.sum())}
+    pairs = [(2 * i, 2 * i + 1) for i in range(len(pairs_l))]
+    H, stride = lx.hermite_H(basis, pairs, solid, ket_sign)
+    H = H.cpu().numpy()
+    for k, (sa, sb) in enumerate(pairs):
+        ref = oracle_H(basis, sa, sb, solid, ket_sign)
+        got = H[k, :ref.size].reshape(ref.shape)
+        scale = np.abs(ref).max()
+        assert np.abs(got - ref).max() <= 1e-13 * scale, f"pair {pairs_l[k]}"
+
+
+# ---------------------------------------------------------------- whole batches
+
+@pytest.mark.parametrize("solid", [False, True])
+def test_gggg_64_quartets(solid):
+    # (gg|gg), 64 quartets, K = 1, 10-bohr cube: every element
+    basis, quartets = inputs.gggg_fp64()
+    run_and_check(basis, quartets, solid)
+
+
+@pytest.mark.parametrize("cls", [(0, 0, 0, 0), (1, 0, 0, 1), (2, 2, 1, 0), (3, 1, 2, 3), (2, 2, 2, 2), (0, 6, 1, 5)])
+def test_low_and_odd_classes_contracted(cls):
+    basis, quartets = inputs.uniform_class(cls, 9, sum(cls) + 100, cube=4.0, exps=(0.05, 50.0), kmin=1, kmax=3)
+    for solid in (False, True):
+        run_and_check(basis, quartets, solid)
+
+
+def test_mixed_classes_contracted():
+    # the five mixed classes, K per shell 1..2, one batch; a 4-bohr cube keeps every class's
+    # largest integral at a realistic size (the tolerance is relative to it)
+    mixed = inputs.mixed_classes(12, seed=11, kmin=1, kmax=2, cube=4.0)
+    # one compact quartet per class, as any realistic batch has (the class scale)
+    anchors = [inputs.uniform_class(c, 1, 50 + i, cube=1.0, exps=(0.1, 5.0), kmin=1, kmax=2)
+               for i, c in enumerate(inputs.MIXED_CLASSES)]
+    basis, quartets = inputs.concat([mixed] + anchors)
+    for solid in (True, False):
+        run_and_check(basis, quartets, solid)
+
+
+def test_iiii_k1_both_outputs():
+    basis, quartets = inputs.uniform_class((6, 6, 6, 6), 5, 2308, cube=4.0, exps=(0.05, 20.0))
+    run_and_check(basis, quartets, True)
+    run_and_check(basis, quartets, False)
+
+
+def test_shared_pairs_and_custom_offsets():
+    # bra-list x ket-list: 3 pairs, all 9 quartets, output blocks with gaps and reversed order
+    rng = np.random.default_rng(9)
+    ls = [4, 5, 2, 3, 6, 4]
+    K = np.array([2, 1, 3, 1, 1, 2], np.int32)
+    off = np.concatenate([[0], np.cumsum(K)[:-1]]).astype(np.int32)
+    basis = {"l": np.asarray(ls, np.int32), "nprim": K, "prim_off": off, "center": rng.uniform(0, 3, (6, 3)),
+             "exps": np.exp(rng.uniform(np.log(0.1), np.log(20), K.sum())), "coefs": 1 - rng.uniform(0, 1, K.sum())}
+    pairs = [(0, 1), (2, 3), (4, 5)]
+    quartets = np.array([[a, b, c, d] for (a, b) in pairs for (c, d) in pairs], np.int32)
+    solid = True
+    sizes = [np.prod([2 * ls[s] + 1 for s in q]) for q in quartets]
+    offs = np.zeros(len(quartets), np.int64)
+    pos = 7
+    for i in reversed(range(len(quartets))):
+        offs[i] = pos
+        pos += int(sizes[i]) + 13
+    b = lx.Batch(basis, quartets, solid, out_off=offs)
+    out = torch.full((b.out_size,), 12345.0, dtype=torch.float64, device="cuda")
+    ws = lx.alloc_workspace(b.workspace_size())
+    b.run(out, ws)
+    lx.sync_status()
+    got = out.cpu().numpy()
+    ref, _ = oracle.eri(basis, quartets, solid=solid, out_off=offs)
+    mask = np.zeros(b.out_size, bool)
+    for o, n in zip(offs, sizes):
+        mask[o:o + n] = True
+    assert np.all(got[~mask] == 12345.0), "wrote outside the quartet blocks"
+    assert_eri_close(basis, quartets, got, ref[:b.out_size], offs, solid)
+
+
+def test_chunked_workspace_is_bitwise_identical():
+    basis, quartets = inputs.mixed_classes(10, seed=5, kmin=1, kmax=2)
+    b = lx.Batch(basis, quartets, True)
+    full = torch.zeros(b.out_size, dtype=torch.float64, device="cuda")
+    small = torch.zeros_like(full)
+    b.run(full, lx.alloc_workspace(b.workspace_size()))
+    b.run(small, lx.alloc_workspace(b.workspace_min()))
+    lx.sync_status()
+    assert torch.equal(full, small)
+
+
+def test_far_separated_quartets_within_fp64_conditioning():
+    # Quartets whose integrals are tiny (separated pairs) are sums with heavy cancellation:
+    # FP64 itself resolves them only to the digits that survive it.  Per quartet, the GPU must
+    # agree with the oracle within 1e-11 of the quartet's own largest integral plus 20 times
+    # the oracle's own rounding noise, measured by translating the quartet rigidly.
+    basis, quartets = inputs.spread_distances(10, seed=3, kmin=1, kmax=2)
+    out, off = lx.eri(basis, quartets, solid=True)
+    got = out.cpu().numpy()
+    ref, _ = oracle.eri(basis, quartets, solid=True)
+    moved = dict(basis)
+    moved["center"] = basis["center"] + np.array([0.37, -1.1, 0.53])
+    ref2, _ = oracle.eri(moved, quartets, solid=True)
+    l = basis["l"]
+    for i, q in enumerate(quartets):
+        n = int(np.prod([2 * l[s] + 1 for s in q]))
+        sl = slice(off[i], off[i] + n)
+        noise = np.abs(ref[sl] - ref2[sl]).max()
+        assert np.abs(got[sl] - ref[sl]).max() <= 1e-11 * np.abs(ref[sl]).max() + 20 * noise + 1e-300
+
+
+def test_empty_batch():
+    basis, quartets = inputs.gggg_fp64()
+    out, off = lx.eri(basis, np.zeros((0, 4), np.int32), solid=True)
+    assert out.numel() == 0 and len(off) == 0
+
+
+def test_identical_centers_and_tight_exponents():
+    # degenerate geometry: all four shells on one center (T = 0, P = A), and extreme exponents
+    ls = [6, 6, 5, 4]
+    basis = {"l": np.asarray(ls, np.int32), "nprim": np.array([1, 2, 1, 1], np.int32),
+             "prim_off": np.array([0, 1, 3, 4], np.int32), "center": np.zeros((4, 3)),
+             "exps": np.array([50.0, 0.05, 3.0, 0.05, 20.0]), "coefs": np.array([1.0, 0.3, 0.7, 1.0, 1.0])}
+    run_and_check(basis, [[0, 1, 2, 3], [3, 2, 1, 0]], True)
+
+
+def test_full_size_iiii_sampled():
+    # (ii|ii), 4096 quartets, one launch sequence as timed by the benchmark; sampled quartets
+    # against the oracle, plus finiteness of every output
+    basis, quartets = inputs.iiii_fp64()
+    b = lx.Batch(basis, quartets, True)
+    out = torch.empty(b.out_size, dtype=torch.float64, device="cuda")
+    b.run(out, lx.alloc_workspace(b.workspace_size()))
+    lx.sync_status()
+    assert bool(torch.isfinite(out).all())
+    sample = [0, 1, 1777, 4095]
+    sb, sq = inputs.subset(basis, quartets, sample)
+    ref, roff = oracle.eri(sb, sq, solid=True)
+    n = 13 ** 4
+    got = np.concatenate([out[i * n:(i + 1) * n].cpu().numpy() for i in sample])
+    # tolerance against the class scale of the whole batch
+    scale = float(out.abs().max())
+    assert np.abs(got - ref).max() <= TOL_ERI * scale
