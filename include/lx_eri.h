@@ -85,6 +85,8 @@ typedef struct {
 #define LX_ERR_ARCH (-8)          /* current device is not compute capability 10.3 */
 #define LX_ERR_DEVICE_STATUS (-9) /* a kernel reported a bad index or an exhausted wait */
 #define LX_ERR_SIZE (-10)         /* a size argument is negative or too large */
+#define LX_ERR_STATIC_SCRATCH (-11) /* lx_eri_batch_static: the batch needs more scratch than
+                                       LX_STATIC_SCRATCH_BYTES even one quartet at a time */
 
 /*
  * Number of doubles the output buffer needs: max over quartets of out_offset + block size.
@@ -120,6 +122,29 @@ int64_t lx_eri_workspace_min(const lx_shell* shells, int32_t nshell, const lx_qu
 int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
                  int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags, double* out,
                  void* workspace, size_t workspace_bytes, void* cuda_stream);
+
+/*
+ * lx_eri_batch without a workspace argument, for callers that cannot allocate device memory
+ * (for example a plugin whose host program owns every device allocation through its own
+ * pool, or a process in which cudaMalloc is not permitted).  There is no counterpart in the
+ * paper; it exists only for such callers.
+ *   Same inputs, output and stream semantics as lx_eri_batch.  The scratch is a fixed array
+ *   of LX_STATIC_SCRATCH_BYTES inside the library's device image: every GPU that loads the
+ *   library holds it until the process exits.  The call allocates no device memory.
+ *   The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *   with that device current); make that first call before any stream capture.
+ *   A batch whose smallest workspace (lx_eri_workspace_min) exceeds LX_STATIC_SCRATCH_BYTES
+ *   is rejected with LX_ERR_STATIC_SCRATCH; larger batches that fit one quartet at a time are
+ *   processed in chunks.
+ *   All calls on a device share the one array: calls that overlap on the GPU (for example on
+ *   two streams at once) race and give wrong results; serialise them on one stream.  The
+ *   array keeps the last call's contents; the pipeline never reads scratch it has not
+ *   written in the same call.
+ */
+#define LX_STATIC_SCRATCH_BYTES (64ull << 20)
+int lx_eri_batch_static(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
+                        int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags,
+                        double* out, void* cuda_stream);
 
 /*
  * Wait for cuda_stream, then read and clear the device status word of the current device.

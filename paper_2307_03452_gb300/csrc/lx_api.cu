@@ -523,6 +523,7 @@ const char* lx_strerror(int code) {
         case LX_ERR_ARCH: return "current device is not compute capability 10.3 (GB300)";
         case LX_ERR_DEVICE_STATUS: return "a kernel reported a bad index or input";
         case LX_ERR_SIZE: return "a size argument is negative or too large";
+        case LX_ERR_STATIC_SCRATCH: return "batch needs more scratch than the static array of lx_eri_batch_static holds";
         default: return "unknown error code";
     }
 }

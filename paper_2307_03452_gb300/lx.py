@@ -30,6 +30,7 @@ _lib = None
 
 #: every symbol the header declares
 EXPORTS = sorted(["lx_eri_out_size", "lx_eri_workspace_size", "lx_eri_workspace_min", "lx_eri_batch",
+                  "lx_eri_batch_static",
                   "lx_eri_sync_status", "lx_eri_stage_times", "lx_strerror", "lx_last_cuda_error", "lx_boys",
                   "lx_hermite_R", "lx_hermite_H"])
 LX_TIME_STAGES = 0x200
@@ -71,6 +72,8 @@ def load(build_if_missing: bool = True):
         lib.lx_eri_workspace_min.restype = c_i64
         lib.lx_eri_batch.argtypes = [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_i64, c_i32, c_vp, c_vp, c_sz, c_vp]
         lib.lx_eri_batch.restype = ctypes.c_int
+        lib.lx_eri_batch_static.argtypes = [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_i64, c_i32, c_vp, c_vp]
+        lib.lx_eri_batch_static.restype = ctypes.c_int
         lib.lx_eri_sync_status.argtypes = [c_vp]
         lib.lx_eri_sync_status.restype = ctypes.c_int
         lib.lx_eri_stage_times.argtypes = [c_vp, c_vp, c_i32, c_vp]
@@ -209,6 +212,19 @@ def stage_times(stream=None) -> tuple[dict, dict]:
     _check(load().lx_eri_stage_times(_ptr(ms), _ptr(n), len(STAGES), ctypes.c_void_p(_stream_ptr(stream))),
            "lx_eri_stage_times")
     return dict(zip(STAGES, ms.tolist())), dict(zip(STAGES, n.tolist()))
+
+
+STATIC_SCRATCH_BYTES = 64 << 20
+
+
+def run_static(batch: "Batch", out, stream=None):
+    """lx_eri_batch_static: the same evaluation with the library's fixed device scratch
+    array instead of a caller workspace (for callers that cannot allocate device memory)."""
+    b = batch
+    rc = load().lx_eri_batch_static(_ptr(b.shells), len(b.shells), _ptr(b.exps), _ptr(b.coefs), len(b.exps),
+                                    _ptr(b.quartets), len(b.quartets), b.flags, ctypes.c_void_p(out.data_ptr()),
+                                    ctypes.c_void_p(_stream_ptr(stream)))
+    _check(rc, "lx_eri_batch_static")
 
 
 def sync_status(stream=None):

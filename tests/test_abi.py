@@ -30,7 +30,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_error_strings():
     lib = lx.load()
-    for code in [0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10]:
+    for code in [0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10, -11]:
         s = lib.lx_strerror(code).decode()
         assert s and s != "unknown error code"
     assert lib.lx_strerror(12345).decode() == "unknown error code"
