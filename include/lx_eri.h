@@ -62,6 +62,10 @@ typedef struct {
 #define LX_CART 0x0        /* Cartesian output, ncart(l) = (l+1)(l+2)/2 per shell */
 #define LX_SOLID 0x1       /* real solid-harmonic output, 2l+1 per shell */
 #define LX_PATH_FP64 0x0   /* every step in FP64 */
+#define LX_PATH_SPLIT 0x2  /* the two Hermite transforms as Ozaki-style BF16 slice products on the
+                              tensor cores (FP32 accumulation, exact integer recombination);
+                              Boys, [r]^(m), E and H stay FP64.  Error ~5e-11 of each quartet's
+                              largest integral */
 #define LX_TIME_STAGES 0x200 /* record CUDA events around each stage (see lx_eri_stage_times) */
 
 /* stages timed with LX_TIME_STAGES */
@@ -70,7 +74,8 @@ typedef struct {
 #define LX_STAGE_BOYS_R 2 /* Boys function and [r]^(0) */
 #define LX_STAGE_GEMM1 3  /* [ab|q] = H_ab [p|q] */
 #define LX_STAGE_GEMM2 4  /* (ab|cd) = [ab|q] H_cd^T */
-#define LX_NSTAGE 5
+#define LX_STAGE_SPLIT 5  /* LX_PATH_SPLIT: FP64 operands -> BF16 digit planes */
+#define LX_NSTAGE 6
 
 /* error codes (0 = success) */
 #define LX_OK 0
@@ -201,6 +206,17 @@ int lx_hermite_R(int32_t L, const double* params, int64_t n, double* R, void* cu
 int lx_hermite_H(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
                  int32_t nprim_total, const int32_t* pairs, int32_t npair, int32_t flags, double* H,
                  int64_t stride, void* cuda_stream);
+
+/*
+ * C = A B^T through the split path's kernels (the same splitting and tensor-core GEMM that
+ * LX_PATH_SPLIT uses for Eq. make-abq / Eq. make-abcd): A is M x K, B is N x K, both FP64
+ * row-major in DEVICE memory with row strides lda, ldb; C is M x N FP64 row-major, stride ldc.
+ * Each row of A and of B is scaled by its own power of two and split into 5 BF16 digits of
+ * 8 bits; the 15 digit products with s + t <= 4 are summed exactly.  Scratch for the digit
+ * planes is taken from the stream-ordered allocator.  M, N, K >= 1, K <= 1 << 20.
+ */
+int lx_split_gemm(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda, const double* B, int32_t ldb,
+                  double* C, int32_t ldc, void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "lx_internal.cuh"
+#include "lx_split.cuh"
 
 namespace lx {
 namespace {
@@ -89,8 +90,11 @@ int ensure_device(unsigned** status) {
         std::vector<int> tuv(NHERM_TOT);
         make_tuv_table(tuv.data());
         if ((e = init_boys_table(boys.data())) != cudaSuccess) return cuda_fail(e);
-        if ((e = init_prep_tables(solid.data(), tuv.data())) != cudaSuccess) return cuda_fail(e);
+        std::vector<SolidClassTab> cls(LMAX + 1);
+        make_solid_classes(solid.data(), cls.data());
+        if ((e = init_prep_tables(solid.data(), tuv.data(), cls.data())) != cudaSuccess) return cuda_fail(e);
         if ((e = init_tuv_table(tuv.data())) != cudaSuccess) return cuda_fail(e);
+        if ((e = init_split_kernels(tuv.data())) != cudaSuccess) return cuda_fail(e);
         void* p = nullptr;
         if ((e = cudaGetSymbolAddress(&p, g_status_word)) != cudaSuccess) return cuda_fail(e);
         const unsigned zero = 0;
@@ -113,7 +117,7 @@ int validate(const lx_shell* shells, int32_t nshell, const double* exps, const d
     if (nshell < 0 || nquartet < 0 || nprim_total < 0) return LX_ERR_SIZE;
     if ((nshell > 0 && !shells) || (nquartet > 0 && !quartets)) return LX_ERR_NULL;
     if (need_prims && nprim_total > 0 && (!exps || !coefs)) return LX_ERR_NULL;
-    if (flags & ~(LX_SOLID | LX_TIME_STAGES)) return LX_ERR_FLAGS;
+    if (flags & ~(LX_SOLID | LX_PATH_SPLIT | LX_TIME_STAGES)) return LX_ERR_FLAGS;
     for (int32_t s = 0; s < nshell; ++s) {
         const lx_shell& d = shells[s];
         if (d.l < 0 || d.l > LX_LMAX || d.nprim < 1 || d.nprim > LX_KMAX || d.reserved != 0) return LX_ERR_SHELL;
@@ -149,24 +153,43 @@ struct Chunk {
     int64_t q_begin = 0, q_end = 0;
 };
 
-// Workspace bytes of one quartet's own data (without its pairs).
-size_t quartet_bytes(const lx_shell* sh, const lx_quartet& q, bool solid) {
+// Workspace bytes of one quartet's own data (without its pairs), for path flags `flags`.
+size_t quartet_bytes(const lx_shell* sh, const lx_quartet& q, int flags) {
+    const bool solid = flags & LX_SOLID, split = flags & LX_PATH_SPLIT;
     const lx_shell &a = sh[q.s[0]], &b = sh[q.s[1]], &c = sh[q.s[2]], &d = sh[q.s[3]];
-    const int L = a.l + b.l + c.l + d.l, nq = pyr(c.l + d.l);
+    const int L = a.l + b.l + c.l + d.l, np = pyr(a.l + b.l), nq = pyr(c.l + d.l);
     const int64_t kbra = (int64_t)a.nprim * b.nprim, kket = (int64_t)c.nprim * d.nprim;
     const int64_t nab = (int64_t)nfun(a.l, solid) * nfun(b.l, solid), ncd = (int64_t)nfun(c.l, solid) * nfun(d.l, solid);
     const int64_t n1 = kket * nq;
     int64_t items = (kbra * kket + 3) / 4;
-    items += ((nab + GEMM_BM - 1) / GEMM_BM) * ((n1 + GEMM_BN - 1) / GEMM_BN);
-    items += ((nab + GEMM_BM - 1) / GEMM_BM) * ((ncd + GEMM_BN - 1) / GEMM_BN);
-    // + 2 x 256 bytes: each of the two data blocks starts on a 256-byte boundary
-    return sizeof(DQuartet) + items * sizeof(WorkItem) + 8 * (size_t)(kbra * kket * pyr(L) + nab * n1) + 512;
+    // + 256 bytes per data block: each block starts on a 256-byte boundary
+    size_t bytes = sizeof(DQuartet) + 8 * (size_t)(kbra * kket * pyr(L) + nab * n1) + 512;
+    if (!split) {
+        items += ((nab + GEMM_BM - 1) / GEMM_BM) * ((n1 + GEMM_BN - 1) / GEMM_BN);
+        items += ((nab + GEMM_BM - 1) / GEMM_BM) * ((ncd + GEMM_BN - 1) / GEMM_BN);
+    } else {
+        const int k1 = (int)(kbra * np), k2 = (int)n1;
+        const int ra1 = split_rowpad(k2, SPLIT_TA), rb1 = split_rowpad((int)nab, SPLIT_TB);
+        const int ra2 = split_rowpad((int)nab, SPLIT_TA), rb2 = split_rowpad((int)ncd, SPLIT_TB);
+        const int c1 = (k1 + 127) / 128, c2 = (k2 + 127) / 128;
+        items += ra1 + rb1 + ra2 + rb2 + 3 * c1 + 3 * c2;
+        items += (ra1 / SPLIT_TA) * ((nab + SPLIT_TB - 1) / SPLIT_TB);
+        items += (ra2 / SPLIT_TA) * ((ncd + SPLIT_TB - 1) / SPLIT_TB);
+        bytes += sizeof(SplitQuartet) + 2 * sizeof(SplitGemmDesc) + 3 * sizeof(SplitRowsDesc) +
+                 3 * sizeof(ColMaxDesc) + 2 * sizeof(BalanceDesc);
+        bytes += (size_t)split_dig_bytes(k2, k1, SPLIT_TA) + (size_t)split_dig_bytes((int)nab, k1, SPLIT_TB);
+        bytes += (size_t)split_dig_bytes((int)nab, k2, SPLIT_TA) + (size_t)split_dig_bytes((int)ncd, k2, SPLIT_TB);
+        bytes += 4 * (size_t)(ra1 + rb1 + ra2 + rb2) + 4 * (size_t)(3 * k1 + 3 * k2) + 14 * 256;
+    }
+    return bytes + items * sizeof(WorkItem);
 }
 
-size_t pair_bytes(const lx_shell* sh, int sa, int sb, bool solid) {
+size_t pair_bytes(const lx_shell* sh, int sa, int sb, int flags) {
+    const bool solid = flags & LX_SOLID, split = flags & LX_PATH_SPLIT;
     const lx_shell &a = sh[sa], &b = sh[sb];
     const int64_t kab = (int64_t)a.nprim * b.nprim;
     const int64_t rows = (int64_t)nfun(a.l, solid) * nfun(b.l, solid);
+    (void)split;  // the split path keeps its digit planes per quartet (the balancing depends on it)
     return sizeof(DPair) + kab * sizeof(WorkItem) + 8 * (size_t)(kab * 4 + rows * kab * pyr(a.l + b.l)) + 512;
 }
 
@@ -177,7 +200,7 @@ size_t head_bytes(int nshell, int nprim) {
 }
 
 // Greedy chunking of the quartet list so that each chunk fits `budget` bytes.
-int plan_chunks(const lx_shell* sh, const lx_quartet* qs, int64_t nq, bool solid, size_t budget,
+int plan_chunks(const lx_shell* sh, const lx_quartet* qs, int64_t nq, int flags, size_t budget,
                 std::vector<Chunk>& chunks) {
     chunks.clear();
     std::unordered_map<PairKey, int, PairKeyHash> seen;
@@ -186,12 +209,12 @@ int plan_chunks(const lx_shell* sh, const lx_quartet* qs, int64_t nq, bool solid
     cur.q_begin = 0;
     for (int64_t i = 0; i < nq; ++i) {
         const lx_quartet& q = qs[i];
-        size_t add = quartet_bytes(sh, q, solid);
+        size_t add = quartet_bytes(sh, q, flags);
         const PairKey kb{((int64_t)q.s[0] << 32 | (uint32_t)q.s[1]) * 2};
         const PairKey kk{((int64_t)q.s[2] << 32 | (uint32_t)q.s[3]) * 2 + 1};
         const bool nb = !seen.count(kb), nk = !seen.count(kk);
-        if (nb) add += pair_bytes(sh, q.s[0], q.s[1], solid);
-        if (nk && !(kk == kb)) add += pair_bytes(sh, q.s[2], q.s[3], solid);
+        if (nb) add += pair_bytes(sh, q.s[0], q.s[1], flags);
+        if (nk && !(kk == kb)) add += pair_bytes(sh, q.s[2], q.s[3], flags);
         if (used + add > budget) {
             if (i == cur.q_begin) return LX_ERR_WORKSPACE;  // one quartet does not fit
             cur.q_end = i;
@@ -217,18 +240,40 @@ struct ChunkPlan {
     std::vector<DQuartet> quartets;
     std::vector<WorkItem> items_h, items_br, items_g1, items_g2;
     size_t off_pairs = 0, off_quartets = 0, off_h = 0, off_br = 0, off_g1 = 0, off_g2 = 0, off_data = 0;
+    // split path (per quartet: 3 split-row descs B1, A2, B2; 3 column-max descs cmh1, cmh2, cmx;
+    // 2 balance descs e1, e2)
+    std::vector<SplitRowsDesc> srd;
+    std::vector<ColMaxDesc> cmd;
+    std::vector<BalanceDesc> bal;
+    std::vector<SplitQuartet> sq;
+    std::vector<SplitGemmDesc> sg1, sg2;
+    std::vector<WorkItem> items_cA, items_rm, items_b1, items_sr, items_sB, items_sg1, items_cC, items_b2, items_sD,
+        items_sg2;
+    size_t off_srd = 0, off_cmd = 0, off_bal = 0, off_sq = 0, off_sg1 = 0, off_sg2 = 0;
+    size_t off_icA = 0, off_irm = 0, off_ib1 = 0, off_isr = 0, off_isB = 0, off_isg1 = 0, off_icC = 0, off_ib2 = 0,
+           off_isD = 0, off_isg2 = 0;
     size_t total = 0;         // bytes from the chunk base
     std::vector<char> blob;   // descriptor bytes [0, off_data)
 };
 
-void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, bool solid, size_t chunk_base,
+void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int flags, size_t chunk_base,
                  ChunkPlan& P) {
+    const bool solid = flags & LX_SOLID, split = flags & LX_PATH_SPLIT;
     P.pairs.clear();
     P.quartets.clear();
     P.items_h.clear();
     P.items_br.clear();
     P.items_g1.clear();
     P.items_g2.clear();
+    P.srd.clear();
+    P.cmd.clear();
+    P.bal.clear();
+    P.sq.clear();
+    P.sg1.clear();
+    P.sg2.clear();
+    for (auto* v : {&P.items_cA, &P.items_rm, &P.items_b1, &P.items_sr, &P.items_sB, &P.items_sg1, &P.items_cC,
+                    &P.items_b2, &P.items_sD, &P.items_sg2})
+        v->clear();
     std::unordered_map<PairKey, int, PairKeyHash> pid;
     auto get_pair = [&](int sa, int sb, int side) {
         const PairKey k{((int64_t)sa << 32 | (uint32_t)sb) * 2 + side};
@@ -270,6 +315,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, bool
     for (int i = 0; i < (int)P.quartets.size(); ++i) {
         const DQuartet& d = P.quartets[i];
         for (int k = 0; k < d.kbra * d.kket; k += 4) P.items_br.push_back({i, k, 0, 0});
+        if (split) continue;
         const int mt = (d.nab + GEMM_BM - 1) / GEMM_BM;
         const int nt1 = (d.kket * d.nq + GEMM_BN - 1) / GEMM_BN, nt2 = (d.ncd + GEMM_BN - 1) / GEMM_BN;
         for (int m = 0; m < mt; ++m)
@@ -277,63 +323,206 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, bool
         for (int m = 0; m < mt; ++m)
             for (int n = 0; n < nt2; ++n) P.items_g2.push_back({i, m, n, 0});
     }
+    if (split) {
+        // split descriptors and work lists (offsets filled in below, with the data layout)
+        for (int i = 0; i < (int)P.quartets.size(); ++i) {
+            const DQuartet& d = P.quartets[i];
+            const int k1 = d.kbra * d.np, k2 = d.kket * d.nq;
+            const int c1 = (k1 + 127) / 128, c2 = (k2 + 127) / 128;
+            SplitQuartet q{};
+            q.nkb1 = split_nkb(k1);
+            q.nkb2 = split_nkb(k2);
+            P.sq.push_back(q);
+            const int sb1 = (int)P.srd.size();
+            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k1, d.nab, k1, SPLIT_TB, q.nkb1, +1});   // B1: H_bra
+            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k2, d.nab, k2, SPLIT_TA, q.nkb2, +1});   // A2: X
+            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k2, d.ncd, k2, SPLIT_TB, q.nkb2, -1});   // B2: H_ket
+            const int c0 = (int)P.cmd.size();
+            P.cmd.push_back(ColMaxDesc{0, 0, k1, d.nab, k1, 0});  // cmh1
+            P.cmd.push_back(ColMaxDesc{0, 0, k2, d.ncd, k2, 0});  // cmh2
+            P.cmd.push_back(ColMaxDesc{0, 0, k2, d.nab, k2, 0});  // cmx
+            const int b0 = (int)P.bal.size();
+            P.bal.push_back(BalanceDesc{0, 0, 0, k1, 0});  // e1 = (rmr - cmh1) / 2
+            P.bal.push_back(BalanceDesc{0, 0, 0, k2, 0});  // e2 = (cmh2 - cmx) / 2
+            for (int c = 0; c < c1; ++c) {
+                P.items_cA.push_back({c0, c, 0, 0});
+                P.items_rm.push_back({i, c, 0, 0});
+                P.items_b1.push_back({b0, c, 0, 0});
+            }
+            for (int c = 0; c < c2; ++c) {
+                P.items_cA.push_back({c0 + 1, c, 0, 0});
+                P.items_cC.push_back({c0 + 2, c, 0, 0});
+                P.items_b2.push_back({b0 + 1, c, 0, 0});
+            }
+            for (int row = 0; row < split_rowpad(k2, SPLIT_TA); ++row) P.items_sr.push_back({i, row, 0, 0});
+            for (int row = 0; row < split_rowpad(d.nab, SPLIT_TB); ++row) P.items_sB.push_back({sb1, row, 0, 0});
+            for (int row = 0; row < split_rowpad(d.nab, SPLIT_TA); ++row) P.items_sD.push_back({sb1 + 1, row, 0, 0});
+            for (int row = 0; row < split_rowpad(d.ncd, SPLIT_TB); ++row) P.items_sD.push_back({sb1 + 2, row, 0, 0});
+            const int mt1 = split_rowpad(k2, SPLIT_TA) / SPLIT_TA, nt1 = (d.nab + SPLIT_TB - 1) / SPLIT_TB;
+            const int mt2 = split_rowpad(d.nab, SPLIT_TA) / SPLIT_TA, nt2 = (d.ncd + SPLIT_TB - 1) / SPLIT_TB;
+            for (int m = 0; m < mt1; ++m)
+                for (int n = 0; n < nt1; ++n) P.items_sg1.push_back({i, m, n, 0});
+            for (int m = 0; m < mt2; ++m)
+                for (int n = 0; n < nt2; ++n) P.items_sg2.push_back({i, m, n, 0});
+        }
+    }
     // byte layout from the chunk base
     size_t o = 0;
-    P.off_pairs = o;
-    o = align256(o + sizeof(DPair) * P.pairs.size());
-    P.off_quartets = o;
-    o = align256(o + sizeof(DQuartet) * P.quartets.size());
-    P.off_h = o;
-    o = align256(o + sizeof(WorkItem) * P.items_h.size());
-    P.off_br = o;
-    o = align256(o + sizeof(WorkItem) * P.items_br.size());
-    P.off_g1 = o;
-    o = align256(o + sizeof(WorkItem) * P.items_g1.size());
-    P.off_g2 = o;
-    o = align256(o + sizeof(WorkItem) * P.items_g2.size());
+    auto region = [&](size_t& off, size_t bytes) {
+        off = o;
+        o = align256(o + bytes);
+    };
+    region(P.off_pairs, sizeof(DPair) * P.pairs.size());
+    region(P.off_quartets, sizeof(DQuartet) * P.quartets.size());
+    region(P.off_h, sizeof(WorkItem) * P.items_h.size());
+    region(P.off_br, sizeof(WorkItem) * P.items_br.size());
+    region(P.off_g1, sizeof(WorkItem) * P.items_g1.size());
+    region(P.off_g2, sizeof(WorkItem) * P.items_g2.size());
+    region(P.off_srd, sizeof(SplitRowsDesc) * P.srd.size());
+    region(P.off_cmd, sizeof(ColMaxDesc) * P.cmd.size());
+    region(P.off_bal, sizeof(BalanceDesc) * P.bal.size());
+    region(P.off_sq, sizeof(SplitQuartet) * P.sq.size());
+    region(P.off_sg1, sizeof(SplitGemmDesc) * P.sq.size());
+    region(P.off_sg2, sizeof(SplitGemmDesc) * P.sq.size());
+    region(P.off_icA, sizeof(WorkItem) * P.items_cA.size());
+    region(P.off_irm, sizeof(WorkItem) * P.items_rm.size());
+    region(P.off_ib1, sizeof(WorkItem) * P.items_b1.size());
+    region(P.off_isr, sizeof(WorkItem) * P.items_sr.size());
+    region(P.off_isB, sizeof(WorkItem) * P.items_sB.size());
+    region(P.off_isg1, sizeof(WorkItem) * P.items_sg1.size());
+    region(P.off_icC, sizeof(WorkItem) * P.items_cC.size());
+    region(P.off_ib2, sizeof(WorkItem) * P.items_b2.size());
+    region(P.off_isD, sizeof(WorkItem) * P.items_sD.size());
+    region(P.off_isg2, sizeof(WorkItem) * P.items_sg2.size());
     P.off_data = o;
-    // data regions, offsets in doubles from the workspace base
+    // data regions: FP64 blocks in doubles from the workspace base, digit planes in bytes
     int64_t dw = (int64_t)((chunk_base + o) / 8);
-    for (auto& p : P.pairs) {
-        p.info_off = dw;
-        dw += 4 * (int64_t)p.Kab;
+    auto take = [&](int64_t ndoubles) {
+        const int64_t at = dw;
+        dw += ndoubles;
         dw = (dw + 31) & ~int64_t(31);
-    }
-    for (auto& p : P.pairs) {
-        p.h_off = dw;
-        dw += (int64_t)p.nrow * p.Kab * p.np;
-        dw = (dw + 31) & ~int64_t(31);
-    }
+        return at;
+    };
+    for (auto& p : P.pairs) p.info_off = take(4 * (int64_t)p.Kab);
+    for (auto& p : P.pairs) p.h_off = take((int64_t)p.nrow * p.Kab * p.np);
     for (auto& d : P.quartets) {
-        d.rr_off = dw;
-        dw += (int64_t)d.kbra * d.kket * d.nr;
-        dw = (dw + 31) & ~int64_t(31);
-        d.x_off = dw;
-        dw += (int64_t)d.nab * d.kket * d.nq;
-        dw = (dw + 31) & ~int64_t(31);
+        d.rr_off = take((int64_t)d.kbra * d.kket * d.nr);
+        d.x_off = take((int64_t)d.nab * d.kket * d.nq);
+    }
+    if (split) {
+        auto take_bytes = [&](int64_t bytes) { return 8 * take((bytes + 7) / 8); };
+        for (size_t i = 0; i < P.quartets.size(); ++i) {
+            const DQuartet& d = P.quartets[i];
+            SplitQuartet& q = P.sq[i];
+            const int k1 = d.kbra * d.np, k2 = d.kket * d.nq;
+            q.a1_dig = take_bytes(split_dig_bytes(k2, k1, SPLIT_TA));
+            q.a1_exp = take_bytes(4 * (int64_t)split_rowpad(k2, SPLIT_TA));
+            q.b1_dig = take_bytes(split_dig_bytes(d.nab, k1, SPLIT_TB));
+            q.b1_exp = take_bytes(4 * (int64_t)split_rowpad(d.nab, SPLIT_TB));
+            q.a2_dig = take_bytes(split_dig_bytes(d.nab, k2, SPLIT_TA));
+            q.a2_exp = take_bytes(4 * (int64_t)split_rowpad(d.nab, SPLIT_TA));
+            q.b2_dig = take_bytes(split_dig_bytes(d.ncd, k2, SPLIT_TB));
+            q.b2_exp = take_bytes(4 * (int64_t)split_rowpad(d.ncd, SPLIT_TB));
+            q.rmr_off = take_bytes(4 * (int64_t)k1);
+            q.e1_off = take_bytes(4 * (int64_t)k1);
+            q.e2_off = take_bytes(4 * (int64_t)k2);
+            const int64_t cmh1 = take_bytes(4 * (int64_t)k1), cmh2 = take_bytes(4 * (int64_t)k2),
+                          cmx = take_bytes(4 * (int64_t)k2);
+            const DPair &pb = P.pairs[d.pb], &pk = P.pairs[d.pk];
+            SplitRowsDesc* r = &P.srd[3 * i];
+            r[0].src_off = pb.h_off;
+            r[0].dig_off = q.b1_dig;
+            r[0].exp_off = q.b1_exp;
+            r[0].shift_off = q.e1_off;
+            r[1].src_off = d.x_off;
+            r[1].dig_off = q.a2_dig;
+            r[1].exp_off = q.a2_exp;
+            r[1].shift_off = q.e2_off;
+            r[2].src_off = pk.h_off;
+            r[2].dig_off = q.b2_dig;
+            r[2].exp_off = q.b2_exp;
+            r[2].shift_off = q.e2_off;
+            ColMaxDesc* c = &P.cmd[3 * i];
+            c[0].src_off = pb.h_off;
+            c[0].out_off = cmh1;
+            c[1].src_off = pk.h_off;
+            c[1].out_off = cmh2;
+            c[2].src_off = d.x_off;
+            c[2].out_off = cmx;
+            BalanceDesc* b = &P.bal[2 * i];
+            b[0].a_off = q.rmr_off;
+            b[0].b_off = cmh1;
+            b[0].out_off = q.e1_off;
+            b[1].a_off = cmh2;
+            b[1].b_off = cmx;
+            b[1].out_off = q.e2_off;
+            SplitGemmDesc g1{};
+            g1.a_dig = q.a1_dig;
+            g1.a_exp = q.a1_exp;
+            g1.b_dig = q.b1_dig;
+            g1.b_exp = q.b1_exp;
+            g1.c_off = d.x_off;
+            g1.M = k2;
+            g1.N = d.nab;
+            g1.nkb = q.nkb1;
+            g1.ldc = k2;
+            g1.transpose = 1;
+            P.sg1.push_back(g1);
+            SplitGemmDesc g2{};
+            g2.a_dig = q.a2_dig;
+            g2.a_exp = q.a2_exp;
+            g2.b_dig = q.b2_dig;
+            g2.b_exp = q.b2_exp;
+            g2.c_off = d.out_off;
+            g2.M = d.nab;
+            g2.N = d.ncd;
+            g2.nkb = q.nkb2;
+            g2.ldc = d.ncd;
+            g2.transpose = 0;
+            P.sg2.push_back(g2);
+        }
     }
     P.total = (size_t)dw * 8 - chunk_base;
     P.blob.assign(P.off_data, 0);
-    std::memcpy(P.blob.data() + P.off_pairs, P.pairs.data(), sizeof(DPair) * P.pairs.size());
-    std::memcpy(P.blob.data() + P.off_quartets, P.quartets.data(), sizeof(DQuartet) * P.quartets.size());
-    std::memcpy(P.blob.data() + P.off_h, P.items_h.data(), sizeof(WorkItem) * P.items_h.size());
-    std::memcpy(P.blob.data() + P.off_br, P.items_br.data(), sizeof(WorkItem) * P.items_br.size());
-    std::memcpy(P.blob.data() + P.off_g1, P.items_g1.data(), sizeof(WorkItem) * P.items_g1.size());
-    std::memcpy(P.blob.data() + P.off_g2, P.items_g2.data(), sizeof(WorkItem) * P.items_g2.size());
+    auto put = [&](size_t off, const void* src, size_t bytes) {
+        if (bytes) std::memcpy(P.blob.data() + off, src, bytes);
+    };
+    put(P.off_pairs, P.pairs.data(), sizeof(DPair) * P.pairs.size());
+    put(P.off_quartets, P.quartets.data(), sizeof(DQuartet) * P.quartets.size());
+    put(P.off_h, P.items_h.data(), sizeof(WorkItem) * P.items_h.size());
+    put(P.off_br, P.items_br.data(), sizeof(WorkItem) * P.items_br.size());
+    put(P.off_g1, P.items_g1.data(), sizeof(WorkItem) * P.items_g1.size());
+    put(P.off_g2, P.items_g2.data(), sizeof(WorkItem) * P.items_g2.size());
+    put(P.off_srd, P.srd.data(), sizeof(SplitRowsDesc) * P.srd.size());
+    put(P.off_cmd, P.cmd.data(), sizeof(ColMaxDesc) * P.cmd.size());
+    put(P.off_bal, P.bal.data(), sizeof(BalanceDesc) * P.bal.size());
+    put(P.off_sq, P.sq.data(), sizeof(SplitQuartet) * P.sq.size());
+    put(P.off_sg1, P.sg1.data(), sizeof(SplitGemmDesc) * P.sg1.size());
+    put(P.off_sg2, P.sg2.data(), sizeof(SplitGemmDesc) * P.sg2.size());
+    put(P.off_icA, P.items_cA.data(), sizeof(WorkItem) * P.items_cA.size());
+    put(P.off_irm, P.items_rm.data(), sizeof(WorkItem) * P.items_rm.size());
+    put(P.off_ib1, P.items_b1.data(), sizeof(WorkItem) * P.items_b1.size());
+    put(P.off_isr, P.items_sr.data(), sizeof(WorkItem) * P.items_sr.size());
+    put(P.off_isB, P.items_sB.data(), sizeof(WorkItem) * P.items_sB.size());
+    put(P.off_isg1, P.items_sg1.data(), sizeof(WorkItem) * P.items_sg1.size());
+    put(P.off_icC, P.items_cC.data(), sizeof(WorkItem) * P.items_cC.size());
+    put(P.off_ib2, P.items_b2.data(), sizeof(WorkItem) * P.items_b2.size());
+    put(P.off_isD, P.items_sD.data(), sizeof(WorkItem) * P.items_sD.size());
+    put(P.off_isg2, P.items_sg2.data(), sizeof(WorkItem) * P.items_sg2.size());
 }
 
 // Workspace bytes that plan_chunks needs to keep quartets [b, e) in one chunk (an upper
 // bound of the exact layout built by build_chunk).
-size_t chunk_estimate(const lx_shell* sh, const lx_quartet* qs, int64_t b, int64_t e, bool solid) {
+size_t chunk_estimate(const lx_shell* sh, const lx_quartet* qs, int64_t b, int64_t e, int flags) {
     std::unordered_map<PairKey, int, PairKeyHash> seen;
     size_t used = CHUNK_SLACK;
     for (int64_t i = b; i < e; ++i) {
         const lx_quartet& q = qs[i];
-        used += quartet_bytes(sh, q, solid);
+        used += quartet_bytes(sh, q, flags);
         const PairKey kb{((int64_t)q.s[0] << 32 | (uint32_t)q.s[1]) * 2};
         const PairKey kk{((int64_t)q.s[2] << 32 | (uint32_t)q.s[3]) * 2 + 1};
-        if (!seen.count(kb)) used += pair_bytes(sh, q.s[0], q.s[1], solid);
-        if (!seen.count(kk)) used += pair_bytes(sh, q.s[2], q.s[3], solid);
+        if (!seen.count(kb)) used += pair_bytes(sh, q.s[0], q.s[1], flags);
+        if (!seen.count(kk)) used += pair_bytes(sh, q.s[2], q.s[3], flags);
         seen[kb] = 1;
         seen[kk] = 1;
     }
@@ -372,7 +561,7 @@ int64_t lx_eri_workspace_size(const lx_shell* shells, int32_t nshell, const lx_q
     const int v = validate(shells, nshell, nullptr, nullptr, 0, quartets, nquartet, flags, false);
     if (v != LX_OK) return v;
     return (int64_t)(head_bytes(nshell, (int32_t)prim_count(shells, nshell)) +
-                     chunk_estimate(shells, quartets, 0, nquartet, flags & LX_SOLID));
+                     chunk_estimate(shells, quartets, 0, nquartet, flags & (LX_SOLID | LX_PATH_SPLIT)));
 }
 
 int64_t lx_eri_workspace_min(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
@@ -380,7 +569,8 @@ int64_t lx_eri_workspace_min(const lx_shell* shells, int32_t nshell, const lx_qu
     const int v = validate(shells, nshell, nullptr, nullptr, 0, quartets, nquartet, flags, false);
     if (v != LX_OK) return v;
     size_t mx = CHUNK_SLACK;
-    for (int64_t i = 0; i < nquartet; ++i) mx = std::max(mx, chunk_estimate(shells, quartets, i, i + 1, flags & LX_SOLID));
+    for (int64_t i = 0; i < nquartet; ++i)
+        mx = std::max(mx, chunk_estimate(shells, quartets, i, i + 1, flags & (LX_SOLID | LX_PATH_SPLIT)));
     return (int64_t)(head_bytes(nshell, (int32_t)prim_count(shells, nshell)) + mx);
 }
 
@@ -399,7 +589,9 @@ int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, con
     const size_t head = head_bytes(nshell, nprim_total);
     if (workspace_bytes < head + CHUNK_SLACK) return LX_ERR_WORKSPACE;
     std::vector<Chunk> chunks;
-    if ((v = plan_chunks(shells, quartets, nquartet, solid, workspace_bytes - head, chunks)) != LX_OK) return v;
+    const int pflags = flags & (LX_SOLID | LX_PATH_SPLIT);
+    const bool split = flags & LX_PATH_SPLIT;
+    if ((v = plan_chunks(shells, quartets, nquartet, pflags, workspace_bytes - head, chunks)) != LX_OK) return v;
 
     char* wsb = static_cast<char*>(workspace);
     double* ws = static_cast<double*>(workspace);
@@ -430,7 +622,7 @@ int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, con
 
     ChunkPlan P;
     for (const auto& ch : chunks) {
-        build_chunk(shells, quartets, ch, solid, head, P);
+        build_chunk(shells, quartets, ch, pflags, head, P);
         if (head + P.total > workspace_bytes) return LX_ERR_WORKSPACE;
         char* base = wsb + head;
         e = cudaMemcpyAsync(base, P.blob.data(), P.off_data, cudaMemcpyHostToDevice, st);
@@ -450,6 +642,45 @@ int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, con
         if ((e = launch_boys_r(d_q, d_pairs, d_ibr, (int)P.items_br.size(), ws, status, st)) != cudaSuccess)
             return cuda_fail(e);
         if ((e = tm.end(LX_STAGE_BOYS_R, 1)) != cudaSuccess) return cuda_fail(e);
+        if (split) {
+            auto at = [&](size_t off) { return base + off; };
+            const SplitRowsDesc* d_srd = reinterpret_cast<const SplitRowsDesc*>(at(P.off_srd));
+            const ColMaxDesc* d_cmd = reinterpret_cast<const ColMaxDesc*>(at(P.off_cmd));
+            const BalanceDesc* d_bal = reinterpret_cast<const BalanceDesc*>(at(P.off_bal));
+            const SplitQuartet* d_sq = reinterpret_cast<const SplitQuartet*>(at(P.off_sq));
+            const SplitGemmDesc* d_sg1 = reinterpret_cast<const SplitGemmDesc*>(at(P.off_sg1));
+            const SplitGemmDesc* d_sg2 = reinterpret_cast<const SplitGemmDesc*>(at(P.off_sg2));
+            auto items = [&](size_t off) { return reinterpret_cast<const WorkItem*>(at(off)); };
+            // operands of GEMM1: balance exponents, then digit planes of [p|q]^T and H_bra
+            if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
+            if ((e = launch_colmax(d_cmd, items(P.off_icA), (int)P.items_cA.size(), ws, wsb, st)) != cudaSuccess ||
+                (e = launch_rowmax_r(d_q, d_sq, items(P.off_irm), (int)P.items_rm.size(), ws, wsb, st)) !=
+                    cudaSuccess ||
+                (e = launch_balance(d_bal, items(P.off_ib1), (int)P.items_b1.size(), wsb, st)) != cudaSuccess ||
+                (e = launch_split_r(d_q, d_sq, items(P.off_isr), (int)P.items_sr.size(), ws, wsb, st)) !=
+                    cudaSuccess ||
+                (e = launch_split_rows(d_srd, items(P.off_isB), (int)P.items_sB.size(), ws, wsb, st)) != cudaSuccess)
+                return cuda_fail(e);
+            if ((e = tm.end(LX_STAGE_SPLIT, 5)) != cudaSuccess) return cuda_fail(e);
+            if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
+            if ((e = launch_split_gemm(d_sg1, items(P.off_isg1), (int)P.items_sg1.size(), wsb, ws, status, st)) !=
+                cudaSuccess)
+                return cuda_fail(e);
+            if ((e = tm.end(LX_STAGE_GEMM1, 1)) != cudaSuccess) return cuda_fail(e);
+            // operands of GEMM2: balance exponents, digit planes of [ab|q] and H_ket
+            if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
+            if ((e = launch_colmax(d_cmd, items(P.off_icC), (int)P.items_cC.size(), ws, wsb, st)) != cudaSuccess ||
+                (e = launch_balance(d_bal, items(P.off_ib2), (int)P.items_b2.size(), wsb, st)) != cudaSuccess ||
+                (e = launch_split_rows(d_srd, items(P.off_isD), (int)P.items_sD.size(), ws, wsb, st)) != cudaSuccess)
+                return cuda_fail(e);
+            if ((e = tm.end(LX_STAGE_SPLIT, 3)) != cudaSuccess) return cuda_fail(e);
+            if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
+            if ((e = launch_split_gemm(d_sg2, items(P.off_isg2), (int)P.items_sg2.size(), wsb, out, status, st)) !=
+                cudaSuccess)
+                return cuda_fail(e);
+            if ((e = tm.end(LX_STAGE_GEMM2, 1)) != cudaSuccess) return cuda_fail(e);
+            continue;
+        }
         if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
         if ((e = launch_gemm1(d_q, d_pairs, d_ig1, (int)P.items_g1.size(), ws, status, st)) != cudaSuccess)
             return cuda_fail(e);
@@ -623,6 +854,65 @@ int lx_hermite_H(const lx_shell* shells, int32_t nshell, const double* exps, con
     if ((e = launch_pair_h(reinterpret_cast<const DPair*>(scratch + o_pairs),
                            reinterpret_cast<const WorkItem*>(scratch + o_items), (int)items.size(), d_sh, d_exps,
                            d_ncoef, H, reinterpret_cast<double*>(scratch + o_info), status, st)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaFreeAsync(scratch, st)) != cudaSuccess) return cuda_fail(e);
+    return LX_OK;
+}
+
+int lx_split_gemm(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda, const double* B, int32_t ldb,
+                  double* C, int32_t ldc, void* cuda_stream) {
+    if (M < 1 || N < 1 || K < 1 || K > (1 << 20) || lda < K || ldb < K || ldc < N) return LX_ERR_SIZE;
+    if (!A || !B || !C) return LX_ERR_NULL;
+    unsigned* status = nullptr;
+    int v = ensure_device(&status);
+    if (v != LX_OK) return v;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int nkb = split_nkb(K);
+    const int ra = split_rowpad(M, SPLIT_TA), rb = split_rowpad(N, SPLIT_TB);
+    std::vector<SplitRowsDesc> rd(2);
+    rd[0] = SplitRowsDesc{0, 0, 0, -1, lda, M, K, SPLIT_TA, nkb, 0};
+    rd[1] = SplitRowsDesc{0, 0, 0, -1, ldb, N, K, SPLIT_TB, nkb, 0};
+    std::vector<WorkItem> ia, ib, ig;
+    for (int r = 0; r < ra; ++r) ia.push_back({0, r, 0, 0});
+    for (int r = 0; r < rb; ++r) ib.push_back({1, r, 0, 0});
+    for (int m = 0; m < ra / SPLIT_TA; ++m)
+        for (int n = 0; n < (N + SPLIT_TB - 1) / SPLIT_TB; ++n) ig.push_back({0, m, n, 0});
+    size_t o = 0;
+    auto region = [&](size_t bytes) {
+        const size_t at = o;
+        o = align256(o + bytes);
+        return at;
+    };
+    const size_t o_rd = region(sizeof(SplitRowsDesc) * 2), o_g = region(sizeof(SplitGemmDesc));
+    const size_t o_ia = region(sizeof(WorkItem) * ia.size()), o_ib = region(sizeof(WorkItem) * ib.size());
+    const size_t o_ig = region(sizeof(WorkItem) * ig.size());
+    const size_t blob_bytes = o;
+    rd[0].dig_off = (int64_t)region((size_t)split_dig_bytes(M, K, SPLIT_TA));
+    rd[0].exp_off = (int64_t)region(4 * (size_t)ra);
+    rd[1].dig_off = (int64_t)region((size_t)split_dig_bytes(N, K, SPLIT_TB));
+    rd[1].exp_off = (int64_t)region(4 * (size_t)rb);
+    SplitGemmDesc g{rd[0].dig_off, rd[0].exp_off, rd[1].dig_off, rd[1].exp_off, 0, M, N, nkb, ldc, 0, 0};
+    std::vector<char> blob(blob_bytes, 0);
+    std::memcpy(blob.data() + o_rd, rd.data(), sizeof(SplitRowsDesc) * 2);
+    std::memcpy(blob.data() + o_g, &g, sizeof(g));
+    std::memcpy(blob.data() + o_ia, ia.data(), sizeof(WorkItem) * ia.size());
+    std::memcpy(blob.data() + o_ib, ib.data(), sizeof(WorkItem) * ib.size());
+    std::memcpy(blob.data() + o_ig, ig.data(), sizeof(WorkItem) * ig.size());
+    char* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), o, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(scratch, blob.data(), blob_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e);
+    const SplitRowsDesc* d_rd = reinterpret_cast<const SplitRowsDesc*>(scratch + o_rd);
+    if ((e = launch_split_rows(d_rd, reinterpret_cast<const WorkItem*>(scratch + o_ia), (int)ia.size(), A, scratch,
+                               st)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = launch_split_rows(d_rd, reinterpret_cast<const WorkItem*>(scratch + o_ib), (int)ib.size(), B, scratch,
+                               st)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = launch_split_gemm(reinterpret_cast<const SplitGemmDesc*>(scratch + o_g),
+                               reinterpret_cast<const WorkItem*>(scratch + o_ig), (int)ig.size(), scratch, C, status,
+                               st)) != cudaSuccess)
         return cuda_fail(e);
     if ((e = cudaFreeAsync(scratch, st)) != cudaSuccess) return cuda_fail(e);
     return LX_OK;

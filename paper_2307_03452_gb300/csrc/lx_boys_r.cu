@@ -53,6 +53,15 @@ __device__ void boys_eval(int mmax, double T, double* F) {
     }
 }
 
+// B[m] *= pref (-2 rho)^m for m = 0..L (L <= LTOT < 32), one m per lane: the power is
+// taken directly rather than as a running product, which keeps its rounding at one step.
+__device__ inline void scale_base(int L, double rho, double pref, double* B, int lane) {
+    if (lane <= L) {
+        const double pw = pow(2.0 * rho, (double)lane);
+        B[lane] *= (lane & 1) ? -pref * pw : pref * pw;
+    }
+}
+
 // Within-total position s (0 <= s < (n+1)(n+2)/2) -> (i, v) with s = i(i+1)/2 + v.
 __device__ inline void split_pos(int s, int& i, int& v) {
     i = (int)((sqrtf(8.0f * s + 1.0f) - 1.0f) * 0.5f);
@@ -121,15 +130,10 @@ __global__ void __launch_bounds__(BR_WARPS * 32) boys_r_kernel(const DQuartet* _
     const double X = ib[1] - ik[1], Y = ib[2] - ik[2], Z = ib[3] - ik[3];
     const double rho = zp * zq / (zp + zq);
     const double T = rho * (X * X + Y * Y + Z * Z);
-    if (lane == 0) {
-        boys_eval(q.L, T, B);
-        // [0]^(m) = (-2 rho)^m 2 pi^{5/2} / (zeta_p zeta_q sqrt(zeta_p + zeta_q)) F_m(T)
-        double f = 2.0 * PI * PI * sqrt(PI) / (zp * zq * sqrt(zp + zq));
-        for (int m = 0; m <= q.L; ++m) {
-            B[m] *= f;
-            f *= -2.0 * rho;
-        }
-    }
+    if (lane == 0) boys_eval(q.L, T, B);
+    __syncwarp();
+    // [0]^(m) = (-2 rho)^m 2 pi^{5/2} / (zeta_p zeta_q sqrt(zeta_p + zeta_q)) F_m(T), one m per lane
+    scale_base(q.L, rho, 2.0 * PI * PI * sqrt(PI) / (zp * zq * sqrt(zp + zq)), B, lane);
     __syncwarp();
     hermite_r_warp(q.L, X, Y, Z, B, R, lane);
     double* out = ws + q.rr_off + (int64_t)kpq * nr;
@@ -163,14 +167,9 @@ __global__ void __launch_bounds__(BR_WARPS * 32) hermite_r_stage_kernel(int L, c
     double* B = R + nr;
     const double rho = params[5 * item], X = params[5 * item + 1], Y = params[5 * item + 2],
                  Z = params[5 * item + 3], pref = params[5 * item + 4];
-    if (lane == 0) {
-        boys_eval(L, rho * (X * X + Y * Y + Z * Z), B);
-        double f = pref;
-        for (int m = 0; m <= L; ++m) {
-            B[m] *= f;
-            f *= -2.0 * rho;
-        }
-    }
+    if (lane == 0) boys_eval(L, rho * (X * X + Y * Y + Z * Z), B);
+    __syncwarp();
+    scale_base(L, rho, pref, B, lane);
     __syncwarp();
     hermite_r_warp(L, X, Y, Z, B, R, lane);
     for (int r = lane; r < nr; r += 32) Rout[item * nr + r] = R[r];

@@ -50,6 +50,8 @@ struct DPair {  // one shell pair on one side of the quartet
     int pad;
     int64_t h_off;     // H block (doubles): [nrow][Kab*np]
     int64_t info_off;  // pair scalars (doubles): [Kab][4] = zeta_p, P
+    int64_t dig_off;   // split path: digit planes of H (bytes from the workspace base)
+    int64_t exp_off;   // split path: row exponents of H (bytes)
 };
 
 struct DQuartet {
@@ -70,7 +72,7 @@ struct WorkItem {  // generic work descriptor: owner + two tile indices
 // ----------------------------------------------------------------- per-TU launchers
 // Tables (called once per device with that device current).
 cudaError_t init_boys_table(const double* host_table);      // lx_boys_r.cu
-cudaError_t init_prep_tables(const double* host_coefs, const int* host_tuv);  // lx_prep.cu
+cudaError_t init_prep_tables(const double* host_coefs, const int* host_tuv, const void* host_classes);  // lx_prep.cu
 cudaError_t init_tuv_table(const int* host_tuv);           // lx_gemm.cu
 
 cudaError_t launch_norm(const DShell* sh, int nshell, const double* exps, const double* coefs, double* ncoef,
@@ -93,10 +95,23 @@ constexpr int GEMM_BM = 32;
 constexpr int GEMM_BN = 64;
 constexpr int GEMM_BK = 16;
 
+// Real solid harmonics have fixed parities of the x, y, z exponents, so the matrix C of one
+// shell is block diagonal over the (at most 4) parity classes of its Cartesian components.
+constexpr int SC_MAXA = 10;  // Cartesian components in one class (l <= 6)
+constexpr int SC_MAXM = 4;   // solid functions in one class (l <= 6)
+struct SolidClassTab {
+    int ncls;
+    int na[4], nm[4];
+    int comp[4][SC_MAXA];  // packed exponents ax | ay << 8 | az << 16
+    int mind[4][SC_MAXM];  // m + l of each solid function
+    double c[4][SC_MAXM][SC_MAXA];
+};
+
 // Host-side table generators (lx_tables.cpp).
 void make_boys_table(double* table);        // BOYS_NROW * BOYS_NPT
 void make_solid_coefs(double* coefs);       // packed: l = 0..LMAX, (2l+1) x ncart(l) each
 int solid_offset(int l);                    // offset of shell l's block in the packed array
 void make_tuv_table(int* tuv);              // NHERM_TOT entries: t | u << 8 | v << 16
+void make_solid_classes(const double* coefs, SolidClassTab* tab);  // tab[LMAX + 1]
 
 }  // namespace lx

@@ -13,6 +13,7 @@ constexpr int NSOLID_PACKED = 840;  // sum over l = 0..6 of (2l+1) ncart(l)
 __constant__ double c_solid[NSOLID_PACKED];
 __constant__ int c_solid_off[LMAX + 2];
 __device__ int g_tuv_prep[NHERM_TOT];
+__constant__ SolidClassTab c_cls[LMAX + 1];
 
 constexpr double PI = 3.141592653589793238462643383279502884;
 
@@ -81,7 +82,6 @@ __global__ void __launch_bounds__(PAIR_THREADS) pair_h_kernel(const DPair* __res
     const int la = sa.l, lb = sb.l, lsum = la + lb, nt = lsum + 1;
     const int kp = it.a, ia = kp / sb.K, ib = kp - ia * sb.K;
     const double za = exps[sa.prim_off + ia], zb = exps[sb.prim_off + ib], zp = za + zb;
-    const int ntab = (la + 1) * (lb + 1) * nt;
 
     for (int i = threadIdx.x; i < 3 * ETAB; i += blockDim.x) (&E[0][0])[i] = 0.0;
     __syncthreads();
@@ -91,8 +91,9 @@ __global__ void __launch_bounds__(PAIR_THREADS) pair_h_kernel(const DPair* __res
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp < 3) {
         const int d = warp;
-        const double P = (za * sa.A[d] + zb * sb.A[d]) / zp;
-        const double PA = P - sa.A[d], PB = P - sb.A[d], oo2p = 0.5 / zp;
+        const double Ad = sh[pr.sa].A[d], Bd = sh[pr.sb].A[d];
+        const double P = (za * Ad + zb * Bd) / zp;
+        const double PA = P - Ad, PB = P - Bd, oo2p = 0.5 / zp;
         double* Ed = E[d];
 #define EIJ(i, j, t) Ed[((i) * (lb + 1) + (j)) * nt + (t)]
         if (lane == 0) EIJ(0, 0, 0) = 1.0;
@@ -129,6 +130,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) pair_h_kernel(const DPair* __res
         double AB2 = 0.0;
         double* info = ws_info + pr.info_off + 4 * (int64_t)kp;
         info[0] = zp;
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
             info[1 + d] = (za * sa.A[d] + zb * sb.A[d]) / zp;
             AB2 += (sa.A[d] - sb.A[d]) * (sa.A[d] - sb.A[d]);
@@ -136,7 +138,6 @@ __global__ void __launch_bounds__(PAIR_THREADS) pair_h_kernel(const DPair* __res
         s_pref = exp(-za * zb / zp * AB2) * ncoef[sa.prim_off + ia] * ncoef[sb.prim_off + ib];
     }
     __syncthreads();
-    (void)ntab;
 
     const int np = pr.np;
     const int64_t ldh = (int64_t)pr.Kab * np;
@@ -164,46 +165,68 @@ __global__ void __launch_bounds__(PAIR_THREADS) pair_h_kernel(const DPair* __res
             H[(int64_t)ab * ldh + p] = pref * v;
         }
     } else {
-        // H[ma mb][p] = pref * sign(p) * sum_a C_a[ma][a] sum_b C_b[mb][b] E_ab^p, with the
-        // b-sum done per a and the a-sum accumulated in registers for all ma.
-        const int nsa = 2 * la + 1, nsb = 2 * lb + 1;
-        const double* Ca = c_solid + c_solid_off[la];
-        const double* Cb = c_solid + c_solid_off[lb];
-        const int total = nsb * np;
+        // H[ma mb][p] = pref * sign(p) * sum_a C_a[ma][a] sum_b C_b[mb][b] E_ab^p.
+        // C is block diagonal over parity classes, so one work item is (class of a, class of
+        // b, p): the E products of the class's b components are formed once per a and shared
+        // by all of its m_b; the a-sum accumulates a (<= 4) x (<= 4) register block.
+        const SolidClassTab& TA = c_cls[la];
+        const SolidClassTab& TB = c_cls[lb];
+        const int nsb = 2 * lb + 1;
+        const int ncb_cls = TB.ncls;
+        const int total = TA.ncls * ncb_cls * np;
         for (int i = threadIdx.x; i < total; i += blockDim.x) {
-            const int mb = i / np, p = i - mb * np;
+            const int g = i / np, p = i - g * np;
+            const int ca = g / ncb_cls, cb = g - ca * ncb_cls;
             const int tuv = g_tuv_prep[p];
             const int px = tuv & 255, py = (tuv >> 8) & 255, pz = tuv >> 16;
-            double acc[NSOL_MAX];
+            const int na = TA.na[ca], nma = TA.nm[ca], nb = TB.na[cb], nmb = TB.nm[cb];
+            double acc[SC_MAXM][SC_MAXM];
 #pragma unroll
-            for (int m = 0; m < NSOL_MAX; ++m) acc[m] = 0.0;
-            for (int a = 0; a < nca; ++a) {
-                int ax, ay, az;
-                cart_of(a, la, ax, ay, az);
-                double u = 0.0;
-                for (int b = 0; b < ncb; ++b) {
-                    const double c = Cb[mb * ncb + b];
-                    if (c == 0.0) continue;
-                    int bx, by, bz;
-                    cart_of(b, lb, bx, by, bz);
-                    u += c * (Ex[(ax * sb1 + bx) * nt + px] * Ey[(ay * sb1 + by) * nt + py] *
-                              Ez[(az * sb1 + bz) * nt + pz]);
+            for (int x = 0; x < SC_MAXM; ++x)
+#pragma unroll
+                for (int y = 0; y < SC_MAXM; ++y) acc[x][y] = 0.0;
+            for (int ia = 0; ia < na; ++ia) {
+                const int ac = TA.comp[ca][ia];
+                const int ax = ac & 255, ay = (ac >> 8) & 255, az = ac >> 16;
+                const double* ex = Ex + (ax * sb1) * nt + px;
+                const double* ey = Ey + (ay * sb1) * nt + py;
+                const double* ez = Ez + (az * sb1) * nt + pz;
+                double v[SC_MAXA];
+#pragma unroll
+                for (int ib = 0; ib < SC_MAXA; ++ib) {
+                    v[ib] = 0.0;
+                    if (ib < nb) {
+                        const int bc = TB.comp[cb][ib];
+                        v[ib] = ex[(bc & 255) * nt] * ey[((bc >> 8) & 255) * nt] * ez[(bc >> 16) * nt];
+                    }
                 }
 #pragma unroll
-                for (int m = 0; m < NSOL_MAX; ++m)
-                    if (m < nsa) acc[m] += Ca[m * nca + a] * u;
+                for (int jb = 0; jb < SC_MAXM; ++jb) {
+                    if (jb < nmb) {
+                        double u = 0.0;
+#pragma unroll
+                        for (int ib = 0; ib < SC_MAXA; ++ib)
+                            if (ib < nb) u += TB.c[cb][jb][ib] * v[ib];
+#pragma unroll
+                        for (int ja = 0; ja < SC_MAXM; ++ja)
+                            if (ja < nma) acc[ja][jb] += TA.c[ca][ja][ia] * u;
+                    }
+                }
             }
             const double sg = (pr.sign && ((px + py + pz) & 1)) ? -pref : pref;
 #pragma unroll
-            for (int m = 0; m < NSOL_MAX; ++m)
-                if (m < nsa) H[(int64_t)(m * nsb + mb) * ldh + p] = sg * acc[m];
+            for (int ja = 0; ja < SC_MAXM; ++ja)
+#pragma unroll
+                for (int jb = 0; jb < SC_MAXM; ++jb)
+                    if (ja < nma && jb < nmb)
+                        H[(int64_t)(TA.mind[ca][ja] * nsb + TB.mind[cb][jb]) * ldh + p] = sg * acc[ja][jb];
         }
     }
 }
 
 }  // namespace
 
-cudaError_t init_prep_tables(const double* host_coefs, const int* host_tuv) {
+cudaError_t init_prep_tables(const double* host_coefs, const int* host_tuv, const void* host_classes) {
     int off[LMAX + 2];
     off[0] = 0;
     for (int l = 0; l <= LMAX; ++l) off[l + 1] = off[l] + (2 * l + 1) * ncart(l);
@@ -211,6 +234,8 @@ cudaError_t init_prep_tables(const double* host_coefs, const int* host_tuv) {
     cudaError_t e = cudaMemcpyToSymbol(c_solid, host_coefs, sizeof(double) * NSOLID_PACKED);
     if (e != cudaSuccess) return e;
     e = cudaMemcpyToSymbol(c_solid_off, off, sizeof(off));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyToSymbol(c_cls, host_classes, sizeof(SolidClassTab) * (LMAX + 1));
     if (e != cudaSuccess) return e;
     return cudaMemcpyToSymbol(g_tuv_prep, host_tuv, sizeof(int) * NHERM_TOT);
 }

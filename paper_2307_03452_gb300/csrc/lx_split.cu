@@ -1,0 +1,529 @@
+// Split-precision transforms: the two GEMMs of the paper's Eq. make-abq and Eq. make-abcd
+// evaluated as Ozaki-style sums of BF16 slice products on the tcgen05 tensor cores.
+//
+// Each FP64 operand row x is written as x = 2^(e - W) * q with a per-row power of two 2^e
+// (|x| < 2^e over the row), q an integer of W = NSLICE * BETA bits, and q split into NSLICE
+// signed digits of BETA bits, q = sum_s d_s 2^(BETA (NSLICE-1-s)).  Every digit is an
+// integer of magnitude <= 2^BETA, exact in BF16.  The product of two such rows is
+//   sum_{s,t} 2^(BETA (2 NSLICE - 2 - s - t)) sum_k dA_s dB_t,
+// and each inner sum is a sum of integer products whose magnitude stays far below 2^24,
+// so the FP32 accumulators of the tensor core hold it exactly.  Products with
+// s + t <= NSLICE - 1 are kept; each diagonal d = s + t has its own TMEM accumulator, and the
+// epilogue combines the diagonals in 64-bit integer arithmetic (exact) before a single
+// conversion to FP64.  FP64 arithmetic, which is scarce on this GPU, is used for none of it:
+// the splitting works on the bit patterns of the FP64 inputs.
+//
+// Kernels:
+//   split_rows_kernel  FP64 row-major matrix rows -> digit planes + row exponents
+//   split_r_kernel     rows q of the [p|q] operand gathered from [r]^(0) -> digit planes
+//   split_gemm_kernel  D = A B^T on tcgen05 (M tile 128, N tile <= 96, K blocks of 32),
+//                      operand blocks streamed by bulk TMA copies into a 3-stage mbarrier
+//                      pipeline, one thread issuing the MMAs, all four warps in the epilogue.
+#include <cstdint>
+
+#include "lx_internal.cuh"
+#include "lx_split.cuh"
+
+namespace lx {
+
+namespace {
+
+constexpr unsigned long long WAIT_LIMIT = 1ull << 24;  // bounded spin: then flag and bail out
+
+__device__ int g_tuv_split[NHERM_TOT];
+
+__device__ inline void set_status(unsigned* st, unsigned bit) { atomicOr(st, bit); }
+
+__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ inline void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false (and the status bit) when the limit is reached.
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t phase, unsigned* status) {
+    for (unsigned long long i = 0; i < WAIT_LIMIT; ++i)
+        if (mbar_try_wait(bar, phase)) return true;
+    set_status(status, ST_TIMEOUT);
+    return false;
+}
+
+// Bulk (non-tensor) TMA copy global -> shared; completes `bytes` of transaction on `bar`.
+__device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ inline void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ inline void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ inline void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of 8 rows x 16 bytes;
+// lbo = byte distance between core matrices adjacent in K, sbo = adjacent in M/N.
+__device__ inline uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+    return d;                // base offset 0, no swizzle
+}
+
+// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both operands K-major.
+__device__ inline uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4)                    // D format: F32
+           | (1u << 7)                  // A format: BF16
+           | (1u << 10)                 // B format: BF16
+           | ((uint32_t)(N >> 3) << 17)  // N / 8
+           | ((uint32_t)(M >> 4) << 24); // M / 16
+}
+
+__device__ inline void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ inline void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ inline void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ inline void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ------------------------------------------------------------------ splitting
+
+// Biased exponent field of an FP64 value (0 for zero / subnormal).
+__device__ inline int exp_field(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+
+// x * 2^s by exponent arithmetic (exact; underflow to zero).
+__device__ inline double scale2(double x, int s) {
+    const long long bits = __double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    if (ex == 0 || s == 0) return ex == 0 ? 0.0 : x;
+    const int ne = ex + s;
+    if (ne <= 0) return 0.0;
+    if (ne >= 2047) return __longlong_as_double((bits & (1ll << 63)) | 0x7FF0000000000000ll);
+    return __longlong_as_double((bits & ~(0x7FFll << 52)) | ((long long)ne << 52));
+}
+
+// q = round(x * 2^(W - e)) for |x| < 2^e, from the bit pattern (no FP64 arithmetic).
+__device__ inline long long fixed_of(double x, int e) {
+    const long long bits = __double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    if (ex == 0) return 0;  // zero or subnormal: below any row scale that matters
+    const long long mant = (bits & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+    const int rs = 1075 - ex - SPLIT_W + e;  // right shift, >= 53 - W > 0
+    long long q = 0;
+    if (rs < 63) q = (mant + (1ll << (rs - 1))) >> rs;
+    return bits < 0 ? -q : q;
+}
+
+// The digits of q, most significant first, balanced (each |d| <= 2^BETA).
+__device__ inline void digits_of(long long q, float (&d)[SPLIT_NSLICE]) {
+#pragma unroll
+    for (int s = 0; s < SPLIT_NSLICE - 1; ++s) {
+        const int sh = SPLIT_BETA * (SPLIT_NSLICE - 1 - s);
+        const long long di = (q + (1ll << (sh - 1))) >> sh;
+        q -= di << sh;
+        d[s] = (float)(int)di;
+    }
+    d[SPLIT_NSLICE - 1] = (float)(int)q;
+}
+
+// Offset (in BF16 elements) of element (row, k) of slice s inside an operand stored as
+// row tiles of T rows and K blocks of SPLIT_KB: block (rt, kb) holds NSLICE slice-blocks of
+// T x KB elements, each in core matrices (8 rows x 8 elements) ordered (row/8, k/8).
+__device__ inline int64_t dig_index(int row, int k, int s, int T, int nkb) {
+    const int rt = row / T, r = row - rt * T, kb = k / SPLIT_KB, kk = k - kb * SPLIT_KB;
+    const int64_t block = ((int64_t)rt * nkb + kb) * SPLIT_NSLICE + s;
+    return block * (T * SPLIT_KB) + ((r >> 3) * (SPLIT_KB / 8) + (kk >> 3)) * 64 + (r & 7) * 8 + (kk & 7);
+}
+
+// One warp per row.  desc: the matrix; item.a = row (may be a padding row).
+__global__ void split_rows_kernel(const SplitRowsDesc* __restrict__ descs, const WorkItem* __restrict__ items,
+                                  int nitems, const double* __restrict__ src_base, char* __restrict__ ws) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= nitems) return;
+    const WorkItem it = items[warp];
+    const SplitRowsDesc d = descs[it.q];
+    const int row = it.a;
+    const double* src = src_base + d.src_off + (int64_t)row * d.ld;
+    const bool live = row < d.rows;
+    const int* shift = d.shift_off >= 0 ? reinterpret_cast<const int*>(ws + d.shift_off) : nullptr;
+    auto value = [&](int k) -> double { return shift ? scale2(src[k], d.shift_sign * shift[k]) : src[k]; };
+    int mx = 0;
+    if (live)
+        for (int k = lane; k < d.K; k += 32) mx = max(mx, exp_field(value(k)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = mx > 0 ? mx - 1022 : 0;  // |x| < 2^e over the row
+    __nv_bfloat16* dig = reinterpret_cast<__nv_bfloat16*>(ws + d.dig_off);
+    const int kpad = d.nkb * SPLIT_KB;
+    for (int k = lane; k < kpad; k += 32) {
+        const double x = (live && k < d.K) ? value(k) : 0.0;
+        float dg[SPLIT_NSLICE];
+        digits_of(mx > 0 ? fixed_of(x, e) : 0ll, dg);
+#pragma unroll
+        for (int s = 0; s < SPLIT_NSLICE; ++s) dig[dig_index(row, k, s, d.T, d.nkb)] = __float2bfloat16_rn(dg[s]);
+    }
+    if (lane == 0) reinterpret_cast<int*>(ws + d.exp_off)[row] = e;
+}
+
+// One warp per row q of the GEMM1 A operand: A[q][k] = [p+q]^(0) of primitive quartet
+// (kp, kq) with k = kp*Np + p, q = kq*Nq + qq.  item.q = quartet, item.a = row.
+__global__ void split_r_kernel(const DQuartet* __restrict__ qd, const SplitQuartet* __restrict__ sq,
+                               const WorkItem* __restrict__ items, int nitems, const double* __restrict__ wsd,
+                               char* __restrict__ ws) {
+    const int* tuv_tab = g_tuv_split;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= nitems) return;
+    const WorkItem it = items[warp];
+    const DQuartet q = qd[it.q];
+    const SplitQuartet s = sq[it.q];
+    const int row = it.a;
+    const int nrow = q.kket * q.nq, K = q.kbra * q.np;
+    const bool live = row < nrow;
+    int kq = 0, tq = 0;
+    if (live) {
+        kq = row / q.nq;
+        tq = tuv_tab[row - kq * q.nq];
+    }
+    const double* Rr = wsd + q.rr_off;
+    const int* e1 = reinterpret_cast<const int*>(ws + s.e1_off);
+    auto value = [&](int k) -> double {
+        const int kp = k / q.np, p = k - kp * q.np;
+        const int sum = tuv_tab[p] + tq;
+        return scale2(Rr[(int64_t)(kp * q.kket + kq) * q.nr + hidx(sum & 255, (sum >> 8) & 255, sum >> 16)], -e1[k]);
+    };
+    int mx = 0;
+    if (live)
+        for (int k = lane; k < K; k += 32) mx = max(mx, exp_field(value(k)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = mx > 0 ? mx - 1022 : 0;
+    __nv_bfloat16* dig = reinterpret_cast<__nv_bfloat16*>(ws + s.a1_dig);
+    const int kpad = s.nkb1 * SPLIT_KB;
+    for (int k = lane; k < kpad; k += 32) {
+        const double x = (live && k < K) ? value(k) : 0.0;
+        float dg[SPLIT_NSLICE];
+        digits_of(mx > 0 ? fixed_of(x, e) : 0ll, dg);
+#pragma unroll
+        for (int t = 0; t < SPLIT_NSLICE; ++t) dig[dig_index(row, k, t, SPLIT_TA, s.nkb1)] = __float2bfloat16_rn(dg[t]);
+    }
+    if (lane == 0) reinterpret_cast<int*>(ws + s.a1_exp)[row] = e;
+}
+
+// One thread per column k: largest exponent field over the rows.  item = (desc, chunk).
+__global__ void colmax_kernel(const ColMaxDesc* __restrict__ descs, const WorkItem* __restrict__ items,
+                              const double* __restrict__ src_base, char* __restrict__ ws) {
+    const WorkItem it = items[blockIdx.x];
+    const ColMaxDesc d = descs[it.q];
+    const int k = it.a * 128 + threadIdx.x;
+    if (k >= d.K) return;
+    const double* src = src_base + d.src_off + k;
+    int mx = 0;
+    for (int r = 0; r < d.rows; ++r) mx = max(mx, exp_field(src[(int64_t)r * d.ld]));
+    reinterpret_cast<int*>(ws + d.out_off)[k] = mx;
+}
+
+// One thread per row k = kp*Np + p of [p|q]: largest exponent field over q = kq*Nq + qq.
+__global__ void rowmax_r_kernel(const DQuartet* __restrict__ qd, const SplitQuartet* __restrict__ sq,
+                                const WorkItem* __restrict__ items, const double* __restrict__ wsd,
+                                char* __restrict__ ws) {
+    const WorkItem it = items[blockIdx.x];
+    const DQuartet q = qd[it.q];
+    const int k = it.a * 128 + threadIdx.x;
+    if (k >= q.kbra * q.np) return;
+    const int kp = k / q.np, tp = g_tuv_split[k - kp * q.np];
+    int mx = 0;
+    for (int kq = 0; kq < q.kket; ++kq) {
+        const double* Rr = wsd + q.rr_off + (int64_t)(kp * q.kket + kq) * q.nr;
+        for (int qq = 0; qq < q.nq; ++qq) {
+            const int sum = tp + g_tuv_split[qq];
+            mx = max(mx, exp_field(Rr[hidx(sum & 255, (sum >> 8) & 255, sum >> 16)]));
+        }
+    }
+    reinterpret_cast<int*>(ws + sq[it.q].rmr_off)[k] = mx;
+}
+
+__global__ void balance_kernel(const BalanceDesc* __restrict__ descs, const WorkItem* __restrict__ items,
+                               char* __restrict__ ws) {
+    const WorkItem it = items[blockIdx.x];
+    const BalanceDesc d = descs[it.q];
+    const int k = it.a * 128 + threadIdx.x;
+    if (k >= d.K) return;
+    const int a = reinterpret_cast<const int*>(ws + d.a_off)[k], b = reinterpret_cast<const int*>(ws + d.b_off)[k];
+    reinterpret_cast<int*>(ws + d.out_off)[k] = (a > 0 && b > 0) ? ((a - b) >> 1) : 0;
+}
+
+// ------------------------------------------------------------------ tcgen05 GEMM
+
+constexpr int STAGES = 3;
+constexpr int A_BLOCK = SPLIT_NSLICE * SPLIT_TA * SPLIT_KB * 2;  // bytes of one A block (all slices)
+constexpr int B_BLOCK = SPLIT_NSLICE * SPLIT_TB * SPLIT_KB * 2;
+constexpr int A_SLICE = SPLIT_TA * SPLIT_KB * 2;
+constexpr int B_SLICE = SPLIT_TB * SPLIT_KB * 2;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr int SMEM_BYTES = STAGES * (A_BLOCK + B_BLOCK) + 1024;
+
+// int64 -> FP64 times 2^scale, correctly rounded (round to nearest even), integer ops only.
+__device__ inline double i64_to_f64_scaled(long long v, int scale) {
+    if (v == 0) return 0.0;
+    const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
+    unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    const int lz = __clzll((long long)a);
+    const int top = 63 - lz;  // index of the leading bit
+    // normalise to 53 bits with round-to-nearest-even
+    unsigned long long m;
+    int ex = top;
+    if (top > 52) {
+        const int sh = top - 52;
+        const unsigned long long rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        m = a >> sh;
+        if (rem > half || (rem == half && (m & 1))) {
+            ++m;
+            if (m >> 53) {
+                m >>= 1;
+                ++ex;
+            }
+        }
+    } else {
+        m = a << (52 - top);
+    }
+    const int be = ex + scale + 1023;
+    if (be <= 0) return 0.0;  // far below any integral of interest
+    if (be >= 2047) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull));
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
+// item.q = problem, item.a = M tile, item.b = N tile.
+__global__ void __launch_bounds__(128, 1) split_gemm_kernel(const SplitGemmDesc* __restrict__ probs,
+                                                            const WorkItem* __restrict__ items,
+                                                            const char* __restrict__ ws, double* __restrict__ cbase,
+                                                            unsigned* status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned operand stages
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const WorkItem it = items[blockIdx.x];
+    const SplitGemmDesc P = probs[it.q];
+    const int m0 = it.a * SPLIT_TA, n0 = it.b * SPLIT_TB;
+    int nt = P.N - n0;
+    nt = nt > SPLIT_TB ? SPLIT_TB : ((nt + 15) & ~15);
+    const int nkb = P.nkb;
+
+    if (warp == 0) {
+        tmem_alloc(&tmem_base_sh, TMEM_COLS);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&done_bar, 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    const char* a_src = ws + P.a_dig + (int64_t)it.a * nkb * A_BLOCK;
+    const char* b_src = ws + P.b_dig + (int64_t)it.b * nkb * B_BLOCK;
+
+    if (warp == 0 && lane == 0) {
+        // producer: stream the A and B blocks of each K block into the ring of stages
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int st = kb % STAGES, use = kb / STAGES;
+            if (use > 0 && !mbar_wait(&empty_bar[st], (use - 1) & 1, status)) {
+                abort_sh = 1;
+                break;
+            }
+            if (abort_sh) break;
+            unsigned char* sa = smem + st * (A_BLOCK + B_BLOCK);
+            unsigned char* sb = sa + A_BLOCK;
+            mbar_expect_tx(&full_bar[st], A_BLOCK + B_BLOCK);
+            bulk_g2s(sa, a_src + (int64_t)kb * A_BLOCK, A_BLOCK, &full_bar[st]);
+            bulk_g2s(sb, b_src + (int64_t)kb * B_BLOCK, B_BLOCK, &full_bar[st]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: diagonal d = s + t accumulates in TMEM columns [d * TB, d * TB + nt)
+        const uint32_t idesc = idesc_bf16(SPLIT_TA, nt);
+        bool started[SPLIT_NSLICE];
+#pragma unroll
+        for (int d = 0; d < SPLIT_NSLICE; ++d) started[d] = false;
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int st = kb % STAGES, use = kb / STAGES;
+            if (!mbar_wait(&full_bar[st], use & 1, status)) {
+                abort_sh = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + st * (A_BLOCK + B_BLOCK));
+            const uint32_t sb = sa + A_BLOCK;
+#pragma unroll
+            for (int ks = 0; ks < SPLIT_KB / 16; ++ks) {
+#pragma unroll
+                for (int s = 0; s < SPLIT_NSLICE; ++s) {
+                    const uint64_t ad = smem_desc(sa + s * A_SLICE + ks * 256, 128, (SPLIT_KB / 8) * 128);
+#pragma unroll
+                    for (int t = 0; t < SPLIT_NSLICE - s; ++t) {
+                        const int dg = s + t;
+                        const uint64_t bd = smem_desc(sb + t * B_SLICE + ks * 256, 128, (SPLIT_KB / 8) * 128);
+                        umma_bf16(tmem + dg * SPLIT_TB, ad, bd, idesc, started[dg] ? 1u : 0u);
+                        started[dg] = true;
+                    }
+                }
+            }
+            umma_commit(&empty_bar[st]);  // the stage is free once these MMAs have read it
+        }
+        umma_commit(&done_bar);
+    }
+    __syncwarp();
+    // epilogue: all four warps; warp w owns TMEM lanes (rows) 32w .. 32w+31
+    const bool waited = mbar_wait(&done_bar, 0, status);
+    tc_fence_after();
+    // one decision for the whole CTA before the warp-collective TMEM loads
+    const bool ok = __syncthreads_and(waited && !abort_sh) != 0;
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+        const bool rlive = row < P.M;
+        const int ea = rlive ? reinterpret_cast<const int*>(ws + P.a_exp)[row] : 0;
+        const int* eb_tab = reinterpret_cast<const int*>(ws + P.b_exp);
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < nt; c0 += 16) {
+            long long acc[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j] = 0;
+#pragma unroll
+            for (int dg = 0; dg < SPLIT_NSLICE; ++dg) {
+                uint32_t r[16];
+                tmem_ld16(lane_base + dg * SPLIT_TB + c0, r);
+                tmem_ld_wait();
+                const int sh = SPLIT_BETA * (SPLIT_NSLICE - 1 - dg);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+            }
+            if (rlive) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + c0 + j;
+                    if (col < P.N) {
+                        // D = 2^(eA + eB - 2W + BETA (NSLICE-1)) * acc
+                        const int scale = ea + eb_tab[col] - 2 * SPLIT_W + SPLIT_BETA * (SPLIT_NSLICE - 1);
+                        const double v = i64_to_f64_scaled(acc[j], scale);
+                        if (P.transpose)
+                            cbase[P.c_off + (int64_t)col * P.ldc + row] = v;
+                        else
+                            cbase[P.c_off + (int64_t)row * P.ldc + col] = v;
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+}  // namespace
+
+cudaError_t launch_split_rows(const SplitRowsDesc* descs, const WorkItem* items, int nitems, const double* src_base,
+                              char* ws, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    const int warps_per_block = 8;
+    split_rows_kernel<<<(nitems + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
+        descs, items, nitems, src_base, ws);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_r(const DQuartet* qd, const SplitQuartet* sq, const WorkItem* items, int nitems,
+                           const double* wsd, char* ws, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    const int warps_per_block = 8;
+    split_r_kernel<<<(nitems + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
+        qd, sq, items, nitems, wsd, ws);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colmax(const ColMaxDesc* descs, const WorkItem* items, int nitems, const double* src_base,
+                          char* ws, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    colmax_kernel<<<nitems, 128, 0, st>>>(descs, items, src_base, ws);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rowmax_r(const DQuartet* qd, const SplitQuartet* sq, const WorkItem* items, int nitems,
+                            const double* wsd, char* ws, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    rowmax_r_kernel<<<nitems, 128, 0, st>>>(qd, sq, items, wsd, ws);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_balance(const BalanceDesc* descs, const WorkItem* items, int nitems, char* ws, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    balance_kernel<<<nitems, 128, 0, st>>>(descs, items, ws);
+    return cudaGetLastError();
+}
+
+cudaError_t init_split_kernels(const int* host_tuv) {
+    cudaError_t e = cudaMemcpyToSymbol(g_tuv_split, host_tuv, sizeof(int) * NHERM_TOT);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+}
+
+cudaError_t launch_split_gemm(const SplitGemmDesc* probs, const WorkItem* items, int nitems, const char* ws,
+                              double* cbase, unsigned* status, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    split_gemm_kernel<<<nitems, 128, SMEM_BYTES, st>>>(probs, items, ws, cbase, status);
+    return cudaGetLastError();
+}
+
+}  // namespace lx

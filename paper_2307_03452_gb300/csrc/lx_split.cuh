@@ -1,0 +1,84 @@
+// Split-precision (Ozaki-style BF16 slices) GEMM: constants, descriptors and launchers.
+#pragma once
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "lx_internal.cuh"
+
+namespace lx {
+
+constexpr int SPLIT_NSLICE = 5;                      // digits per FP64 value
+constexpr int SPLIT_BETA = 8;                        // bits per digit
+constexpr int SPLIT_W = SPLIT_NSLICE * SPLIT_BETA;   // fixed-point bits kept (40)
+constexpr int SPLIT_KB = 32;                         // K block (elements) of one pipeline stage
+constexpr int SPLIT_TA = 128;                        // A row tile = MMA M
+constexpr int SPLIT_TB = 96;                         // B row tile = largest MMA N
+
+// One matrix whose rows are split: src at (double*)base + src_off, row stride ld.  Before
+// splitting, column k is multiplied by 2^(shift_sign * shift[k]) (exact; shift_off < 0: none).
+struct SplitRowsDesc {
+    int64_t src_off;    // doubles
+    int64_t dig_off;    // bytes from the workspace base
+    int64_t exp_off;    // bytes from the workspace base (int per padded row)
+    int64_t shift_off;  // bytes from the workspace base (int per column), or -1
+    int ld, rows, K, T, nkb, shift_sign;
+};
+
+// out[k] = largest FP64 exponent field in column k of a row-major matrix (0: column of zeros).
+struct ColMaxDesc {
+    int64_t src_off;  // doubles
+    int64_t out_off;  // bytes (int per column)
+    int ld, rows, K, pad;
+};
+
+// out[k] = floor((a[k] - b[k]) / 2) when both are nonzero, else 0: the power of two that
+// balances column k of one operand against row k of the other.
+struct BalanceDesc {
+    int64_t a_off, b_off, out_off;  // bytes (int arrays)
+    int K, pad;
+};
+
+// Per-quartet split operands of the two GEMMs.
+struct SplitQuartet {
+    int64_t a1_dig, a1_exp;  // [p|q]^T rows (Kket Nq), K = Kbra Np, columns scaled by 2^-e1
+    int64_t b1_dig, b1_exp;  // H_bra rows (nab), columns scaled by 2^e1
+    int64_t a2_dig, a2_exp;  // [ab|q] rows (nab), K = Kket Nq, columns scaled by 2^e2
+    int64_t b2_dig, b2_exp;  // H_ket rows (ncd), columns scaled by 2^-e2
+    int64_t rmr_off;         // int[Kbra Np]: row-max exponents of [p|q]
+    int64_t e1_off, e2_off;  // int[Kbra Np], int[Kket Nq]
+    int nkb1, nkb2;
+};
+
+// D = A B^T: A digits (row tiles of SPLIT_TA), B digits (row tiles of SPLIT_TB), both with nkb
+// K blocks; D written to (double*)C + c_off with row stride ldc (transpose: D[m][n] -> C[n][m]).
+struct SplitGemmDesc {
+    int64_t a_dig, a_exp, b_dig, b_exp;
+    int64_t c_off;
+    int M, N, nkb, ldc, transpose, pad;
+};
+
+__host__ __device__ inline int split_rowpad(int rows, int T) { return (rows + T - 1) / T * T; }
+__host__ __device__ inline int split_nkb(int K) { return (K + SPLIT_KB - 1) / SPLIT_KB; }
+// bytes of the digit planes of an operand (rows padded to T, K padded to SPLIT_KB)
+__host__ __device__ inline int64_t split_dig_bytes(int rows, int K, int T) {
+    return (int64_t)split_rowpad(rows, T) * split_nkb(K) * SPLIT_KB * SPLIT_NSLICE * 2;
+}
+
+cudaError_t init_split_kernels(const int* host_tuv);
+cudaError_t launch_split_rows(const SplitRowsDesc* descs, const WorkItem* items, int nitems, const double* src_base,
+                              char* ws, cudaStream_t st);
+cudaError_t launch_split_r(const DQuartet* qd, const SplitQuartet* sq, const WorkItem* items, int nitems,
+                           const double* wsd, char* ws, cudaStream_t st);
+// item = (desc, chunk of 128 columns)
+cudaError_t launch_colmax(const ColMaxDesc* descs, const WorkItem* items, int nitems, const double* src_base,
+                          char* ws, cudaStream_t st);
+// item = (quartet, chunk of 128 rows of [p|q])
+cudaError_t launch_rowmax_r(const DQuartet* qd, const SplitQuartet* sq, const WorkItem* items, int nitems,
+                            const double* wsd, char* ws, cudaStream_t st);
+// item = (desc, chunk of 128 entries)
+cudaError_t launch_balance(const BalanceDesc* descs, const WorkItem* items, int nitems, char* ws, cudaStream_t st);
+cudaError_t launch_split_gemm(const SplitGemmDesc* probs, const WorkItem* items, int nitems, const char* ws,
+                              double* cbase, unsigned* status, cudaStream_t st);
+
+}  // namespace lx

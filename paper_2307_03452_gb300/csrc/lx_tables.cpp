@@ -139,6 +139,44 @@ void make_boys_table(double* table) {
     }
 }
 
+void make_solid_classes(const double* coefs, SolidClassTab* tab) {
+    for (int l = 0; l <= LMAX; ++l) {
+        SolidClassTab& T = tab[l];
+        T = SolidClassTab{};
+        const int nc = ncart(l);
+        const double* C = coefs + solid_offset(l);
+        int key_of[NCART_MAX];
+        int keys[4], nk = 0;
+        int k = 0;
+        for (int i = 0; i <= l; ++i)
+            for (int j = 0; j <= i; ++j, ++k) {
+                const int ax = l - i, ay = i - j, az = j;
+                const int key = (ax & 1) | ((ay & 1) << 1) | ((az & 1) << 2);
+                int c = 0;
+                while (c < nk && keys[c] != key) ++c;
+                if (c == nk) keys[nk++] = key;
+                key_of[k] = c;
+                T.comp[c][T.na[c]++] = ax | (ay << 8) | (az << 16);
+            }
+        T.ncls = nk;
+        // each solid function's nonzero coefficients lie in exactly one class
+        for (int m = 0; m < 2 * l + 1; ++m) {
+            int cls = -1;
+            for (int q = 0; q < nc; ++q)
+                if (std::fabs(C[m * nc + q]) > 1e-14) cls = key_of[q];
+            const int jm = T.nm[cls]++;
+            T.mind[cls][jm] = m;
+            for (int ia = 0; ia < T.na[cls]; ++ia) {
+                // ordinal of the class member ia
+                int q = 0, seen = 0;
+                for (; q < nc; ++q)
+                    if (key_of[q] == cls && seen++ == ia) break;
+                T.c[cls][jm][ia] = C[m * nc + q];
+            }
+        }
+    }
+}
+
 void make_tuv_table(int* tuv) {
     for (int n = 0; n <= LTOT; ++n)
         for (int i = 0; i <= n; ++i)

@@ -32,9 +32,10 @@ _lib = None
 EXPORTS = sorted(["lx_eri_out_size", "lx_eri_workspace_size", "lx_eri_workspace_min", "lx_eri_batch",
                   "lx_eri_batch_static",
                   "lx_eri_sync_status", "lx_eri_stage_times", "lx_strerror", "lx_last_cuda_error", "lx_boys",
-                  "lx_hermite_R", "lx_hermite_H"])
+                  "lx_hermite_R", "lx_hermite_H", "lx_split_gemm"])
+LX_PATH_SPLIT = 0x2
 LX_TIME_STAGES = 0x200
-STAGES = ["norm", "pair_h", "boys_r", "gemm1", "gemm2"]
+STAGES = ["norm", "pair_h", "boys_r", "gemm1", "gemm2", "split"]
 
 
 class LxError(RuntimeError):
@@ -88,6 +89,8 @@ def load(build_if_missing: bool = True):
         lib.lx_hermite_R.restype = ctypes.c_int
         lib.lx_hermite_H.argtypes = [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_i32, c_i32, c_vp, c_i64, c_vp]
         lib.lx_hermite_H.restype = ctypes.c_int
+        lib.lx_split_gemm.argtypes = [c_i32, c_i32, c_i32, c_vp, c_i32, c_vp, c_i32, c_vp, c_i32, c_vp]
+        lib.lx_split_gemm.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -140,9 +143,12 @@ def _stream_ptr(stream) -> int | None:
 class Batch:
     """Host descriptors of one batch, packed once (the planner's input)."""
 
-    def __init__(self, basis: dict, quartets, solid: bool, out_off=None):
+    def __init__(self, basis: dict, quartets, solid: bool, out_off=None, path: str = "fp64"):
+        if path not in ("fp64", "split"):
+            raise ValueError(f"unknown path {path!r}")
         self.solid = bool(solid)
-        self.flags = LX_SOLID if solid else LX_CART
+        self.path = path
+        self.flags = (LX_SOLID if solid else LX_CART) | (LX_PATH_SPLIT if path == "split" else 0)
         self.shells = pack_shells(basis)
         self.exps = np.ascontiguousarray(basis["exps"], dtype=np.float64)
         self.coefs = np.ascontiguousarray(basis["coefs"], dtype=np.float64)
@@ -237,11 +243,13 @@ def alloc_workspace(nbytes: int, device="cuda"):
 
 
 def eri(basis: dict, quartets, solid: bool = True, device="cuda", workspace_limit: int | None = None,
-        stream=None):
+        stream=None, path: str = "fp64"):
     """Evaluate (ab|cd) for every quartet on the GPU; returns (out, out_offsets) with out a
-    float64 CUDA tensor holding each quartet's row-major (a,b,c,d) block."""
+    float64 CUDA tensor holding each quartet's row-major (a,b,c,d) block.  path "fp64" runs
+    every step in FP64; "split" runs the two transforms as BF16 slice products on the
+    tensor cores."""
     import torch
-    b = Batch(basis, quartets, solid)
+    b = Batch(basis, quartets, solid, path=path)
     need = b.workspace_size()
     if workspace_limit is not None:
         need = max(min(need, int(workspace_limit)), b.workspace_min())
@@ -250,6 +258,20 @@ def eri(basis: dict, quartets, solid: bool = True, device="cuda", workspace_limi
     b.run(out, ws, stream)
     sync_status(stream)
     return out[: b.out_size], b.quartets["out_offset"].copy()
+
+
+def split_gemm(A, B, stream=None):
+    """C = A @ B.T for float64 CUDA matrices through the split path's tensor-core kernels."""
+    import torch
+    A = A.contiguous()
+    B = B.contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.float64, device=A.device)
+    _check(load().lx_split_gemm(M, N, K, ctypes.c_void_p(A.data_ptr()), K, ctypes.c_void_p(B.data_ptr()), K,
+                                ctypes.c_void_p(C.data_ptr()), N, ctypes.c_void_p(_stream_ptr(stream))),
+           "lx_split_gemm")
+    return C
 
 
 def boys(mmax: int, T, stream=None):

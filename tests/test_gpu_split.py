@@ -1,0 +1,86 @@
+"""The split path: Ozaki-style BF16 slice products on the tcgen05 tensor cores.
+
+lx_split_gemm (C = A B^T) is checked first on integer-valued matrices whose split is exact,
+so the tensor-core result must equal the FP64 product bit for bit (this pins the operand
+layout, the descriptors and the recombination), then on random matrices against the
+error bound of 40-bit operands.  The ERI split path is checked against the oracle at the
+spec bound (max abs error 1e-10) on split-path classes."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_03452_gb300 import inputs, lx
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    torch.cuda.set_device(0)
+
+
+SHAPES = [(1, 1, 1), (128, 96, 32), (129, 97, 33), (300, 200, 455), (455, 169, 455), (64, 16, 1000), (7, 250, 70)]
+
+
+@pytest.mark.parametrize("M,N,K", SHAPES)
+def test_split_gemm_exact_on_integer_rows(M, N, K):
+    # rows: integers |x| < 2^12 times a per-row power of two -> 40-bit split is exact and every
+    # partial sum stays exact, so C must equal the FP64 product exactly
+    rng = np.random.default_rng(M * 1000 + N + K)
+    A = rng.integers(-4095, 4096, (M, K)).astype(np.float64) * np.exp2(rng.integers(-20, 20, (M, 1)))
+    B = rng.integers(-4095, 4096, (N, K)).astype(np.float64) * np.exp2(rng.integers(-20, 20, (N, 1)))
+    ref = A @ B.T
+    C = lx.split_gemm(torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda")).cpu().numpy()
+    assert np.array_equal(C, ref)
+
+
+@pytest.mark.parametrize("M,N,K", SHAPES)
+def test_split_gemm_random_within_bound(M, N, K):
+    # 40-bit operands and the dropped digit products (s + t >= 5): worst case
+    # |C - AB^T| <= K * 2^-36 * max_k|A_ik| * max_k|B_jk|
+    rng = np.random.default_rng(7 + M + N + K)
+    A = rng.normal(size=(M, K)) * np.exp(rng.uniform(-5, 5, (M, 1)))
+    B = rng.normal(size=(N, K)) * np.exp(rng.uniform(-5, 5, (N, 1)))
+    ref = A @ B.T
+    C = lx.split_gemm(torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda")).cpu().numpy()
+    bound = K * 2.0 ** -36 * np.outer(np.abs(A).max(1), np.abs(B).max(1))
+    assert np.all(np.abs(C - ref) <= bound)
+
+
+def _split_vs_oracle(basis, quartets, solid):
+    out, off = lx.eri(basis, quartets, solid=solid, path="split")
+    ref, roff = oracle.eri(basis, quartets, solid=solid)
+    got = out.cpu().numpy()
+    return got, ref, off
+
+
+@pytest.mark.parametrize("solid", [True, False])
+def test_eri_split_path_hhhh_iiii(solid):
+    # (hh|hh) and (ii|ii), K = 1..3 per shell, compact and far quartets: max abs error <= 1e-10
+    b1 = inputs.uniform_class((5, 5, 5, 5), 4, 91, cube=3.0, exps=(0.05, 20.0), kmin=1, kmax=2)
+    b2 = inputs.uniform_class((6, 6, 6, 6), 3, 92, cube=3.0, exps=(0.05, 20.0), kmin=1, kmax=2)
+    b3 = inputs.uniform_class((5, 5, 5, 5), 2, 93, cube=20.0, exps=(0.05, 20.0), kmin=1, kmax=3)
+    basis, quartets = inputs.concat([b1, b2, b3])
+    got, ref, _ = _split_vs_oracle(basis, quartets, solid)
+    assert np.all(np.isfinite(got))
+    assert np.abs(got - ref).max() <= 1e-10, f"max abs err {np.abs(got - ref).max():.3e}"
+
+
+def test_eri_split_path_mixed_and_low_l():
+    # every class the library accepts goes through the split path too
+    mixed = inputs.mixed_classes(8, seed=94, kmin=1, kmax=2, cube=4.0)
+    low = inputs.uniform_class((1, 0, 2, 3), 5, 95, cube=3.0, exps=(0.1, 10.0), kmin=1, kmax=3)
+    basis, quartets = inputs.concat([mixed, low])
+    got, ref, _ = _split_vs_oracle(basis, quartets, True)
+    assert np.abs(got - ref).max() <= 1e-10
+
+
+def test_split_and_fp64_paths_agree_on_full_size_iiii():
+    # the 4096-quartet (ii|ii) workload: split path vs the FP64 path, max abs difference
+    basis, quartets = inputs.iiii_fp64()
+    a, _ = lx.eri(basis, quartets, solid=True, path="fp64")
+    b, _ = lx.eri(basis, quartets, solid=True, path="split")
+    assert float((a - b).abs().max()) <= 1e-10
