@@ -42,6 +42,7 @@ def parse_args(argv=None):
     p.add_argument("--nquartet", type=int, default=4096)
     p.add_argument("--no-cart", action="store_true", help="skip the Cartesian-output measurement")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-split", action="store_true", help="skip the split-precision measurement")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
     return p.parse_args(argv)
 
@@ -211,6 +212,14 @@ def time_steps(torch, lx, batch, out, ws, steps, warmup, flush_buf, world):
     return step_ms, stage_ms, launches
 
 
+def _measured_bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0  # fallback figure for a GB300 when the measured file is absent
+
+
 def cpu_baseline(basis, quartets, solid, seconds):
     """The oracle as it stands, on the host cores, on a bounded prefix of the workload."""
     import numpy as np
@@ -311,6 +320,35 @@ def main(argv=None):
     del ws
     torch.cuda.empty_cache()
 
+    # ---- split-precision path on the same batch (BF16 slices on the tensor cores)
+    split = None
+    if not args.no_split:
+        bsp = lx.Batch(basis, quartets, solid=True, path="split")
+        outs = torch.empty(bsp.out_size, dtype=torch.float64, device="cuda")
+        wss = lx.alloc_workspace(bsp.workspace_size())
+        sms, sstage, slaunch = time_steps(torch, lx, bsp, outs, wss, args.steps, args.warmup, flush_buf, world)
+        stot = reduce_max(sum(sms), world)
+        maxdiff = float((outs - out).abs().max())
+        # roofline of the dominant tensor-core kernel of the split path
+        sdom = max(("gemm1", "gemm2"), key=lambda k: sstage[k])
+        # tensor work actually asked of the tensor cores: 15 digit products of the useful sizes
+        tens = {"gemm1": 15 * g1, "gemm2": 15 * g2}.get(sdom)
+        sper = sstage[sdom] / max(1, slaunch[sdom])
+        bf16_peak = _measured_bf16_peak()
+        sroof = {"bound": "tensor", "kernel": f"split_{sdom}", "unit": "TFLOP/s",
+                 "achieved": (tens / (sper * 1e-3) / 1e12) if tens else None, "peak": bf16_peak,
+                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured", "traffic": None}
+        sroof["frac"] = sroof["achieved"] / bf16_peak if sroof["achieved"] and bf16_peak else None
+        split = {"quartets_per_s": world * nq * args.steps / (stot * 1e-3), "ms_per_step": stot / args.steps,
+                 "fp64_equiv_tflops": world * (g1 + g2) * args.steps / (stot * 1e-3) / 1e12,
+                 "max_abs_diff_vs_fp64_path": maxdiff, "speedup_vs_fp64_path": (total_ms / stot),
+                 "stage_ms_per_step": {k: v / args.steps for k, v in sstage.items()},
+                 "gpu_launches": int(sum(slaunch.values())), "roofline": sroof,
+                 "scheme": "5 BF16 digits of 8 bits per FP64 value, per-row powers of two, power-of-two "
+                           "balancing along the reduction index, 15 digit products, exact int64 recombination"}
+        del wss, outs
+        torch.cuda.empty_cache()
+
     # ---- end to end through the public API: pinned host descriptors in, result out to pinned host
     e2e = None
     if not args.no_e2e:
@@ -373,6 +411,7 @@ def main(argv=None):
             "fp64_equiv_tflops": fp64_tf, "integrals_per_s": world * nint * args.steps / (total_ms * 1e-3),
             "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
             "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "cartesian": cart,
+            "split": split,
             "gpu_launches": int(sum(launches.values())),
         }
         print(json.dumps(line), flush=True)

@@ -62,6 +62,47 @@ __global__ void norm_kernel(const DShell* __restrict__ sh, int nshell, const dou
     for (int i = 0; i < K; ++i) ncoef[o + i] = coefs[o + i] * prim_norm(l, exps[o + i]) * sc;
 }
 
+// Solid fold of one (class of a, class of b, p) item with exactly NMA x NMB solid functions:
+// for each a of the class, u[jb] = sum_b C_b[jb][b] E_ab^p over the class of b (the E product
+// formed once per b), then acc[ja][jb] += C_a[ja][a] u[jb].  The class sizes are template
+// arguments so that no padded FP64 operation is issued.
+template <int NMA, int NMB>
+__device__ inline void fold_item(const SolidClassTab& TA, const SolidClassTab& TB, int ca, int cb, int px, int py,
+                                 int pz, const double* Ex, const double* Ey, const double* Ez, int sb1, int nt,
+                                 double (&out)[SC_MAXM][SC_MAXM]) {
+    double acc[NMA][NMB];
+#pragma unroll
+    for (int x = 0; x < NMA; ++x)
+#pragma unroll
+        for (int y = 0; y < NMB; ++y) acc[x][y] = 0.0;
+    const int na = TA.na[ca], nb = TB.na[cb];
+    for (int ia = 0; ia < na; ++ia) {
+        const int ac = TA.comp[ca][ia];
+        const double* ex = Ex + ((ac & 255) * sb1) * nt + px;
+        const double* ey = Ey + (((ac >> 8) & 255) * sb1) * nt + py;
+        const double* ez = Ez + ((ac >> 16) * sb1) * nt + pz;
+        double u[NMB];
+#pragma unroll
+        for (int y = 0; y < NMB; ++y) u[y] = 0.0;
+        for (int ib = 0; ib < nb; ++ib) {
+            const int bc = TB.comp[cb][ib];
+            const double v = ex[(bc & 255) * nt] * ey[((bc >> 8) & 255) * nt] * ez[(bc >> 16) * nt];
+#pragma unroll
+            for (int y = 0; y < NMB; ++y) u[y] += TB.c[cb][y][ib] * v;
+        }
+#pragma unroll
+        for (int x = 0; x < NMA; ++x) {
+            const double c = TA.c[ca][x][ia];
+#pragma unroll
+            for (int y = 0; y < NMB; ++y) acc[x][y] += c * u[y];
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < NMA; ++x)
+#pragma unroll
+        for (int y = 0; y < NMB; ++y) out[x][y] = acc[x][y];
+}
+
 constexpr int PAIR_THREADS = 128;
 constexpr int ETAB = (LMAX + 1) * (LMAX + 1) * (2 * LMAX + 1);  // 637 per direction
 
@@ -179,40 +220,18 @@ __global__ void __launch_bounds__(PAIR_THREADS) pair_h_kernel(const DPair* __res
             const int ca = g / ncb_cls, cb = g - ca * ncb_cls;
             const int tuv = g_tuv_prep[p];
             const int px = tuv & 255, py = (tuv >> 8) & 255, pz = tuv >> 16;
-            const int na = TA.na[ca], nma = TA.nm[ca], nb = TB.na[cb], nmb = TB.nm[cb];
+            const int nma = TA.nm[ca], nmb = TB.nm[cb];
             double acc[SC_MAXM][SC_MAXM];
-#pragma unroll
-            for (int x = 0; x < SC_MAXM; ++x)
-#pragma unroll
-                for (int y = 0; y < SC_MAXM; ++y) acc[x][y] = 0.0;
-            for (int ia = 0; ia < na; ++ia) {
-                const int ac = TA.comp[ca][ia];
-                const int ax = ac & 255, ay = (ac >> 8) & 255, az = ac >> 16;
-                const double* ex = Ex + (ax * sb1) * nt + px;
-                const double* ey = Ey + (ay * sb1) * nt + py;
-                const double* ez = Ez + (az * sb1) * nt + pz;
-                double v[SC_MAXA];
-#pragma unroll
-                for (int ib = 0; ib < SC_MAXA; ++ib) {
-                    v[ib] = 0.0;
-                    if (ib < nb) {
-                        const int bc = TB.comp[cb][ib];
-                        v[ib] = ex[(bc & 255) * nt] * ey[((bc >> 8) & 255) * nt] * ez[(bc >> 16) * nt];
-                    }
-                }
-#pragma unroll
-                for (int jb = 0; jb < SC_MAXM; ++jb) {
-                    if (jb < nmb) {
-                        double u = 0.0;
-#pragma unroll
-                        for (int ib = 0; ib < SC_MAXA; ++ib)
-                            if (ib < nb) u += TB.c[cb][jb][ib] * v[ib];
-#pragma unroll
-                        for (int ja = 0; ja < SC_MAXM; ++ja)
-                            if (ja < nma) acc[ja][jb] += TA.c[ca][ja][ia] * u;
-                    }
-                }
+#define LX_FOLD(A, B) \
+    case (A) * 8 + (B): fold_item<A, B>(TA, TB, ca, cb, px, py, pz, Ex, Ey, Ez, sb1, nt, acc); break;
+            switch (nma * 8 + nmb) {
+                LX_FOLD(1, 1) LX_FOLD(1, 2) LX_FOLD(1, 3) LX_FOLD(1, 4)
+                LX_FOLD(2, 1) LX_FOLD(2, 2) LX_FOLD(2, 3) LX_FOLD(2, 4)
+                LX_FOLD(3, 1) LX_FOLD(3, 2) LX_FOLD(3, 3) LX_FOLD(3, 4)
+                LX_FOLD(4, 1) LX_FOLD(4, 2) LX_FOLD(4, 3) LX_FOLD(4, 4)
+                default: break;
             }
+#undef LX_FOLD
             const double sg = (pr.sign && ((px + py + pz) & 1)) ? -pref : pref;
 #pragma unroll
             for (int ja = 0; ja < SC_MAXM; ++ja)

@@ -171,6 +171,27 @@ __device__ inline void digits_of(long long q, float (&d)[SPLIT_NSLICE]) {
     d[SPLIT_NSLICE - 1] = (float)(int)q;
 }
 
+// Digits of 8 consecutive values (k0 .. k0+7, k0 a multiple of 8) of one row, written as one
+// 16-byte store per slice (one row of a core matrix).
+__device__ inline int64_t dig_index(int row, int k, int s, int T, int nkb);
+__device__ inline void store_digit_group(__nv_bfloat16* dig, int row, int k0, int T, int nkb,
+                                         const long long (&q)[8]) {
+    float d[8][SPLIT_NSLICE];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) digits_of(q[j], d[j]);
+#pragma unroll
+    for (int s = 0; s < SPLIT_NSLICE; ++s) {
+        uint4 w;
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(d[0][s], d[1][s]), h1 = __floats2bfloat162_rn(d[2][s], d[3][s]),
+                       h2 = __floats2bfloat162_rn(d[4][s], d[5][s]), h3 = __floats2bfloat162_rn(d[6][s], d[7][s]);
+        w.x = *reinterpret_cast<unsigned*>(&h0);
+        w.y = *reinterpret_cast<unsigned*>(&h1);
+        w.z = *reinterpret_cast<unsigned*>(&h2);
+        w.w = *reinterpret_cast<unsigned*>(&h3);
+        *reinterpret_cast<uint4*>(dig + dig_index(row, k0, s, T, nkb)) = w;
+    }
+}
+
 // Offset (in BF16 elements) of element (row, k) of slice s inside an operand stored as
 // row tiles of T rows and K blocks of SPLIT_KB: block (rt, kb) holds NSLICE slice-blocks of
 // T x KB elements, each in core matrices (8 rows x 8 elements) ordered (row/8, k/8).
@@ -199,13 +220,15 @@ __global__ void split_rows_kernel(const SplitRowsDesc* __restrict__ descs, const
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = mx > 0 ? mx - 1022 : 0;  // |x| < 2^e over the row
     __nv_bfloat16* dig = reinterpret_cast<__nv_bfloat16*>(ws + d.dig_off);
-    const int kpad = d.nkb * SPLIT_KB;
-    for (int k = lane; k < kpad; k += 32) {
-        const double x = (live && k < d.K) ? value(k) : 0.0;
-        float dg[SPLIT_NSLICE];
-        digits_of(mx > 0 ? fixed_of(x, e) : 0ll, dg);
+    const int ngroup = d.nkb * SPLIT_KB / 8;
+    for (int g = lane; g < ngroup; g += 32) {
+        long long q[8];
 #pragma unroll
-        for (int s = 0; s < SPLIT_NSLICE; ++s) dig[dig_index(row, k, s, d.T, d.nkb)] = __float2bfloat16_rn(dg[s]);
+        for (int j = 0; j < 8; ++j) {
+            const int k = 8 * g + j;
+            q[j] = (mx > 0 && live && k < d.K) ? fixed_of(value(k), e) : 0ll;
+        }
+        store_digit_group(dig, row, 8 * g, d.T, d.nkb, q);
     }
     if (lane == 0) reinterpret_cast<int*>(ws + d.exp_off)[row] = e;
 }
@@ -243,13 +266,15 @@ __global__ void split_r_kernel(const DQuartet* __restrict__ qd, const SplitQuart
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = mx > 0 ? mx - 1022 : 0;
     __nv_bfloat16* dig = reinterpret_cast<__nv_bfloat16*>(ws + s.a1_dig);
-    const int kpad = s.nkb1 * SPLIT_KB;
-    for (int k = lane; k < kpad; k += 32) {
-        const double x = (live && k < K) ? value(k) : 0.0;
-        float dg[SPLIT_NSLICE];
-        digits_of(mx > 0 ? fixed_of(x, e) : 0ll, dg);
+    const int ngroup = s.nkb1 * SPLIT_KB / 8;
+    for (int g = lane; g < ngroup; g += 32) {
+        long long qv[8];
 #pragma unroll
-        for (int t = 0; t < SPLIT_NSLICE; ++t) dig[dig_index(row, k, t, SPLIT_TA, s.nkb1)] = __float2bfloat16_rn(dg[t]);
+        for (int j = 0; j < 8; ++j) {
+            const int k = 8 * g + j;
+            qv[j] = (mx > 0 && live && k < K) ? fixed_of(value(k), e) : 0ll;
+        }
+        store_digit_group(dig, row, 8 * g, SPLIT_TA, s.nkb1, qv);
     }
     if (lane == 0) reinterpret_cast<int*>(ws + s.a1_exp)[row] = e;
 }
