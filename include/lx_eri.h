@@ -63,9 +63,9 @@ typedef struct {
 #define LX_SOLID 0x1       /* real solid-harmonic output, 2l+1 per shell */
 #define LX_PATH_FP64 0x0   /* every step in FP64 */
 #define LX_PATH_SPLIT 0x2  /* the two Hermite transforms as Ozaki-style BF16 slice products on the
-                              tensor cores (FP32 accumulation, exact integer recombination);
-                              Boys, [r]^(m), E and H stay FP64.  Error ~5e-11 of each quartet's
-                              largest integral */
+                              tensor cores (FP32 accumulation, integer recombination); Boys,
+                              [r]^(m), E and H stay FP64.  Operands carry 48 bits; the absolute
+                              error grows with the magnitude of a quartet's intermediates */
 #define LX_TIME_STAGES 0x200 /* record CUDA events around each stage (see lx_eri_stage_times) */
 
 /* stages timed with LX_TIME_STAGES */
@@ -211,12 +211,52 @@ int lx_hermite_H(const lx_shell* shells, int32_t nshell, const double* exps, con
  * C = A B^T through the split path's kernels (the same splitting and tensor-core GEMM that
  * LX_PATH_SPLIT uses for Eq. make-abq / Eq. make-abcd): A is M x K, B is N x K, both FP64
  * row-major in DEVICE memory with row strides lda, ldb; C is M x N FP64 row-major, stride ldc.
- * Each row of A and of B is scaled by its own power of two and split into 5 BF16 digits of
- * 8 bits; the 15 digit products with s + t <= 4 are summed exactly.  Scratch for the digit
+ * Each row of A and of B is scaled by its own power of two and split into 6 BF16 digits of
+ * 8 bits; the 21 digit products with s + t <= 5 are summed.  Scratch for the digit
  * planes is taken from the stream-ordered allocator.  M, N, K >= 1, K <= 1 << 20.
  */
 int lx_split_gemm(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda, const double* B, int32_t ldb,
                   double* C, int32_t ldc, void* cuda_stream);
+
+/* ---------------------------------------------------------------- learned router
+ * A small MLP predicts, per quartet, log10 of its largest |integral| from shell descriptors;
+ * the caller routes quartets predicted large to LX_PATH_FP64 and the rest to LX_PATH_SPLIT,
+ * whose absolute error grows with the integrals' magnitude.  The paper has no such part.
+ * Network: LX_MLP_NIN inputs -> 64 -> 64 -> 1, ReLU, parameters packed as W1[64][20], b1[64],
+ * W2[64][64], b2[64], W3[64], b3; the forward pass uses FP16 weights. */
+#define LX_MLP_NIN 20
+#define LX_MLP_WIDTH 64
+#define LX_MLP_NPARAM (LX_MLP_WIDTH * LX_MLP_NIN + LX_MLP_WIDTH + LX_MLP_WIDTH * LX_MLP_WIDTH + LX_MLP_WIDTH + \
+                       LX_MLP_WIDTH + 1)
+
+/*
+ * Router features of each quartet: feat[q * LX_MLP_NIN + k] (DEVICE, float).  Descriptors are
+ * HOST arrays as for lx_eri_batch (coefficients are not needed).  Features: l / 6 of each
+ * shell; ln of the smallest and largest exponent of each shell / 4; |AB|, |CD| / 10; the
+ * distance of the most diffuse product centers / 30; mu |AB|^2 and nu |CD|^2 of the most
+ * diffuse primitives / 20; ln(1 + rho |PQ|^2) / 3; ln(Ka Kb Kc Kd) / 6; log10 of an
+ * (ss|ss)-type magnitude estimate / 10.  Scratch comes from the stream-ordered allocator.
+ */
+int lx_route_features(const lx_shell* shells, int32_t nshell, const double* exps, int32_t nprim_total,
+                      const lx_quartet* quartets, int64_t nquartet, float* feat, void* cuda_stream);
+
+/* Inference: out[i] = MLP(feat[i]) with FP16 parameters params_f16 (DEVICE, LX_MLP_NPARAM halves). */
+int lx_mlp_forward(const void* params_f16, const float* feat, int64_t n, float* out, void* cuda_stream);
+
+/*
+ * Training gradient: loss[0] = mean over i < n of (MLP(feat[i]) - target[i])^2, evaluated with
+ * the FP16-rounded params, and grad = its gradient with respect to params (straight through
+ * the rounding).  All DEVICE float arrays; grad and loss are overwritten.
+ */
+int lx_mlp_grad(const float* params, const float* feat, const float* target, int64_t n, float* grad, float* loss,
+                void* cuda_stream);
+
+/*
+ * One Adam step (step counts from 1) on params with moments m, v (DEVICE, LX_MLP_NPARAM floats
+ * each) from grad, which is then cleared; params_f16 receives the rounded parameters.
+ */
+int lx_mlp_adam(float* params, float* m, float* v, float* grad, void* params_f16, int32_t step, float lr,
+                float beta1, float beta2, float eps, void* cuda_stream);
 
 #ifdef __cplusplus
 }

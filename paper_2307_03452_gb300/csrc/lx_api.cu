@@ -95,6 +95,7 @@ int ensure_device(unsigned** status) {
         if ((e = init_prep_tables(solid.data(), tuv.data(), cls.data())) != cudaSuccess) return cuda_fail(e);
         if ((e = init_tuv_table(tuv.data())) != cudaSuccess) return cuda_fail(e);
         if ((e = init_split_kernels(tuv.data())) != cudaSuccess) return cuda_fail(e);
+        if ((e = init_router_kernels()) != cudaSuccess) return cuda_fail(e);
         void* p = nullptr;
         if ((e = cudaGetSymbolAddress(&p, g_status_word)) != cudaSuccess) return cuda_fail(e);
         const unsigned zero = 0;
@@ -916,6 +917,76 @@ int lx_split_gemm(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda,
         return cuda_fail(e);
     if ((e = cudaFreeAsync(scratch, st)) != cudaSuccess) return cuda_fail(e);
     return LX_OK;
+}
+
+int lx_route_features(const lx_shell* shells, int32_t nshell, const double* exps, int32_t nprim_total,
+                      const lx_quartet* quartets, int64_t nquartet, float* feat, void* cuda_stream) {
+    // coefficients are not used: pass the exponents twice to reuse the validation
+    int v = validate(shells, nshell, exps, exps, nprim_total, quartets, nquartet, 0, true);
+    if (v != LX_OK) return v;
+    if (nquartet == 0) return LX_OK;
+    if (!feat) return LX_ERR_NULL;
+    unsigned* status = nullptr;
+    if ((v = ensure_device(&status)) != LX_OK) return v;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const size_t o_sh = 0, o_ex = align256(sizeof(DShell) * (size_t)nshell);
+    const size_t o_q = o_ex + align256(8 * (size_t)nprim_total), total = o_q + align256(16 * (size_t)nquartet);
+    std::vector<char> blob(total, 0);
+    DShell* dsh = reinterpret_cast<DShell*>(blob.data() + o_sh);
+    for (int32_t s = 0; s < nshell; ++s) {
+        dsh[s].l = shells[s].l;
+        dsh[s].K = shells[s].nprim;
+        dsh[s].prim_off = shells[s].prim_offset;
+        for (int k = 0; k < 3; ++k) dsh[s].A[k] = shells[s].center[k];
+    }
+    std::memcpy(blob.data() + o_ex, exps, 8 * (size_t)nprim_total);
+    int* q4 = reinterpret_cast<int*>(blob.data() + o_q);
+    for (int64_t i = 0; i < nquartet; ++i)
+        for (int k = 0; k < 4; ++k) q4[4 * i + k] = quartets[i].s[k];
+    char* scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), total, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemcpyAsync(scratch, blob.data(), total, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = launch_features(reinterpret_cast<const DShell*>(scratch + o_sh),
+                             reinterpret_cast<const double*>(scratch + o_ex), reinterpret_cast<const int*>(scratch + o_q),
+                             nquartet, feat, st)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaFreeAsync(scratch, st)) != cudaSuccess) return cuda_fail(e);
+    return LX_OK;
+}
+
+int lx_mlp_forward(const void* params_f16, const float* feat, int64_t n, float* out, void* cuda_stream) {
+    if (n < 0) return LX_ERR_SIZE;
+    if (n > 0 && (!params_f16 || !feat || !out)) return LX_ERR_NULL;
+    unsigned* status = nullptr;
+    int v = ensure_device(&status);
+    if (v != LX_OK) return v;
+    cudaError_t e = launch_mlp_forward(params_f16, feat, n, out, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? LX_OK : cuda_fail(e);
+}
+
+int lx_mlp_grad(const float* params, const float* feat, const float* target, int64_t n, float* grad, float* loss,
+                void* cuda_stream) {
+    if (n < 0) return LX_ERR_SIZE;
+    if (!params || !grad || !loss || (n > 0 && (!feat || !target))) return LX_ERR_NULL;
+    unsigned* status = nullptr;
+    int v = ensure_device(&status);
+    if (v != LX_OK) return v;
+    cudaError_t e = launch_mlp_grad(params, feat, target, n, grad, loss, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? LX_OK : cuda_fail(e);
+}
+
+int lx_mlp_adam(float* params, float* m, float* v, float* grad, void* params_f16, int32_t step, float lr, float beta1,
+                float beta2, float eps, void* cuda_stream) {
+    if (step < 1) return LX_ERR_SIZE;
+    if (!params || !m || !v || !grad || !params_f16) return LX_ERR_NULL;
+    unsigned* status = nullptr;
+    int rc = ensure_device(&status);
+    if (rc != LX_OK) return rc;
+    cudaError_t e = launch_mlp_adam(params, m, v, grad, params_f16, step, lr, beta1, beta2, eps,
+                                    static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? LX_OK : cuda_fail(e);
 }
 
 }  // extern "C"

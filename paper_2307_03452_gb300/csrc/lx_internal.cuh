@@ -90,6 +90,16 @@ cudaError_t launch_gemm2(const DQuartet* qd, const DPair* pairs, const WorkItem*
 cudaError_t launch_boys(int mmax, const double* T, int64_t n, double* F, unsigned* status, cudaStream_t st);
 cudaError_t launch_hermite_r(int L, const double* params, int64_t n, double* R, unsigned* status, cudaStream_t st);
 
+// Router (lx_router.cu).
+cudaError_t init_router_kernels();
+cudaError_t launch_features(const DShell* sh, const double* exps, const int* q4, int64_t nq, float* feat,
+                            cudaStream_t st);
+cudaError_t launch_mlp_forward(const void* p16, const float* feat, int64_t n, float* out, cudaStream_t st);
+cudaError_t launch_mlp_grad(const float* params, const float* feat, const float* target, int64_t n, float* grad,
+                            float* loss, cudaStream_t st);
+cudaError_t launch_mlp_adam(float* params, float* m, float* v, float* grad, void* p16, int step, float lr, float b1,
+                            float b2, float eps, cudaStream_t st);
+
 // GEMM tiling (shared by the planner and the kernels).
 constexpr int GEMM_BM = 32;
 constexpr int GEMM_BN = 64;

@@ -9,15 +9,16 @@
 // and each inner sum is a sum of integer products whose magnitude stays far below 2^24,
 // so the FP32 accumulators of the tensor core hold it exactly.  Products with
 // s + t <= NSLICE - 1 are kept; each diagonal d = s + t has its own TMEM accumulator, and the
-// epilogue combines the diagonals in 64-bit integer arithmetic (exact) before a single
-// conversion to FP64.  FP64 arithmetic, which is scarce on this GPU, is used for none of it:
+// epilogue combines the diagonals in 64-bit integer arithmetic before a single conversion to
+// FP64 (exact except for the lowest BETA bits of the last diagonal, which are rounded off to
+// keep the sum clear of 64-bit overflow).  FP64 arithmetic, which is scarce on this GPU, is used for none of it:
 // the splitting works on the bit patterns of the FP64 inputs.
 //
 // Kernels:
 //   split_rows_kernel  FP64 row-major matrix rows -> digit planes + row exponents
 //   split_r_kernel     rows q of the [p|q] operand gathered from [r]^(0) -> digit planes
-//   split_gemm_kernel  D = A B^T on tcgen05 (M tile 128, N tile <= 96, K blocks of 32),
-//                      operand blocks streamed by bulk TMA copies into a 3-stage mbarrier
+//   split_gemm_kernel  D = A B^T on tcgen05 (M tile 128, N tile <= 80, K blocks of 32),
+//                      operand blocks streamed by bulk TMA copies into a 2-stage mbarrier
 //                      pipeline, one thread issuing the MMAs, all four warps in the epilogue.
 #include <cstdint>
 
@@ -324,7 +325,7 @@ __global__ void balance_kernel(const BalanceDesc* __restrict__ descs, const Work
 
 // ------------------------------------------------------------------ tcgen05 GEMM
 
-constexpr int STAGES = 3;
+constexpr int STAGES = 2;
 constexpr int A_BLOCK = SPLIT_NSLICE * SPLIT_TA * SPLIT_KB * 2;  // bytes of one A block (all slices)
 constexpr int B_BLOCK = SPLIT_NSLICE * SPLIT_TB * SPLIT_KB * 2;
 constexpr int A_SLICE = SPLIT_TA * SPLIT_KB * 2;
@@ -472,17 +473,23 @@ __global__ void __launch_bounds__(128, 1) split_gemm_kernel(const SplitGemmDesc*
                 uint32_t r[16];
                 tmem_ld16(lane_base + dg * SPLIT_TB + c0, r);
                 tmem_ld_wait();
-                const int sh = SPLIT_BETA * (SPLIT_NSLICE - 1 - dg);
+                // acc = sum_d G_d 2^(BETA (NSLICE-2-d)); the last diagonal is rounded down BETA bits
 #pragma unroll
-                for (int j = 0; j < 16; ++j) acc[j] += (long long)__float2int_rn(__uint_as_float(r[j])) << sh;
+                for (int j = 0; j < 16; ++j) {
+                    const long long g = (long long)__float2int_rn(__uint_as_float(r[j]));
+                    if (dg < SPLIT_NSLICE - 1)
+                        acc[j] += g << (SPLIT_BETA * (SPLIT_NSLICE - 2 - dg));
+                    else
+                        acc[j] += (g + (1ll << (SPLIT_BETA - 1))) >> SPLIT_BETA;
+                }
             }
             if (rlive) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int col = n0 + c0 + j;
                     if (col < P.N) {
-                        // D = 2^(eA + eB - 2W + BETA (NSLICE-1)) * acc
-                        const int scale = ea + eb_tab[col] - 2 * SPLIT_W + SPLIT_BETA * (SPLIT_NSLICE - 1);
+                        // D = 2^(eA + eB - 2W + BETA NSLICE) * acc
+                        const int scale = ea + eb_tab[col] - 2 * SPLIT_W + SPLIT_BETA * SPLIT_NSLICE;
                         const double v = i64_to_f64_scaled(acc[j], scale);
                         if (P.transpose)
                             cbase[P.c_off + (int64_t)col * P.ldc + row] = v;

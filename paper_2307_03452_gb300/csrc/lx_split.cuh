@@ -8,12 +8,12 @@
 
 namespace lx {
 
-constexpr int SPLIT_NSLICE = 5;                      // digits per FP64 value
+constexpr int SPLIT_NSLICE = 6;                      // digits per FP64 value
 constexpr int SPLIT_BETA = 8;                        // bits per digit
-constexpr int SPLIT_W = SPLIT_NSLICE * SPLIT_BETA;   // fixed-point bits kept (40)
+constexpr int SPLIT_W = SPLIT_NSLICE * SPLIT_BETA;   // fixed-point bits kept (48)
 constexpr int SPLIT_KB = 32;                         // K block (elements) of one pipeline stage
 constexpr int SPLIT_TA = 128;                        // A row tile = MMA M
-constexpr int SPLIT_TB = 96;                         // B row tile = largest MMA N
+constexpr int SPLIT_TB = 80;                         // B row tile = largest MMA N (6 x 80 TMEM columns)
 
 // One matrix whose rows are split: src at (double*)base + src_off, row stride ld.  Before
 // splitting, column k is multiplied by 2^(shift_sign * shift[k]) (exact; shift_off < 0: none).

@@ -32,7 +32,11 @@ _lib = None
 EXPORTS = sorted(["lx_eri_out_size", "lx_eri_workspace_size", "lx_eri_workspace_min", "lx_eri_batch",
                   "lx_eri_batch_static",
                   "lx_eri_sync_status", "lx_eri_stage_times", "lx_strerror", "lx_last_cuda_error", "lx_boys",
-                  "lx_hermite_R", "lx_hermite_H", "lx_split_gemm"])
+                  "lx_hermite_R", "lx_hermite_H", "lx_split_gemm", "lx_route_features", "lx_mlp_forward",
+                  "lx_mlp_grad", "lx_mlp_adam"])
+MLP_NIN = 20
+MLP_WIDTH = 64
+MLP_NPARAM = MLP_WIDTH * MLP_NIN + MLP_WIDTH + MLP_WIDTH * MLP_WIDTH + MLP_WIDTH + MLP_WIDTH + 1
 LX_PATH_SPLIT = 0x2
 LX_TIME_STAGES = 0x200
 STAGES = ["norm", "pair_h", "boys_r", "gemm1", "gemm2", "split"]
@@ -91,6 +95,15 @@ def load(build_if_missing: bool = True):
         lib.lx_hermite_H.restype = ctypes.c_int
         lib.lx_split_gemm.argtypes = [c_i32, c_i32, c_i32, c_vp, c_i32, c_vp, c_i32, c_vp, c_i32, c_vp]
         lib.lx_split_gemm.restype = ctypes.c_int
+        lib.lx_route_features.argtypes = [c_vp, c_i32, c_vp, c_i32, c_vp, c_i64, c_vp, c_vp]
+        lib.lx_route_features.restype = ctypes.c_int
+        lib.lx_mlp_forward.argtypes = [c_vp, c_vp, c_i64, c_vp, c_vp]
+        lib.lx_mlp_forward.restype = ctypes.c_int
+        lib.lx_mlp_grad.argtypes = [c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]
+        lib.lx_mlp_grad.restype = ctypes.c_int
+        c_f32 = ctypes.c_float
+        lib.lx_mlp_adam.argtypes = [c_vp, c_vp, c_vp, c_vp, c_vp, c_i32, c_f32, c_f32, c_f32, c_f32, c_vp]
+        lib.lx_mlp_adam.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -272,6 +285,46 @@ def split_gemm(A, B, stream=None):
                                 ctypes.c_void_p(C.data_ptr()), N, ctypes.c_void_p(_stream_ptr(stream))),
            "lx_split_gemm")
     return C
+
+
+def route_features(basis: dict, quartets, device="cuda", stream=None):
+    """Router features (nq, MLP_NIN) float32 CUDA tensor (lx_route_features)."""
+    import torch
+    sh = pack_shells(basis)
+    ex = np.ascontiguousarray(basis["exps"], dtype=np.float64)
+    q, _ = pack_quartets(basis, quartets, True)
+    feat = torch.empty((len(q), MLP_NIN), dtype=torch.float32, device=device)
+    _check(load().lx_route_features(_ptr(sh), len(sh), _ptr(ex), len(ex), _ptr(q), len(q),
+                                    ctypes.c_void_p(feat.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+           "lx_route_features")
+    return feat
+
+
+def mlp_forward(params_f16, feat, stream=None):
+    import torch
+    out = torch.empty(feat.shape[0], dtype=torch.float32, device=feat.device)
+    _check(load().lx_mlp_forward(ctypes.c_void_p(params_f16.data_ptr()), ctypes.c_void_p(feat.data_ptr()),
+                                 feat.shape[0], ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
+           "lx_mlp_forward")
+    return out
+
+
+def mlp_grad(params, feat, target, stream=None):
+    """(loss, grad) of the mean squared error, forward with FP16-rounded params."""
+    import torch
+    grad = torch.empty(MLP_NPARAM, dtype=torch.float32, device=params.device)
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    _check(load().lx_mlp_grad(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(feat.data_ptr()),
+                              ctypes.c_void_p(target.data_ptr()), feat.shape[0], ctypes.c_void_p(grad.data_ptr()),
+                              ctypes.c_void_p(loss.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))), "lx_mlp_grad")
+    return loss, grad
+
+
+def mlp_adam(params, m, v, grad, params_f16, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().lx_mlp_adam(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(m.data_ptr()),
+                              ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
+                              ctypes.c_void_p(params_f16.data_ptr()), int(step), float(lr), float(beta1), float(beta2),
+                              float(eps), ctypes.c_void_p(_stream_ptr(stream))), "lx_mlp_adam")
 
 
 def boys(mmax: int, T, stream=None):
