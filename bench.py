@@ -43,6 +43,8 @@ def parse_args(argv=None):
     p.add_argument("--no-cart", action="store_true", help="skip the Cartesian-output measurement")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-split", action="store_true", help="skip the split-precision measurement")
+    p.add_argument("--no-mixed", action="store_true", help="skip the mixed-class graph measurement")
+    p.add_argument("--mixed-quartets", type=int, default=1000)
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
     return p.parse_args(argv)
 
@@ -395,6 +397,47 @@ def main(argv=None):
         del wsc, outc
         torch.cuda.empty_cache()
 
+    # ---- mixed classes, K = 1..5: autotuned tiles, the whole batch as one CUDA graph
+    mixed = None
+    if not args.no_mixed:
+        mb, mq = inputs.mixed_fp64(nquartet=args.mixed_quartets, seed=2309)
+        mixed = {"workload": f"{args.mixed_quartets} quartets over (gg|gg),(hh|hh),(ii|ii),(gh|ii),(gi|hh), K = 1..5 "
+                             "per shell, exponents log-uniform [0.05, 50], solid harmonics"}
+        mg1, mg2, _ = gemm_flops(mb, mq, True)
+        bt = lx.Batch(mb, mq, solid=True)
+        t0 = time.perf_counter()
+        rows = lx.autotune(bt, max_keys=24, samples=4)
+        mixed["autotune_s"] = time.perf_counter() - t0
+        mixed["tuned_keys"] = int(len(rows))
+        for path in ("fp64", "split"):
+            b = lx.Batch(mb, mq, solid=True, path=path)
+            outm = torch.empty(b.out_size, dtype=torch.float64, device="cuda")
+            wsm = lx.alloc_workspace(min(b.workspace_size(), 64 << 30))
+            g = lx.Graph(b, outm, wsm)
+            g.launch()
+            torch.cuda.synchronize()
+            ev = []
+            for _ in range(2):
+                flush_buf.add_(1)
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record()
+                g.launch()
+                s1.record()
+                ev.append((s0, s1))
+            torch.cuda.synchronize()
+            lx.sync_status()
+            ms = sum(a.elapsed_time(b_) for a, b_ in ev) / len(ev)
+            mixed[path] = {"quartets_per_s": world * len(mq) / (ms * 1e-3), "ms_per_step": ms,
+                           "fp64_equiv_tflops": world * (mg1 + mg2) / (ms * 1e-3) / 1e12, "graph_launches_per_step": 1}
+            if path == "fp64":
+                ref_m = outm
+            else:
+                mixed["split"]["max_abs_diff_vs_fp64_path"] = float((outm - ref_m).abs().max())
+            g.close()
+            del wsm
+        del ref_m, outm
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
         cpu = cpu_baseline(basis, quartets, True, args.cpu_seconds)
@@ -411,7 +454,7 @@ def main(argv=None):
             "fp64_equiv_tflops": fp64_tf, "integrals_per_s": world * nint * args.steps / (total_ms * 1e-3),
             "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
             "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "cartesian": cart,
-            "split": split,
+            "split": split, "mixed": mixed,
             "gpu_launches": int(sum(launches.values())),
         }
         print(json.dumps(line), flush=True)

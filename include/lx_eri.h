@@ -152,6 +152,40 @@ int lx_eri_batch_static(const lx_shell* shells, int32_t nshell, const double* ex
                         double* out, void* cuda_stream);
 
 /*
+ * Capture the whole evaluation of a batch into a CUDA graph bound to `out` and `workspace`
+ * (same arguments and meaning as lx_eri_batch, LX_TIME_STAGES not allowed): every stage of
+ * every chunk, over quartets of any mix of classes and contraction degrees, then replays with
+ * one lx_eri_graph_launch.  The descriptors are copied into pinned host memory owned by the
+ * handle, so the host arrays may be freed after the call.  *handle receives the graph.
+ */
+int lx_eri_graph_create(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
+                        int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags,
+                        double* out, void* workspace, size_t workspace_bytes, void** handle);
+/* Enqueue one replay of a captured batch on cuda_stream (asynchronous). */
+int lx_eri_graph_launch(void* handle, void* cuda_stream);
+/* Release a captured batch (after its last replay has completed). */
+int lx_eri_graph_destroy(void* handle);
+
+/*
+ * Autotune the tile shape of the two FP64 GEMM stages per (l_a, l_b, l_c, l_d, K_bra, K_ket,
+ * output kind): for each of the `max_keys` costliest keys of the batch, up to `samples` of its
+ * quartets are evaluated with every tile shape (32x64, 64x32, 32x32, 64x64) and the fastest,
+ * timed with CUDA events on cuda_stream, is recorded in the library's tuning table, which the
+ * planner consults for every later call.  out (DEVICE, out_doubles long) and workspace are
+ * scratch.  Synchronises cuda_stream.  The split path has a single tile shape: no-op.
+ */
+int lx_eri_autotune(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
+                    int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags, double* out,
+                    int64_t out_doubles, void* workspace, size_t workspace_bytes, int32_t max_keys, int32_t samples,
+                    void* cuda_stream);
+/* Tuning table rows (9 int32 each: l_a, l_b, l_c, l_d, K_bra, K_ket, solid, shape of GEMM1,
+   shape of GEMM2): export writes min(count, cap) rows and returns the count; import adds or
+   replaces rows (LX_ERR_SIZE on an invalid row, nothing imported); clear empties the table. */
+int64_t lx_tune_export(int32_t* rows, int64_t cap);
+int lx_tune_import(const int32_t* rows, int64_t n);
+int lx_tune_clear(void);
+
+/*
  * Wait for cuda_stream, then read and clear the device status word of the current device.
  * Returns LX_OK, LX_ERR_DEVICE_STATUS if a kernel flagged an error since the last call,
  * or LX_ERR_CUDA if the stream reported a CUDA error.

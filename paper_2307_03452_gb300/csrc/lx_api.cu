@@ -10,6 +10,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
+#include <map>
 #include <mutex>
 #include <unordered_map>
 #include <vector>
@@ -140,6 +142,35 @@ int validate(const lx_shell* shells, int32_t nshell, const double* exps, const d
     return LX_OK;
 }
 
+// ------------------------------------------------------------------ tuning table
+
+// Tile shape per (class, contraction) of the FP64 GEMMs, filled by lx_eri_autotune or
+// lx_tune_import; keys not in the table use GEMM_V32x64.
+struct TuneKey {
+    int la, lb, lc, ld, kbra, kket, solid;
+    bool operator<(const TuneKey& o) const {
+        const int a[7] = {la, lb, lc, ld, kbra, kket, solid}, b[7] = {o.la, o.lb, o.lc, o.ld, o.kbra, o.kket, o.solid};
+        for (int i = 0; i < 7; ++i)
+            if (a[i] != b[i]) return a[i] < b[i];
+        return false;
+    }
+};
+struct TuneVal {
+    int v1, v2;
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, TuneVal> g_tune;
+
+TuneKey tune_key(const lx_shell* sh, const lx_quartet& q, bool solid) {
+    return TuneKey{sh[q.s[0]].l, sh[q.s[1]].l, sh[q.s[2]].l, sh[q.s[3]].l, sh[q.s[0]].nprim * sh[q.s[1]].nprim,
+                   sh[q.s[2]].nprim * sh[q.s[3]].nprim, solid ? 1 : 0};
+}
+
+// Forced tile shapes (autotuning); -1 = use the table.
+struct Overrides {
+    int v1 = -1, v2 = -1;
+};
+
 // ------------------------------------------------------------------ planning
 
 struct PairKey {
@@ -166,8 +197,9 @@ size_t quartet_bytes(const lx_shell* sh, const lx_quartet& q, int flags) {
     // + 256 bytes per data block: each block starts on a 256-byte boundary
     size_t bytes = sizeof(DQuartet) + 8 * (size_t)(kbra * kket * pyr(L) + nab * n1) + 512;
     if (!split) {
-        items += ((nab + GEMM_BM - 1) / GEMM_BM) * ((n1 + GEMM_BN - 1) / GEMM_BN);
-        items += ((nab + GEMM_BM - 1) / GEMM_BM) * ((ncd + GEMM_BN - 1) / GEMM_BN);
+        // bound: the 32 x 32 tile gives the most work items
+        items += ((nab + 31) / 32) * ((n1 + 31) / 32);
+        items += ((nab + 31) / 32) * ((ncd + 31) / 32);
     } else {
         const int k1 = (int)(kbra * np), k2 = (int)n1;
         const int ra1 = split_rowpad(k2, SPLIT_TA), rb1 = split_rowpad((int)nab, SPLIT_TB);
@@ -194,7 +226,7 @@ size_t pair_bytes(const lx_shell* sh, int sa, int sb, int flags) {
     return sizeof(DPair) + kab * sizeof(WorkItem) + 8 * (size_t)(kab * 4 + rows * kab * pyr(a.l + b.l)) + 512;
 }
 
-constexpr size_t CHUNK_SLACK = 16 * 256;  // alignment padding of the chunk's regions
+constexpr size_t CHUNK_SLACK = 32 * 256;  // alignment padding of the chunk's regions and the work counters
 
 size_t head_bytes(int nshell, int nprim) {
     return align256(sizeof(DShell) * (size_t)nshell) + 3 * align256(sizeof(double) * (size_t)nprim);
@@ -241,6 +273,8 @@ struct ChunkPlan {
     std::vector<DQuartet> quartets;
     std::vector<WorkItem> items_h, items_br, items_g1, items_g2;
     size_t off_pairs = 0, off_quartets = 0, off_h = 0, off_br = 0, off_g1 = 0, off_g2 = 0, off_data = 0;
+    int g1_counts[GEMM_NVARIANT] = {0, 0, 0, 0}, g2_counts[GEMM_NVARIANT] = {0, 0, 0, 0};
+    size_t off_counters = 0;  // 2 x GEMM_NVARIANT work counters, uploaded as zeros with the blob
     // split path (per quartet: 3 split-row descs B1, A2, B2; 3 column-max descs cmh1, cmh2, cmx;
     // 2 balance descs e1, e2)
     std::vector<SplitRowsDesc> srd;
@@ -258,7 +292,7 @@ struct ChunkPlan {
 };
 
 void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int flags, size_t chunk_base,
-                 ChunkPlan& P) {
+                 ChunkPlan& P, const Overrides& ov = Overrides()) {
     const bool solid = flags & LX_SOLID, split = flags & LX_PATH_SPLIT;
     P.pairs.clear();
     P.quartets.clear();
@@ -313,17 +347,55 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     // work lists
     for (int i = 0; i < (int)P.pairs.size(); ++i)
         for (int kp = 0; kp < P.pairs[i].Kab; ++kp) P.items_h.push_back({i, kp, 0, 0});
-    for (int i = 0; i < (int)P.quartets.size(); ++i) {
-        const DQuartet& d = P.quartets[i];
-        for (int k = 0; k < d.kbra * d.kket; k += 4) P.items_br.push_back({i, k, 0, 0});
-        if (split) continue;
-        const int mt = (d.nab + GEMM_BM - 1) / GEMM_BM;
-        const int nt1 = (d.kket * d.nq + GEMM_BN - 1) / GEMM_BN, nt2 = (d.ncd + GEMM_BN - 1) / GEMM_BN;
-        for (int m = 0; m < mt; ++m)
-            for (int n = 0; n < nt1; ++n) P.items_g1.push_back({i, m, n, 0});
-        for (int m = 0; m < mt; ++m)
-            for (int n = 0; n < nt2; ++n) P.items_g2.push_back({i, m, n, 0});
+    std::vector<int64_t> cost1, cost2;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        for (int i = 0; i < (int)P.quartets.size(); ++i) {
+            const DQuartet& d = P.quartets[i];
+            for (int k = 0; k < d.kbra * d.kket; k += 4) P.items_br.push_back({i, k, 0, 0});
+            if (split) continue;
+            int v1 = GEMM_V32x64, v2 = GEMM_V32x64;
+            auto f = g_tune.find(tune_key(sh, qs[ch.q_begin + i], solid));
+            if (f != g_tune.end()) {
+                v1 = f->second.v1;
+                v2 = f->second.v2;
+            }
+            if (ov.v1 >= 0) v1 = ov.v1;
+            if (ov.v2 >= 0) v2 = ov.v2;
+            const int n1 = d.kket * d.nq, k1 = d.kbra * d.np;
+            const int mt1 = (d.nab + gemm_bm(v1) - 1) / gemm_bm(v1), nt1 = (n1 + gemm_bn(v1) - 1) / gemm_bn(v1);
+            const int mt2 = (d.nab + gemm_bm(v2) - 1) / gemm_bm(v2), nt2 = (d.ncd + gemm_bn(v2) - 1) / gemm_bn(v2);
+            for (int m = 0; m < mt1; ++m)
+                for (int n = 0; n < nt1; ++n) {
+                    P.items_g1.push_back({i, m, n, v1});
+                    cost1.push_back((int64_t)gemm_bm(v1) * gemm_bn(v1) * k1);
+                }
+            for (int m = 0; m < mt2; ++m)
+                for (int n = 0; n < nt2; ++n) {
+                    P.items_g2.push_back({i, m, n, v2});
+                    cost2.push_back((int64_t)gemm_bm(v2) * gemm_bn(v2) * n1);
+                }
+        }
     }
+    // grouped by tile shape (one persistent launch each), largest tiles first within a shape:
+    // the persistent launches hand items out round-robin
+    auto lpt = [](std::vector<WorkItem>& items, const std::vector<int64_t>& cost, int* counts) {
+        std::vector<size_t> idx(items.size());
+        for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
+        std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
+            if (items[x].c != items[y].c) return items[x].c < items[y].c;
+            return cost[x] > cost[y];
+        });
+        std::vector<WorkItem> sorted(items.size());
+        for (int v = 0; v < GEMM_NVARIANT; ++v) counts[v] = 0;
+        for (size_t k = 0; k < idx.size(); ++k) {
+            sorted[k] = items[idx[k]];
+            ++counts[sorted[k].c];
+        }
+        items.swap(sorted);
+    };
+    lpt(P.items_g1, cost1, P.g1_counts);
+    lpt(P.items_g2, cost2, P.g2_counts);
     if (split) {
         // split descriptors and work lists (offsets filled in below, with the data layout)
         for (int i = 0; i < (int)P.quartets.size(); ++i) {
@@ -379,6 +451,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     region(P.off_br, sizeof(WorkItem) * P.items_br.size());
     region(P.off_g1, sizeof(WorkItem) * P.items_g1.size());
     region(P.off_g2, sizeof(WorkItem) * P.items_g2.size());
+    region(P.off_counters, sizeof(int) * 2 * GEMM_NVARIANT);
     region(P.off_srd, sizeof(SplitRowsDesc) * P.srd.size());
     region(P.off_cmd, sizeof(ColMaxDesc) * P.cmd.size());
     region(P.off_bal, sizeof(BalanceDesc) * P.bal.size());
@@ -536,97 +609,75 @@ int64_t prim_count(const lx_shell* sh, int32_t nshell) {
     return n;
 }
 
-}  // namespace
-}  // namespace lx
+// ------------------------------------------------------------------ plan + enqueue
 
-using namespace lx;
+// Host-side plan of one lx_eri_batch call: the head (shells, exponents, coefficients) and
+// every chunk's descriptors, laid out for a workspace of `workspace_bytes`.
+struct PlannedBatch {
+    int flags = 0, nshell = 0, nprim = 0;
+    size_t head = 0, o_exps = 0, o_coefs = 0, o_ncoef = 0;
+    std::vector<char> head_blob;  // bytes [0, o_ncoef) of the workspace
+    std::vector<ChunkPlan> chunks;
+};
 
-extern "C" {
-
-int64_t lx_eri_out_size(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
-                        int32_t flags) {
-    const int v = validate(shells, nshell, nullptr, nullptr, 0, quartets, nquartet, flags, false);
-    if (v != LX_OK) return v;
-    const bool solid = flags & LX_SOLID;
-    int64_t n = 0;
-    for (int64_t i = 0; i < nquartet; ++i) {
-        int64_t sz = 1;
-        for (int k = 0; k < 4; ++k) sz *= nfun(shells[quartets[i].s[k]].l, solid);
-        n = std::max(n, quartets[i].out_offset + sz);
-    }
-    return n;
-}
-
-int64_t lx_eri_workspace_size(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
-                              int32_t flags) {
-    const int v = validate(shells, nshell, nullptr, nullptr, 0, quartets, nquartet, flags, false);
-    if (v != LX_OK) return v;
-    return (int64_t)(head_bytes(nshell, (int32_t)prim_count(shells, nshell)) +
-                     chunk_estimate(shells, quartets, 0, nquartet, flags & (LX_SOLID | LX_PATH_SPLIT)));
-}
-
-int64_t lx_eri_workspace_min(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
-                             int32_t flags) {
-    const int v = validate(shells, nshell, nullptr, nullptr, 0, quartets, nquartet, flags, false);
-    if (v != LX_OK) return v;
-    size_t mx = CHUNK_SLACK;
-    for (int64_t i = 0; i < nquartet; ++i)
-        mx = std::max(mx, chunk_estimate(shells, quartets, i, i + 1, flags & (LX_SOLID | LX_PATH_SPLIT)));
-    return (int64_t)(head_bytes(nshell, (int32_t)prim_count(shells, nshell)) + mx);
-}
-
-int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
-                 int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags, double* out,
-                 void* workspace, size_t workspace_bytes, void* cuda_stream) {
-    int v = validate(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, true);
-    if (v != LX_OK) return v;
-    if (nquartet == 0) return LX_OK;
-    if (!out) return LX_ERR_NULL;
-    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return LX_ERR_WORKSPACE;
-    unsigned* status = nullptr;
-    if ((v = ensure_device(&status)) != LX_OK) return v;
-    const bool solid = flags & LX_SOLID;
-    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    const size_t head = head_bytes(nshell, nprim_total);
-    if (workspace_bytes < head + CHUNK_SLACK) return LX_ERR_WORKSPACE;
-    std::vector<Chunk> chunks;
+int plan_batch(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs, int32_t nprim_total,
+               const lx_quartet* quartets, int64_t nquartet, int32_t flags, size_t workspace_bytes,
+               const Overrides& ov, PlannedBatch& B) {
+    B.flags = flags;
+    B.nshell = nshell;
+    B.nprim = nprim_total;
+    B.head = head_bytes(nshell, nprim_total);
+    if (workspace_bytes < B.head + CHUNK_SLACK) return LX_ERR_WORKSPACE;
     const int pflags = flags & (LX_SOLID | LX_PATH_SPLIT);
-    const bool split = flags & LX_PATH_SPLIT;
-    if ((v = plan_chunks(shells, quartets, nquartet, pflags, workspace_bytes - head, chunks)) != LX_OK) return v;
-
-    char* wsb = static_cast<char*>(workspace);
-    double* ws = static_cast<double*>(workspace);
-    // head: shells, exponents, raw and normalised coefficients
-    std::vector<char> hb(head, 0);
-    DShell* dsh = reinterpret_cast<DShell*>(hb.data());
+    std::vector<Chunk> chunks;
+    int v = plan_chunks(shells, quartets, nquartet, pflags, workspace_bytes - B.head, chunks);
+    if (v != LX_OK) return v;
+    B.head_blob.assign(B.head, 0);
+    DShell* dsh = reinterpret_cast<DShell*>(B.head_blob.data());
     for (int32_t s = 0; s < nshell; ++s) {
         dsh[s].l = shells[s].l;
         dsh[s].K = shells[s].nprim;
         dsh[s].prim_off = shells[s].prim_offset;
         for (int k = 0; k < 3; ++k) dsh[s].A[k] = shells[s].center[k];
     }
-    const size_t o_exps = align256(sizeof(DShell) * (size_t)nshell);
-    const size_t o_coefs = o_exps + align256(sizeof(double) * (size_t)nprim_total);
-    const size_t o_ncoef = o_coefs + align256(sizeof(double) * (size_t)nprim_total);
-    std::memcpy(hb.data() + o_exps, exps, sizeof(double) * (size_t)nprim_total);
-    std::memcpy(hb.data() + o_coefs, coefs, sizeof(double) * (size_t)nprim_total);
-    cudaError_t e = cudaMemcpyAsync(wsb, hb.data(), o_ncoef, cudaMemcpyHostToDevice, st);
+    B.o_exps = align256(sizeof(DShell) * (size_t)nshell);
+    B.o_coefs = B.o_exps + align256(sizeof(double) * (size_t)nprim_total);
+    B.o_ncoef = B.o_coefs + align256(sizeof(double) * (size_t)nprim_total);
+    if (nprim_total > 0) {
+        std::memcpy(B.head_blob.data() + B.o_exps, exps, sizeof(double) * (size_t)nprim_total);
+        std::memcpy(B.head_blob.data() + B.o_coefs, coefs, sizeof(double) * (size_t)nprim_total);
+    }
+    B.chunks.resize(chunks.size());
+    for (size_t c = 0; c < chunks.size(); ++c) {
+        build_chunk(shells, quartets, chunks[c], pflags, B.head, B.chunks[c], ov);
+        if (B.head + B.chunks[c].total > workspace_bytes) return LX_ERR_WORKSPACE;
+    }
+    return LX_OK;
+}
+
+// Enqueue a planned batch on stream st: the head upload, normalisation, then per chunk the
+// descriptor upload and the kernels of the chosen path.  head_src / blob_src are the host
+// bytes to upload (pageable, or pinned for graph capture).
+int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector<const char*>& blob_src, double* out,
+                  void* workspace, unsigned* status, cudaStream_t st, bool time_stages) {
+    const bool split = B.flags & LX_PATH_SPLIT;
+    const int nshell = B.nshell;
+    char* wsb = static_cast<char*>(workspace);
+    double* ws = static_cast<double*>(workspace);
+    cudaError_t e = cudaMemcpyAsync(wsb, head_src, B.o_ncoef, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e);
     const DShell* d_sh = reinterpret_cast<const DShell*>(wsb);
-    const double* d_exps = reinterpret_cast<const double*>(wsb + o_exps);
-    const double* d_coefs = reinterpret_cast<const double*>(wsb + o_coefs);
-    double* d_ncoef = reinterpret_cast<double*>(wsb + o_ncoef);
-    StageTimer tm{(flags & LX_TIME_STAGES) != 0, st};
+    const double* d_exps = reinterpret_cast<const double*>(wsb + B.o_exps);
+    const double* d_coefs = reinterpret_cast<const double*>(wsb + B.o_coefs);
+    double* d_ncoef = reinterpret_cast<double*>(wsb + B.o_ncoef);
+    StageTimer tm{time_stages, st};
     if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
     if ((e = launch_norm(d_sh, nshell, d_exps, d_coefs, d_ncoef, status, st)) != cudaSuccess) return cuda_fail(e);
     if ((e = tm.end(LX_STAGE_NORM, 1)) != cudaSuccess) return cuda_fail(e);
-
-    ChunkPlan P;
-    for (const auto& ch : chunks) {
-        build_chunk(shells, quartets, ch, pflags, head, P);
-        if (head + P.total > workspace_bytes) return LX_ERR_WORKSPACE;
-        char* base = wsb + head;
-        e = cudaMemcpyAsync(base, P.blob.data(), P.off_data, cudaMemcpyHostToDevice, st);
+    for (size_t c = 0; c < B.chunks.size(); ++c) {
+        const ChunkPlan& P = B.chunks[c];
+        char* base = wsb + B.head;
+        e = cudaMemcpyAsync(base, blob_src[c], P.off_data, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e);
         const DPair* d_pairs = reinterpret_cast<const DPair*>(base + P.off_pairs);
         const DQuartet* d_q = reinterpret_cast<const DQuartet*>(base + P.off_quartets);
@@ -683,14 +734,298 @@ int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, con
             continue;
         }
         if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
-        if ((e = launch_gemm1(d_q, d_pairs, d_ig1, (int)P.items_g1.size(), ws, status, st)) != cudaSuccess)
+        int* d_counters = reinterpret_cast<int*>(base + P.off_counters);
+        if ((e = launch_gemm1(d_q, d_pairs, d_ig1, P.g1_counts, ws, d_counters, status, st)) != cudaSuccess)
             return cuda_fail(e);
         if ((e = tm.end(LX_STAGE_GEMM1, 1)) != cudaSuccess) return cuda_fail(e);
         if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
-        if ((e = launch_gemm2(d_q, d_pairs, d_ig2, (int)P.items_g2.size(), ws, out, status, st)) != cudaSuccess)
+        if ((e = launch_gemm2(d_q, d_pairs, d_ig2, P.g2_counts, ws, out, d_counters + GEMM_NVARIANT, status, st)) !=
+            cudaSuccess)
             return cuda_fail(e);
         if ((e = tm.end(LX_STAGE_GEMM2, 1)) != cudaSuccess) return cuda_fail(e);
     }
+    return LX_OK;
+}
+
+}  // namespace
+}  // namespace lx
+
+using namespace lx;
+
+extern "C" {
+
+int64_t lx_eri_out_size(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
+                        int32_t flags) {
+    const int v = validate(shells, nshell, nullptr, nullptr, 0, quartets, nquartet, flags, false);
+    if (v != LX_OK) return v;
+    const bool solid = flags & LX_SOLID;
+    int64_t n = 0;
+    for (int64_t i = 0; i < nquartet; ++i) {
+        int64_t sz = 1;
+        for (int k = 0; k < 4; ++k) sz *= nfun(shells[quartets[i].s[k]].l, solid);
+        n = std::max(n, quartets[i].out_offset + sz);
+    }
+    return n;
+}
+
+int64_t lx_eri_workspace_size(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
+                              int32_t flags) {
+    const int v = validate(shells, nshell, nullptr, nullptr, 0, quartets, nquartet, flags, false);
+    if (v != LX_OK) return v;
+    return (int64_t)(head_bytes(nshell, (int32_t)prim_count(shells, nshell)) +
+                     chunk_estimate(shells, quartets, 0, nquartet, flags & (LX_SOLID | LX_PATH_SPLIT)));
+}
+
+int64_t lx_eri_workspace_min(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
+                             int32_t flags) {
+    const int v = validate(shells, nshell, nullptr, nullptr, 0, quartets, nquartet, flags, false);
+    if (v != LX_OK) return v;
+    size_t mx = CHUNK_SLACK;
+    for (int64_t i = 0; i < nquartet; ++i)
+        mx = std::max(mx, chunk_estimate(shells, quartets, i, i + 1, flags & (LX_SOLID | LX_PATH_SPLIT)));
+    return (int64_t)(head_bytes(nshell, (int32_t)prim_count(shells, nshell)) + mx);
+}
+
+int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
+                 int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags, double* out,
+                 void* workspace, size_t workspace_bytes, void* cuda_stream) {
+    int v = validate(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, true);
+    if (v != LX_OK) return v;
+    if (nquartet == 0) return LX_OK;
+    if (!out) return LX_ERR_NULL;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return LX_ERR_WORKSPACE;
+    unsigned* status = nullptr;
+    if ((v = ensure_device(&status)) != LX_OK) return v;
+    PlannedBatch B;
+    if ((v = plan_batch(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, workspace_bytes,
+                        Overrides(), B)) != LX_OK)
+        return v;
+    std::vector<const char*> blobs;
+    for (const auto& P : B.chunks) blobs.push_back(P.blob.data());
+    return enqueue_batch(B, B.head_blob.data(), blobs, out, workspace, status, static_cast<cudaStream_t>(cuda_stream),
+                         (flags & LX_TIME_STAGES) != 0);
+}
+
+namespace {
+struct GraphHandle {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<void*> pinned;
+    int device = 0;
+};
+
+// Device milliseconds per stage of the LX_TIME_STAGES work on stream st (clears it).
+int collect_stage_ms(cudaStream_t st, double* ms) {
+    for (int i = 0; i < LX_NSTAGE; ++i) ms[i] = 0.0;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    std::lock_guard<std::mutex> lock(g_timing_mutex);
+    std::vector<PendingTiming> keep;
+    for (const auto& p : g_pending) {
+        if (p.stream != st) {
+            keep.push_back(p);
+            continue;
+        }
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, p.begin, p.end) == cudaSuccess) ms[p.stage] += t;
+        cudaEventDestroy(p.begin);
+        cudaEventDestroy(p.end);
+    }
+    g_pending.swap(keep);
+    return LX_OK;
+}
+}  // namespace
+
+int lx_eri_graph_create(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
+                        int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags,
+                        double* out, void* workspace, size_t workspace_bytes, void** handle) {
+    if (!handle) return LX_ERR_NULL;
+    *handle = nullptr;
+    if (flags & LX_TIME_STAGES) return LX_ERR_FLAGS;
+    int v = validate(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, true);
+    if (v != LX_OK) return v;
+    if (!out) return LX_ERR_NULL;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return LX_ERR_WORKSPACE;
+    unsigned* status = nullptr;
+    if ((v = ensure_device(&status)) != LX_OK) return v;
+    PlannedBatch B;
+    if ((v = plan_batch(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, workspace_bytes,
+                        Overrides(), B)) != LX_OK)
+        return v;
+    GraphHandle* h = new GraphHandle();
+    cudaGetDevice(&h->device);
+    auto fail = [&](int code) {
+        for (void* p : h->pinned) cudaFreeHost(p);
+        if (h->exec) cudaGraphExecDestroy(h->exec);
+        if (h->graph) cudaGraphDestroy(h->graph);
+        delete h;
+        return code;
+    };
+    // host bytes the graph's copy nodes read: pinned and owned by the handle
+    auto pin = [&](const std::vector<char>& src, const char** dst) {
+        void* p = nullptr;
+        cudaError_t e = cudaHostAlloc(&p, src.size() > 0 ? src.size() : 1, cudaHostAllocDefault);
+        if (e != cudaSuccess) return e;
+        if (!src.empty()) std::memcpy(p, src.data(), src.size());
+        h->pinned.push_back(p);
+        *dst = static_cast<const char*>(p);
+        return cudaSuccess;
+    };
+    const char* head_src = nullptr;
+    std::vector<const char*> blobs(B.chunks.size());
+    cudaError_t e = pin(B.head_blob, &head_src);
+    for (size_t c = 0; e == cudaSuccess && c < B.chunks.size(); ++c) e = pin(B.chunks[c].blob, &blobs[c]);
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+    cudaStream_t cs = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) return fail(cuda_fail(e));
+    if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return fail(cuda_fail(e));
+    }
+    v = nquartet > 0 ? enqueue_batch(B, head_src, blobs, out, workspace, status, cs, false) : LX_OK;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    h->graph = g;
+    if (v != LX_OK) return fail(v);
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+    if ((e = cudaGraphInstantiate(&h->exec, h->graph, 0)) != cudaSuccess) return fail(cuda_fail(e));
+    *handle = h;
+    return LX_OK;
+}
+
+int lx_eri_graph_launch(void* handle, void* cuda_stream) {
+    if (!handle) return LX_ERR_NULL;
+    GraphHandle* h = static_cast<GraphHandle*>(handle);
+    cudaError_t e = cudaGraphLaunch(h->exec, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? LX_OK : cuda_fail(e);
+}
+
+int lx_eri_graph_destroy(void* handle) {
+    if (!handle) return LX_OK;
+    GraphHandle* h = static_cast<GraphHandle*>(handle);
+    for (void* p : h->pinned) cudaFreeHost(p);
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    delete h;
+    return LX_OK;
+}
+
+int lx_eri_autotune(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
+                    int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags, double* out,
+                    int64_t out_doubles, void* workspace, size_t workspace_bytes, int32_t max_keys, int32_t samples,
+                    void* cuda_stream) {
+    int v = validate(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, true);
+    if (v != LX_OK) return v;
+    if (flags & LX_PATH_SPLIT) return LX_OK;  // the split path has one tile shape
+    if (max_keys < 1 || samples < 1 || out_doubles < 0) return LX_ERR_SIZE;
+    if (!out || !workspace) return LX_ERR_NULL;
+    unsigned* status = nullptr;
+    if ((v = ensure_device(&status)) != LX_OK) return v;
+    const bool solid = flags & LX_SOLID;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // group by key; the costliest keys (total GEMM1 work) first
+    std::map<TuneKey, std::vector<int64_t>> groups;
+    std::map<TuneKey, double> cost;
+    for (int64_t i = 0; i < nquartet; ++i) {
+        const TuneKey k = tune_key(shells, quartets[i], solid);
+        groups[k].push_back(i);
+        cost[k] += (double)nfun(k.la, solid) * nfun(k.lb, solid) * k.kbra * pyr(k.la + k.lb) * k.kket * pyr(k.lc + k.ld);
+    }
+    std::vector<std::pair<double, TuneKey>> order;
+    for (const auto& kv : cost) order.push_back({-kv.second, kv.first});
+    std::sort(order.begin(), order.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    int tuned = 0;
+    for (const auto& ok : order) {
+        if (tuned >= max_keys) break;
+        const std::vector<int64_t>& idx = groups[ok.second];
+        std::vector<lx_quartet> sub;
+        int64_t pos = 0;
+        for (size_t j = 0; j < idx.size() && (int)j < samples; ++j) {
+            lx_quartet q = quartets[idx[j]];
+            int64_t sz = 1;
+            for (int k = 0; k < 4; ++k) sz *= nfun(shells[q.s[k]].l, solid);
+            if (pos + sz > out_doubles) break;
+            q.out_offset = pos;
+            pos += sz;
+            sub.push_back(q);
+        }
+        if (sub.empty()) continue;
+        double best1 = 1e300, best2 = 1e300;
+        int v1 = GEMM_V32x64, v2 = GEMM_V32x64;
+        for (int var = 0; var < GEMM_NVARIANT; ++var) {
+            PlannedBatch B;
+            Overrides ov;
+            ov.v1 = ov.v2 = var;
+            if ((v = plan_batch(shells, nshell, exps, coefs, nprim_total, sub.data(), (int64_t)sub.size(),
+                                flags & (LX_SOLID | LX_PATH_SPLIT), workspace_bytes, ov, B)) != LX_OK)
+                return v;
+            std::vector<const char*> blobs;
+            for (const auto& P : B.chunks) blobs.push_back(P.blob.data());
+            double t1 = 1e300, t2 = 1e300;
+            for (int rep = 0; rep < 3; ++rep) {  // first repetition warms up
+                if ((v = enqueue_batch(B, B.head_blob.data(), blobs, out, workspace, status, st, true)) != LX_OK)
+                    return v;
+                double ms[LX_NSTAGE];
+                if ((v = collect_stage_ms(st, ms)) != LX_OK) return v;
+                if (rep > 0) {
+                    t1 = std::min(t1, ms[LX_STAGE_GEMM1]);
+                    t2 = std::min(t2, ms[LX_STAGE_GEMM2]);
+                }
+            }
+            if (t1 < best1) {
+                best1 = t1;
+                v1 = var;
+            }
+            if (t2 < best2) {
+                best2 = t2;
+                v2 = var;
+            }
+        }
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune[ok.second] = TuneVal{v1, v2};
+        ++tuned;
+    }
+    return LX_OK;
+}
+
+int64_t lx_tune_export(int32_t* rows, int64_t cap) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    int64_t n = 0;
+    for (const auto& kv : g_tune) {
+        if (rows && n < cap) {
+            const TuneKey& k = kv.first;
+            int32_t* r = rows + 9 * n;
+            r[0] = k.la, r[1] = k.lb, r[2] = k.lc, r[3] = k.ld, r[4] = k.kbra, r[5] = k.kket, r[6] = k.solid;
+            r[7] = kv.second.v1, r[8] = kv.second.v2;
+        }
+        ++n;
+    }
+    return n;
+}
+
+int lx_tune_import(const int32_t* rows, int64_t n) {
+    if (n < 0) return LX_ERR_SIZE;
+    if (n > 0 && !rows) return LX_ERR_NULL;
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t* r = rows + 9 * i;
+        for (int k = 0; k < 4; ++k)
+            if (r[k] < 0 || r[k] > LX_LMAX) return LX_ERR_SIZE;
+        if (r[4] < 1 || r[5] < 1 || r[6] < 0 || r[6] > 1 || r[7] < 0 || r[7] >= GEMM_NVARIANT || r[8] < 0 ||
+            r[8] >= GEMM_NVARIANT)
+            return LX_ERR_SIZE;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t* r = rows + 9 * i;
+        g_tune[TuneKey{r[0], r[1], r[2], r[3], r[4], r[5], r[6]}] = TuneVal{r[7], r[8]};
+    }
+    return LX_OK;
+}
+
+int lx_tune_clear(void) {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune.clear();
     return LX_OK;
 }
 

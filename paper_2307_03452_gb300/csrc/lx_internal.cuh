@@ -83,10 +83,12 @@ cudaError_t launch_pair_h(const DPair* pairs, const WorkItem* items, int nitems,
                           cudaStream_t st);
 cudaError_t launch_boys_r(const DQuartet* qd, const DPair* pairs, const WorkItem* items, int nitems, double* ws,
                           unsigned* status, cudaStream_t st);
-cudaError_t launch_gemm1(const DQuartet* qd, const DPair* pairs, const WorkItem* items, int nitems, double* ws,
-                         unsigned* status, cudaStream_t st);
-cudaError_t launch_gemm2(const DQuartet* qd, const DPair* pairs, const WorkItem* items, int nitems,
-                         const double* ws_in, double* out, unsigned* status, cudaStream_t st);
+// items grouped by tile shape: counts[v] items of shape v, in shape order; counters[v] is the
+// zero-initialised work counter of shape v's launch
+cudaError_t launch_gemm1(const DQuartet* qd, const DPair* pairs, const WorkItem* items, const int* counts, double* ws,
+                         int* counters, unsigned* status, cudaStream_t st);
+cudaError_t launch_gemm2(const DQuartet* qd, const DPair* pairs, const WorkItem* items, const int* counts,
+                         const double* ws_in, double* out, int* counters, unsigned* status, cudaStream_t st);
 cudaError_t launch_boys(int mmax, const double* T, int64_t n, double* F, unsigned* status, cudaStream_t st);
 cudaError_t launch_hermite_r(int L, const double* params, int64_t n, double* R, unsigned* status, cudaStream_t st);
 
@@ -100,9 +102,10 @@ cudaError_t launch_mlp_grad(const float* params, const float* feat, const float*
 cudaError_t launch_mlp_adam(float* params, float* m, float* v, float* grad, void* p16, int step, float lr, float b1,
                             float b2, float eps, cudaStream_t st);
 
-// GEMM tiling (shared by the planner and the kernels).
-constexpr int GEMM_BM = 32;
-constexpr int GEMM_BN = 64;
+// FP64 GEMM tile shapes (shared by the planner, the autotuner and the kernels).
+enum : int { GEMM_V32x64 = 0, GEMM_V64x32 = 1, GEMM_V32x32 = 2, GEMM_V64x64 = 3, GEMM_NVARIANT = 4 };
+__host__ __device__ inline int gemm_bm(int v) { return (v == GEMM_V64x32 || v == GEMM_V64x64) ? 64 : 32; }
+__host__ __device__ inline int gemm_bn(int v) { return (v == GEMM_V32x64 || v == GEMM_V64x64) ? 64 : 32; }
 constexpr int GEMM_BK = 16;
 
 // Real solid harmonics have fixed parities of the x, y, z exponents, so the matrix C of one

@@ -33,7 +33,9 @@ EXPORTS = sorted(["lx_eri_out_size", "lx_eri_workspace_size", "lx_eri_workspace_
                   "lx_eri_batch_static",
                   "lx_eri_sync_status", "lx_eri_stage_times", "lx_strerror", "lx_last_cuda_error", "lx_boys",
                   "lx_hermite_R", "lx_hermite_H", "lx_split_gemm", "lx_route_features", "lx_mlp_forward",
-                  "lx_mlp_grad", "lx_mlp_adam"])
+                  "lx_mlp_grad", "lx_mlp_adam", "lx_eri_graph_create", "lx_eri_graph_launch",
+                  "lx_eri_graph_destroy", "lx_eri_autotune", "lx_tune_export", "lx_tune_import", "lx_tune_clear"])
+TILE_SHAPES = ["32x64", "64x32", "32x32", "64x64"]
 MLP_NIN = 20
 MLP_WIDTH = 64
 MLP_NPARAM = MLP_WIDTH * MLP_NIN + MLP_WIDTH + MLP_WIDTH * MLP_WIDTH + MLP_WIDTH + MLP_WIDTH + 1
@@ -95,6 +97,22 @@ def load(build_if_missing: bool = True):
         lib.lx_hermite_H.restype = ctypes.c_int
         lib.lx_split_gemm.argtypes = [c_i32, c_i32, c_i32, c_vp, c_i32, c_vp, c_i32, c_vp, c_i32, c_vp]
         lib.lx_split_gemm.restype = ctypes.c_int
+        lib.lx_eri_graph_create.argtypes = [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_i64, c_i32, c_vp, c_vp, c_sz,
+                                            ctypes.POINTER(c_vp)]
+        lib.lx_eri_graph_create.restype = ctypes.c_int
+        lib.lx_eri_graph_launch.argtypes = [c_vp, c_vp]
+        lib.lx_eri_graph_launch.restype = ctypes.c_int
+        lib.lx_eri_graph_destroy.argtypes = [c_vp]
+        lib.lx_eri_graph_destroy.restype = ctypes.c_int
+        lib.lx_eri_autotune.argtypes = [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_i64, c_i32, c_vp, c_i64, c_vp, c_sz,
+                                        c_i32, c_i32, c_vp]
+        lib.lx_eri_autotune.restype = ctypes.c_int
+        lib.lx_tune_export.argtypes = [c_vp, c_i64]
+        lib.lx_tune_export.restype = c_i64
+        lib.lx_tune_import.argtypes = [c_vp, c_i64]
+        lib.lx_tune_import.restype = ctypes.c_int
+        lib.lx_tune_clear.argtypes = []
+        lib.lx_tune_clear.restype = ctypes.c_int
         lib.lx_route_features.argtypes = [c_vp, c_i32, c_vp, c_i32, c_vp, c_i64, c_vp, c_vp]
         lib.lx_route_features.restype = ctypes.c_int
         lib.lx_mlp_forward.argtypes = [c_vp, c_vp, c_i64, c_vp, c_vp]
@@ -244,6 +262,88 @@ def run_static(batch: "Batch", out, stream=None):
                                     _ptr(b.quartets), len(b.quartets), b.flags, ctypes.c_void_p(out.data_ptr()),
                                     ctypes.c_void_p(_stream_ptr(stream)))
     _check(rc, "lx_eri_batch_static")
+
+
+class Graph:
+    """A batch captured into a CUDA graph (lx_eri_graph_create); replay with launch()."""
+
+    def __init__(self, batch: "Batch", out, workspace):
+        self._keep = (out, workspace)
+        h = ctypes.c_void_p()
+        b = batch
+        rc = load().lx_eri_graph_create(_ptr(b.shells), len(b.shells), _ptr(b.exps), _ptr(b.coefs), len(b.exps),
+                                        _ptr(b.quartets), len(b.quartets), b.flags, ctypes.c_void_p(out.data_ptr()),
+                                        ctypes.c_void_p(workspace.data_ptr()),
+                                        workspace.numel() * workspace.element_size(), ctypes.byref(h))
+        _check(rc, "lx_eri_graph_create")
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(load().lx_eri_graph_launch(self.handle, ctypes.c_void_p(_stream_ptr(stream))), "lx_eri_graph_launch")
+
+    def close(self):
+        if self.handle:
+            load().lx_eri_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(batch: "Batch", max_keys=16, samples=8, workspace_bytes=None, stream=None):
+    """Time the FP64 GEMM tile shapes on the batch's costliest classes; returns the table rows."""
+    import torch
+    b = batch
+    ws_bytes = workspace_bytes or min(b.workspace_size(), 4 << 30)
+    ws = alloc_workspace(max(ws_bytes, b.workspace_min()))
+    nout = int(min(b.out_size, max(b.sizes[: max(samples, 1) * 64].sum(), int(b.sizes.max()) * samples)))
+    out = torch.empty(max(nout, 1), dtype=torch.float64, device=ws.device)
+    _check(load().lx_eri_autotune(_ptr(b.shells), len(b.shells), _ptr(b.exps), _ptr(b.coefs), len(b.exps),
+                                  _ptr(b.quartets), len(b.quartets), b.flags, ctypes.c_void_p(out.data_ptr()),
+                                  out.numel(), ctypes.c_void_p(ws.data_ptr()), ws.numel(), int(max_keys),
+                                  int(samples), ctypes.c_void_p(_stream_ptr(stream))), "lx_eri_autotune")
+    return tune_export()
+
+
+def tune_export() -> np.ndarray:
+    lib = load()
+    n = int(lib.lx_tune_export(None, 0))
+    rows = np.zeros((max(n, 1), 9), dtype=np.int32)
+    lib.lx_tune_export(_ptr(rows), n)
+    return rows[:n]
+
+
+def tune_import(rows):
+    rows = np.ascontiguousarray(rows, dtype=np.int32).reshape(-1, 9)
+    _check(load().lx_tune_import(_ptr(rows), len(rows)), "lx_tune_import")
+
+
+def tune_clear():
+    load().lx_tune_clear()
+
+
+TUNE_FORMAT = 1
+
+
+def save_tuning(path):
+    """Persist the tuning table as versioned JSON."""
+    import json
+    rows = tune_export()
+    with open(path, "w") as f:
+        json.dump({"format": TUNE_FORMAT, "columns": ["la", "lb", "lc", "ld", "kbra", "kket", "solid", "gemm1",
+                                                      "gemm2"], "shapes": TILE_SHAPES, "rows": rows.tolist()}, f)
+
+
+def load_tuning(path):
+    import json
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("format") != TUNE_FORMAT or d.get("shapes") != TILE_SHAPES:
+        raise ValueError(f"incompatible tuning file {path}")
+    tune_import(np.asarray(d["rows"], dtype=np.int32).reshape(-1, 9))
 
 
 def sync_status(stream=None):

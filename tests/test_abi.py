@@ -145,3 +145,20 @@ def test_sizes():
     off = np.arange(8, dtype=np.int64) * 13 ** 4 * 2
     b2 = lx.Batch(b, qs, True, out_off=off)
     assert b2.out_size == off[-1] + 13 ** 4
+
+
+def test_tuning_table_round_trip(tmp_path):
+    lx.tune_clear()
+    rows = np.array([[4, 4, 4, 4, 1, 1, 1, 0, 3], [6, 6, 6, 6, 4, 9, 0, 2, 1]], dtype=np.int32)
+    lx.tune_import(rows)
+    got = lx.tune_export()
+    assert sorted(map(tuple, got.tolist())) == sorted(map(tuple, rows.tolist()))
+    path = tmp_path / "tune.json"
+    lx.save_tuning(str(path))
+    lx.tune_clear()
+    assert len(lx.tune_export()) == 0
+    lx.load_tuning(str(path))
+    assert sorted(map(tuple, lx.tune_export().tolist())) == sorted(map(tuple, rows.tolist()))
+    with pytest.raises(lx.LxError):
+        lx.tune_import(np.array([[4, 4, 4, 4, 1, 1, 1, 9, 0]], dtype=np.int32))  # bad shape id
+    lx.tune_clear()
