@@ -45,6 +45,10 @@ def parse_args(argv=None):
     p.add_argument("--no-split", action="store_true", help="skip the split-precision measurement")
     p.add_argument("--no-mixed", action="store_true", help="skip the mixed-class graph measurement")
     p.add_argument("--mixed-quartets", type=int, default=1000)
+    p.add_argument("--no-split-config", action="store_true",
+                   help="skip the (hh|hh)+(ii|ii) K=1..3 split-path workload")
+    p.add_argument("--no-routed", action="store_true", help="skip the routed-workload sample")
+    p.add_argument("--routed-quartets", type=int, default=4000)
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
     return p.parse_args(argv)
 
@@ -438,6 +442,63 @@ def main(argv=None):
         del ref_m, outm
         torch.cuda.empty_cache()
 
+    # ---- split path at full size: 16384 (hh|hh) + 16384 (ii|ii), K = 1..3 per shell
+    split_cfg = None
+    if not args.no_split_config:
+        sb_, sq_ = inputs.split_hhhh_iiii()
+        sg1, sg2, _ = gemm_flops(sb_, sq_, True)
+        bsc = lx.Batch(sb_, sq_, solid=True, path="split")
+        outc = torch.empty(bsc.out_size, dtype=torch.float64, device="cuda")
+        wsc = lx.alloc_workspace(max(bsc.workspace_min(), min(bsc.workspace_size(), 64 << 30)))
+        cms, cstage, _ = time_steps(torch, lx, bsc, outc, wsc, 2, 1, flush_buf, world)
+        ctot = reduce_max(sum(cms), world)
+        # FP64 path and error on a 1024-quartet sample (512 of each class)
+        samp = np.concatenate([np.arange(512), len(sq_) // 2 + np.arange(512)])
+        ssb, ssq = inputs.subset(sb_, sq_, samp)
+        bsf = lx.Batch(ssb, ssq, solid=True)
+        outf = torch.empty(bsf.out_size, dtype=torch.float64, device="cuda")
+        fms, _, _ = time_steps(torch, lx, bsf, outf, lx.alloc_workspace(bsf.workspace_size()), 1, 1, flush_buf, 1)
+        offs = bsc.quartets["out_offset"]
+        gathered = torch.cat([outc[int(offs[i]):int(offs[i]) + int(bsc.sizes[i])] for i in samp])
+        split_cfg = {"workload": f"{len(sq_)} quartets: (hh|hh) and (ii|ii) halves, K = 1..3 per shell, 20-bohr cube, "
+                                 "exponents log-uniform [0.05, 20], solid harmonics, split path",
+                     "quartets_per_s": world * len(sq_) * 2 / (ctot * 1e-3), "ms_per_step": ctot / 2,
+                     "fp64_equiv_tflops": world * (sg1 + sg2) * 2 / (ctot * 1e-3) / 1e12,
+                     "stage_ms_per_step": {k: v / 2 for k, v in cstage.items()},
+                     "fp64_path_sample_quartets_per_s": len(samp) / (fms[0] * 1e-3),
+                     "max_abs_err_vs_fp64_path_on_sample": float((gathered - outf).abs().max())}
+        del wsc, outc, outf, gathered
+        torch.cuda.empty_cache()
+
+    # ---- routed workload sample: l = 4..6, K = 1..5, separations 0..30 bohr
+    routed = None
+    if not args.no_routed:
+        from paper_2307_03452_gb300 import router as rtr
+        if os.path.exists(rtr.WEIGHTS):
+            r = rtr.Router.load()
+            rb, rq = inputs.routed(nquartet=args.routed_quartets, seed=2311 + 7)
+            rg1, rg2, _ = gemm_flops(rb, rq, True)
+            rtr.routed_eri(rb, rq, r)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rout, roff, to_fp64 = rtr.routed_eri(rb, rq, r)
+            torch.cuda.synchronize()
+            t_routed = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            fout, _ = lx.eri(rb, rq, solid=True, path="fp64", workspace_limit=32 << 30)
+            torch.cuda.synchronize()
+            t_fp64 = time.perf_counter() - t0
+            routed = {"workload": f"{len(rq)} quartets, l = 4..6 and K = 1..5 per shell, pair centers within 3 bohr, "
+                                  "bra-ket separations 0..30 bohr, exponents log-uniform [0.05, 50], solid harmonics",
+                      "routed_quartets_per_s": len(rq) / t_routed, "fp64_quartets_per_s": len(rq) / t_fp64,
+                      "speedup": t_fp64 / t_routed, "fraction_to_fp64": float(to_fp64.mean()),
+                      "max_abs_err_vs_fp64_path": float((rout - fout).abs().max()), "tau": r.tau,
+                      "timing": "wall clock per call incl. features, MLP inference and host planning",
+                      "router_val_rmse_log10": r.meta.get("val_rmse_log10"),
+                      "baseline_rmse_log10": r.meta.get("baseline_rmse_log10")}
+            del rout, fout
+            torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
         cpu = cpu_baseline(basis, quartets, True, args.cpu_seconds)
@@ -454,7 +515,7 @@ def main(argv=None):
             "fp64_equiv_tflops": fp64_tf, "integrals_per_s": world * nint * args.steps / (total_ms * 1e-3),
             "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
             "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "cartesian": cart,
-            "split": split, "mixed": mixed,
+            "split": split, "mixed": mixed, "split_config": split_cfg, "routed": routed,
             "gpu_launches": int(sum(launches.values())),
         }
         print(json.dumps(line), flush=True)

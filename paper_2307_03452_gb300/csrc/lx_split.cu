@@ -202,6 +202,10 @@ __device__ inline int64_t dig_index(int row, int k, int s, int T, int nkb) {
     return block * (T * SPLIT_KB) + ((r >> 3) * (SPLIT_KB / 8) + (kk >> 3)) * 64 + (r & 7) * 8 + (kk & 7);
 }
 
+// Groups of 8 consecutive columns handled by one lane, cached in registers between the
+// exponent pass and the digit pass when the row is short enough.
+constexpr int CACHE_GROUPS = 4;  // per lane: rows up to 32 * 4 * 8 = 1024 columns are cached
+
 // One warp per row.  desc: the matrix; item.a = row (may be a padding row).
 __global__ void split_rows_kernel(const SplitRowsDesc* __restrict__ descs, const WorkItem* __restrict__ items,
                                   int nitems, const double* __restrict__ src_base, char* __restrict__ ws) {
@@ -213,29 +217,56 @@ __global__ void split_rows_kernel(const SplitRowsDesc* __restrict__ descs, const
     const double* src = src_base + d.src_off + (int64_t)row * d.ld;
     const bool live = row < d.rows;
     const int* shift = d.shift_off >= 0 ? reinterpret_cast<const int*>(ws + d.shift_off) : nullptr;
-    auto value = [&](int k) -> double { return shift ? scale2(src[k], d.shift_sign * shift[k]) : src[k]; };
+    auto value = [&](int k) -> double {
+        if (!live || k >= d.K) return 0.0;
+        return shift ? scale2(src[k], d.shift_sign * shift[k]) : src[k];
+    };
+    const int ngroup = d.nkb * SPLIT_KB / 8;
+    const bool cached = ngroup <= 32 * CACHE_GROUPS;
+    double cache[CACHE_GROUPS][8];
     int mx = 0;
-    if (live)
+    if (cached) {
+#pragma unroll
+        for (int j = 0; j < CACHE_GROUPS; ++j) {
+            const int g = lane + 32 * j;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const double x = g < ngroup ? value(8 * g + i) : 0.0;
+                cache[j][i] = x;
+                mx = max(mx, exp_field(x));
+            }
+        }
+    } else if (live) {
         for (int k = lane; k < d.K; k += 32) mx = max(mx, exp_field(value(k)));
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = mx > 0 ? mx - 1022 : 0;  // |x| < 2^e over the row
     __nv_bfloat16* dig = reinterpret_cast<__nv_bfloat16*>(ws + d.dig_off);
-    const int ngroup = d.nkb * SPLIT_KB / 8;
-    for (int g = lane; g < ngroup; g += 32) {
-        long long q[8];
+    if (cached) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int k = 8 * g + j;
-            q[j] = (mx > 0 && live && k < d.K) ? fixed_of(value(k), e) : 0ll;
+        for (int j = 0; j < CACHE_GROUPS; ++j) {
+            const int g = lane + 32 * j;
+            if (g >= ngroup) break;
+            long long q[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) q[i] = mx > 0 ? fixed_of(cache[j][i], e) : 0ll;
+            store_digit_group(dig, row, 8 * g, d.T, d.nkb, q);
         }
-        store_digit_group(dig, row, 8 * g, d.T, d.nkb, q);
+    } else {
+        for (int g = lane; g < ngroup; g += 32) {
+            long long q[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) q[i] = mx > 0 ? fixed_of(value(8 * g + i), e) : 0ll;
+            store_digit_group(dig, row, 8 * g, d.T, d.nkb, q);
+        }
     }
     if (lane == 0) reinterpret_cast<int*>(ws + d.exp_off)[row] = e;
 }
 
 // One warp per row q of the GEMM1 A operand: A[q][k] = [p+q]^(0) of primitive quartet
-// (kp, kq) with k = kp*Np + p, q = kq*Nq + qq.  item.q = quartet, item.a = row.
+// (kp, kq) with k = kp*Np + p, q = kq*Nq + qq, scaled by 2^-e1[k].  item.q = quartet,
+// item.a = row.  Each lane walks its groups of 8 columns with an incremental (kp, p).
 __global__ void split_r_kernel(const DQuartet* __restrict__ qd, const SplitQuartet* __restrict__ sq,
                                const WorkItem* __restrict__ items, int nitems, const double* __restrict__ wsd,
                                char* __restrict__ ws) {
@@ -253,29 +284,75 @@ __global__ void split_r_kernel(const DQuartet* __restrict__ qd, const SplitQuart
         kq = row / q.nq;
         tq = tuv_tab[row - kq * q.nq];
     }
-    const double* Rr = wsd + q.rr_off;
+    const double* Rr = wsd + q.rr_off + (int64_t)kq * q.nr;
+    const int64_t kp_stride = (int64_t)q.kket * q.nr;
     const int* e1 = reinterpret_cast<const int*>(ws + s.e1_off);
-    auto value = [&](int k) -> double {
-        const int kp = k / q.np, p = k - kp * q.np;
-        const int sum = tuv_tab[p] + tq;
-        return scale2(Rr[(int64_t)(kp * q.kket + kq) * q.nr + hidx(sum & 255, (sum >> 8) & 255, sum >> 16)], -e1[k]);
+    // the 8 values of group g (columns 8g .. 8g+7)
+    auto group = [&](int g, double (&v)[8]) {
+        int k = 8 * g;
+        int kp = k / q.np, p = k - kp * q.np;
+#pragma unroll
+        for (int i = 0; i < 8; ++i, ++k) {
+            double x = 0.0;
+            if (live && k < K) {
+                const int sum = tuv_tab[p] + tq;
+                x = scale2(Rr[kp * kp_stride + hidx(sum & 255, (sum >> 8) & 255, sum >> 16)], -e1[k]);
+            }
+            v[i] = x;
+            if (++p == q.np) {
+                p = 0;
+                ++kp;
+            }
+        }
     };
+    const int ngroup = s.nkb1 * SPLIT_KB / 8;
+    const bool cached = ngroup <= 32 * CACHE_GROUPS;
+    double cache[CACHE_GROUPS][8];
     int mx = 0;
-    if (live)
-        for (int k = lane; k < K; k += 32) mx = max(mx, exp_field(value(k)));
+    if (cached) {
+#pragma unroll
+        for (int j = 0; j < CACHE_GROUPS; ++j) {
+            const int g = lane + 32 * j;
+            if (g < ngroup) {
+                group(g, cache[j]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) cache[j][i] = 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) mx = max(mx, exp_field(cache[j][i]));
+        }
+    } else {
+        for (int g = lane; g < ngroup; g += 32) {
+            double v[8];
+            group(g, v);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) mx = max(mx, exp_field(v[i]));
+        }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = mx > 0 ? mx - 1022 : 0;
     __nv_bfloat16* dig = reinterpret_cast<__nv_bfloat16*>(ws + s.a1_dig);
-    const int ngroup = s.nkb1 * SPLIT_KB / 8;
-    for (int g = lane; g < ngroup; g += 32) {
-        long long qv[8];
+    if (cached) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int k = 8 * g + j;
-            qv[j] = (mx > 0 && live && k < K) ? fixed_of(value(k), e) : 0ll;
+        for (int j = 0; j < CACHE_GROUPS; ++j) {
+            const int g = lane + 32 * j;
+            if (g >= ngroup) break;
+            long long qv[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) qv[i] = mx > 0 ? fixed_of(cache[j][i], e) : 0ll;
+            store_digit_group(dig, row, 8 * g, SPLIT_TA, s.nkb1, qv);
         }
-        store_digit_group(dig, row, 8 * g, SPLIT_TA, s.nkb1, qv);
+    } else {
+        for (int g = lane; g < ngroup; g += 32) {
+            double v[8];
+            group(g, v);
+            long long qv[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) qv[i] = mx > 0 ? fixed_of(v[i], e) : 0ll;
+            store_digit_group(dig, row, 8 * g, SPLIT_TA, s.nkb1, qv);
+        }
     }
     if (lane == 0) reinterpret_cast<int*>(ws + s.a1_exp)[row] = e;
 }

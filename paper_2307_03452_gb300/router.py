@@ -107,8 +107,11 @@ def labels(basis, quartets, solid=True):
     return block_log10_max(out, off, b.sizes), out, off
 
 
-def routed_eri(basis, quartets, router: Router, solid=True, tau=None, device="cuda"):
-    """Evaluate with per-quartet routing; returns (out, offsets, route mask: True = FP64)."""
+def routed_eri(basis, quartets, router: Router, solid=True, tau=None, device="cuda",
+               workspace_limit: int = 16 << 30):
+    """Evaluate with per-quartet routing; returns (out, offsets, route mask: True = FP64).
+    Each of the two sub-batches is chunked to fit workspace_limit bytes of scratch (or the
+    smallest workspace that holds its largest quartet, if that is more)."""
     import torch
     tau = router.tau if tau is None else tau
     feat = lx.route_features(basis, quartets, device=device)
@@ -121,6 +124,7 @@ def routed_eri(basis, quartets, router: Router, solid=True, tau=None, device="cu
     for mask, path in ((to_fp64, "fp64"), (~to_fp64, "split")):
         if mask.any():
             b = lx.Batch(basis, qs[mask], solid, out_off=off[mask], path=path)
-            b.run(out, lx.alloc_workspace(b.workspace_size(), device))
+            need = max(min(b.workspace_size(), int(workspace_limit)), b.workspace_min())
+            b.run(out, lx.alloc_workspace(need, device))
     lx.sync_status()
     return out[: full.out_size], off, to_fp64
