@@ -407,9 +407,10 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             q.nkb2 = split_nkb(k2);
             P.sq.push_back(q);
             const int sb1 = (int)P.srd.size();
-            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k1, d.nab, k1, SPLIT_TB, q.nkb1, +1});   // B1: H_bra
+            const int tb1 = split_tb(d.nab), tb2 = split_tb(d.ncd);
+            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k1, d.nab, k1, tb1, q.nkb1, +1});   // B1: H_bra
             P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k2, d.nab, k2, SPLIT_TA, q.nkb2, +1});   // A2: X
-            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k2, d.ncd, k2, SPLIT_TB, q.nkb2, -1});   // B2: H_ket
+            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k2, d.ncd, k2, tb2, q.nkb2, -1});   // B2: H_ket
             const int c0 = (int)P.cmd.size();
             P.cmd.push_back(ColMaxDesc{0, 0, k1, d.nab, k1, 0});  // cmh1
             P.cmd.push_back(ColMaxDesc{0, 0, k2, d.ncd, k2, 0});  // cmh2
@@ -428,11 +429,11 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
                 P.items_b2.push_back({b0 + 1, c, 0, 0});
             }
             for (int row = 0; row < split_rowpad(k2, SPLIT_TA); ++row) P.items_sr.push_back({i, row, 0, 0});
-            for (int row = 0; row < split_rowpad(d.nab, SPLIT_TB); ++row) P.items_sB.push_back({sb1, row, 0, 0});
+            for (int row = 0; row < split_rowpad(d.nab, tb1); ++row) P.items_sB.push_back({sb1, row, 0, 0});
             for (int row = 0; row < split_rowpad(d.nab, SPLIT_TA); ++row) P.items_sD.push_back({sb1 + 1, row, 0, 0});
-            for (int row = 0; row < split_rowpad(d.ncd, SPLIT_TB); ++row) P.items_sD.push_back({sb1 + 2, row, 0, 0});
-            const int mt1 = split_rowpad(k2, SPLIT_TA) / SPLIT_TA, nt1 = (d.nab + SPLIT_TB - 1) / SPLIT_TB;
-            const int mt2 = split_rowpad(d.nab, SPLIT_TA) / SPLIT_TA, nt2 = (d.ncd + SPLIT_TB - 1) / SPLIT_TB;
+            for (int row = 0; row < split_rowpad(d.ncd, tb2); ++row) P.items_sD.push_back({sb1 + 2, row, 0, 0});
+            const int mt1 = split_rowpad(k2, SPLIT_TA) / SPLIT_TA, nt1 = (d.nab + tb1 - 1) / tb1;
+            const int mt2 = split_rowpad(d.nab, SPLIT_TA) / SPLIT_TA, nt2 = (d.ncd + tb2 - 1) / tb2;
             for (int m = 0; m < mt1; ++m)
                 for (int n = 0; n < nt1; ++n) P.items_sg1.push_back({i, m, n, 0});
             for (int m = 0; m < mt2; ++m)
@@ -491,12 +492,12 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             const int k1 = d.kbra * d.np, k2 = d.kket * d.nq;
             q.a1_dig = take_bytes(split_dig_bytes(k2, k1, SPLIT_TA));
             q.a1_exp = take_bytes(4 * (int64_t)split_rowpad(k2, SPLIT_TA));
-            q.b1_dig = take_bytes(split_dig_bytes(d.nab, k1, SPLIT_TB));
-            q.b1_exp = take_bytes(4 * (int64_t)split_rowpad(d.nab, SPLIT_TB));
+            q.b1_dig = take_bytes(split_dig_bytes(d.nab, k1, split_tb(d.nab)));
+            q.b1_exp = take_bytes(4 * (int64_t)split_rowpad(d.nab, split_tb(d.nab)));
             q.a2_dig = take_bytes(split_dig_bytes(d.nab, k2, SPLIT_TA));
             q.a2_exp = take_bytes(4 * (int64_t)split_rowpad(d.nab, SPLIT_TA));
-            q.b2_dig = take_bytes(split_dig_bytes(d.ncd, k2, SPLIT_TB));
-            q.b2_exp = take_bytes(4 * (int64_t)split_rowpad(d.ncd, SPLIT_TB));
+            q.b2_dig = take_bytes(split_dig_bytes(d.ncd, k2, split_tb(d.ncd)));
+            q.b2_exp = take_bytes(4 * (int64_t)split_rowpad(d.ncd, split_tb(d.ncd)));
             q.rmr_off = take_bytes(4 * (int64_t)k1);
             q.e1_off = take_bytes(4 * (int64_t)k1);
             q.e2_off = take_bytes(4 * (int64_t)k2);
@@ -541,6 +542,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             g1.nkb = q.nkb1;
             g1.ldc = k2;
             g1.transpose = 1;
+            g1.tb = split_tb(d.nab);
             P.sg1.push_back(g1);
             SplitGemmDesc g2{};
             g2.a_dig = q.a2_dig;
@@ -553,6 +555,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             g2.nkb = q.nkb2;
             g2.ldc = d.ncd;
             g2.transpose = 0;
+            g2.tb = split_tb(d.ncd);
             P.sg2.push_back(g2);
         }
     }
@@ -1204,15 +1207,16 @@ int lx_split_gemm(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda,
     if (v != LX_OK) return v;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const int nkb = split_nkb(K);
-    const int ra = split_rowpad(M, SPLIT_TA), rb = split_rowpad(N, SPLIT_TB);
+    const int tb = split_tb(N);
+    const int ra = split_rowpad(M, SPLIT_TA), rb = split_rowpad(N, tb);
     std::vector<SplitRowsDesc> rd(2);
     rd[0] = SplitRowsDesc{0, 0, 0, -1, lda, M, K, SPLIT_TA, nkb, 0};
-    rd[1] = SplitRowsDesc{0, 0, 0, -1, ldb, N, K, SPLIT_TB, nkb, 0};
+    rd[1] = SplitRowsDesc{0, 0, 0, -1, ldb, N, K, tb, nkb, 0};
     std::vector<WorkItem> ia, ib, ig;
     for (int r = 0; r < ra; ++r) ia.push_back({0, r, 0, 0});
     for (int r = 0; r < rb; ++r) ib.push_back({1, r, 0, 0});
     for (int m = 0; m < ra / SPLIT_TA; ++m)
-        for (int n = 0; n < (N + SPLIT_TB - 1) / SPLIT_TB; ++n) ig.push_back({0, m, n, 0});
+        for (int n = 0; n < (N + tb - 1) / tb; ++n) ig.push_back({0, m, n, 0});
     size_t o = 0;
     auto region = [&](size_t bytes) {
         const size_t at = o;
@@ -1225,9 +1229,9 @@ int lx_split_gemm(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda,
     const size_t blob_bytes = o;
     rd[0].dig_off = (int64_t)region((size_t)split_dig_bytes(M, K, SPLIT_TA));
     rd[0].exp_off = (int64_t)region(4 * (size_t)ra);
-    rd[1].dig_off = (int64_t)region((size_t)split_dig_bytes(N, K, SPLIT_TB));
+    rd[1].dig_off = (int64_t)region((size_t)split_dig_bytes(N, K, tb));
     rd[1].exp_off = (int64_t)region(4 * (size_t)rb);
-    SplitGemmDesc g{rd[0].dig_off, rd[0].exp_off, rd[1].dig_off, rd[1].exp_off, 0, M, N, nkb, ldc, 0, 0};
+    SplitGemmDesc g{rd[0].dig_off, rd[0].exp_off, rd[1].dig_off, rd[1].exp_off, 0, M, N, nkb, ldc, 0, tb};
     std::vector<char> blob(blob_bytes, 0);
     std::memcpy(blob.data() + o_rd, rd.data(), sizeof(SplitRowsDesc) * 2);
     std::memcpy(blob.data() + o_g, &g, sizeof(g));

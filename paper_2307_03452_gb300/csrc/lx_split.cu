@@ -404,11 +404,13 @@ __global__ void balance_kernel(const BalanceDesc* __restrict__ descs, const Work
 
 constexpr int STAGES = 2;
 constexpr int A_BLOCK = SPLIT_NSLICE * SPLIT_TA * SPLIT_KB * 2;  // bytes of one A block (all slices)
-constexpr int B_BLOCK = SPLIT_NSLICE * SPLIT_TB * SPLIT_KB * 2;
+constexpr int B_BLOCK_MAX = SPLIT_NSLICE * SPLIT_TB * SPLIT_KB * 2;
 constexpr int A_SLICE = SPLIT_TA * SPLIT_KB * 2;
-constexpr int B_SLICE = SPLIT_TB * SPLIT_KB * 2;
+constexpr int STAGE_BYTES = A_BLOCK + B_BLOCK_MAX;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int SMEM_BYTES = STAGES * (A_BLOCK + B_BLOCK) + 1024;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr int GEMM_THREADS = 192;  // warp 0 TMA, warp 1 MMA issue + TMEM, warps 2..5 drain / epilogue
+constexpr int NCHUNK = SPLIT_TB / 16;
 
 // int64 -> FP64 times 2^scale, correctly rounded (round to nearest even), integer ops only.
 __device__ inline double i64_to_f64_scaled(long long v, int scale) {
@@ -440,27 +442,47 @@ __device__ inline double i64_to_f64_scaled(long long v, int scale) {
     return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
+__device__ inline void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // item.q = problem, item.a = M tile, item.b = N tile.
-__global__ void __launch_bounds__(128, 1) split_gemm_kernel(const SplitGemmDesc* __restrict__ probs,
-                                                            const WorkItem* __restrict__ items,
-                                                            const char* __restrict__ ws, double* __restrict__ cbase,
-                                                            unsigned* status) {
+//
+// Accumulation is exact.  Every digit is an integer with |d_0| <= 2^BETA and |d_s| <= 2^(BETA-1)
+// for s > 0, so one k adds at most 2^17 to any diagonal d = s + t (2 * 2^15 + (d - 1) * 2^14 for
+// d >= 2, 2^16 for d < 2).  The MMAs of SPLIT_SEG_KB K blocks (128 k) therefore leave every
+// FP32 accumulator, and every partial sum on the way, an integer of magnitude <= 2^24, which
+// FP32 holds exactly; the four drain warps then move the diagonals into 64-bit integers and
+// the next segment starts its accumulators from zero.  Per k the combined value is at most
+// 2^(2W - 48) = 2^48, so the 64-bit sum is shifted down by xs bits when K exceeds 2^14.
+//
+// The MMAs of one A slice s and one K step are issued against the B slices 0..NSLICE-1-s at
+// once: slice t lies tb rows after slice t-1 in shared memory and diagonal s + t lies tb TMEM
+// columns after s + t - 1, so A_s [B_0; B_1; ...] lands every product on its diagonal (split
+// into pieces of at most 256 columns, the largest MMA N).
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+    split_gemm_kernel(const SplitGemmDesc* __restrict__ probs, const WorkItem* __restrict__ items,
+                      const char* __restrict__ ws, double* __restrict__ cbase, unsigned* status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned operand stages
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], seg_bar, drained_bar, final_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const WorkItem it = items[blockIdx.x];
     const SplitGemmDesc P = probs[it.q];
-    const int m0 = it.a * SPLIT_TA, n0 = it.b * SPLIT_TB;
-    int nt = P.N - n0;
-    nt = nt > SPLIT_TB ? SPLIT_TB : ((nt + 15) & ~15);
+    const int tb = P.tb;
+    const int b_block = SPLIT_NSLICE * tb * SPLIT_KB * 2;
+    const int m0 = it.a * SPLIT_TA, n0 = it.b * tb;
+    const int nt = min(tb, P.N - n0);
     const int nkb = P.nkb;
+    const int nseg = (nkb + SPLIT_SEG_KB - 1) / SPLIT_SEG_KB;
+    const int kpad = nkb * SPLIT_KB;
+    const int xs = max(0, 32 - __clz(kpad - 1) - 14);  // ceil(log2 K) - 14, if positive
 
-    if (warp == 0) {
+    if (warp == 1) {
         tmem_alloc(&tmem_base_sh, TMEM_COLS);
         tmem_relinquish();
     }
@@ -469,7 +491,9 @@ __global__ void __launch_bounds__(128, 1) split_gemm_kernel(const SplitGemmDesc*
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
-        mbar_init(&done_bar, 1);
+        mbar_init(&seg_bar, 1);
+        mbar_init(&drained_bar, 4);
+        mbar_init(&final_bar, 1);
         abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -479,107 +503,148 @@ __global__ void __launch_bounds__(128, 1) split_gemm_kernel(const SplitGemmDesc*
     const uint32_t tmem = tmem_base_sh;
 
     const char* a_src = ws + P.a_dig + (int64_t)it.a * nkb * A_BLOCK;
-    const char* b_src = ws + P.b_dig + (int64_t)it.b * nkb * B_BLOCK;
+    const char* b_src = ws + P.b_dig + (int64_t)it.b * nkb * b_block;
 
-    if (warp == 0 && lane == 0) {
-        // producer: stream the A and B blocks of each K block into the ring of stages
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int st = kb % STAGES, use = kb / STAGES;
-            if (use > 0 && !mbar_wait(&empty_bar[st], (use - 1) & 1, status)) {
-                abort_sh = 1;
-                break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: stream the A and B blocks of each K block into the ring of stages
+            int issued = 0;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int st = kb % STAGES, use = kb / STAGES;
+                if (use > 0 && !mbar_wait(&empty_bar[st], (use - 1) & 1, status)) {
+                    abort_sh = 1;
+                    break;
+                }
+                if (*(volatile int*)&abort_sh) break;
+                unsigned char* sa = smem + st * STAGE_BYTES;
+                unsigned char* sb = sa + A_BLOCK;
+                mbar_expect_tx(&full_bar[st], A_BLOCK + b_block);
+                bulk_g2s(sa, a_src + (int64_t)kb * A_BLOCK, A_BLOCK, &full_bar[st]);
+                bulk_g2s(sb, b_src + (int64_t)kb * b_block, b_block, &full_bar[st]);
+                issued = kb + 1;
             }
-            if (abort_sh) break;
-            unsigned char* sa = smem + st * (A_BLOCK + B_BLOCK);
-            unsigned char* sb = sa + A_BLOCK;
-            mbar_expect_tx(&full_bar[st], A_BLOCK + B_BLOCK);
-            bulk_g2s(sa, a_src + (int64_t)kb * A_BLOCK, A_BLOCK, &full_bar[st]);
-            bulk_g2s(sb, b_src + (int64_t)kb * B_BLOCK, B_BLOCK, &full_bar[st]);
+            // no copy may still be landing in shared memory when the CTA exits
+            for (int st = 0; st < STAGES && st < issued; ++st) {
+                const int last = issued - 1 - ((issued - 1 - st) % STAGES);
+                if (!mbar_wait(&full_bar[st], (last / STAGES) & 1, status)) abort_sh = 1;
+            }
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer: diagonal d = s + t accumulates in TMEM columns [d * TB, d * TB + nt)
-        const uint32_t idesc = idesc_bf16(SPLIT_TA, nt);
-        bool started[SPLIT_NSLICE];
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t sbase = smem_u32(smem);
+            for (int seg = 0; seg < nseg; ++seg) {
+                if (seg > 0) {
+                    if (!mbar_wait(&drained_bar, (seg - 1) & 1, status)) abort_sh = 1;
+                    tc_fence_after();
+                }
+                if (*(volatile int*)&abort_sh) break;
+                const int kb0 = seg * SPLIT_SEG_KB, kb1 = min(nkb, kb0 + SPLIT_SEG_KB);
+                bool ok = true;
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    const int st = kb % STAGES, use = kb / STAGES;
+                    if (!mbar_wait(&full_bar[st], use & 1, status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = sbase + st * STAGE_BYTES;
+                    const uint32_t sb = sa + A_BLOCK;
 #pragma unroll
-        for (int d = 0; d < SPLIT_NSLICE; ++d) started[d] = false;
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int st = kb % STAGES, use = kb / STAGES;
-            if (!mbar_wait(&full_bar[st], use & 1, status)) {
-                abort_sh = 1;
-                break;
+                    for (int ks = 0; ks < SPLIT_KB / 16; ++ks) {
+#pragma unroll
+                        for (int s = 0; s < SPLIT_NSLICE; ++s) {
+                            const uint64_t ad = smem_desc(sa + s * A_SLICE + ks * 256, 128, (SPLIT_KB / 8) * 128);
+                            const int rows = (SPLIT_NSLICE - s) * tb;  // B slices 0 .. NSLICE-1-s
+                            for (int r0 = 0; r0 < rows; r0 += 256) {
+                                const int n = min(256, rows - r0);
+                                const uint64_t bd =
+                                    smem_desc(sb + (r0 >> 3) * (SPLIT_KB / 8) * 128 + ks * 256, 128, (SPLIT_KB / 8) * 128);
+                                // the slice-0 MMAs of a segment's first K step cover every diagonal
+                                const uint32_t acc = (kb == kb0 && ks == 0 && s == 0) ? 0u : 1u;
+                                umma_bf16(tmem + s * tb + r0, ad, bd, idesc_bf16(SPLIT_TA, n), acc);
+                            }
+                        }
+                    }
+                    umma_commit(&empty_bar[st]);  // the stage is free once these MMAs have read it
+                }
+                if (!ok) {
+                    abort_sh = 1;
+                    break;
+                }
+                umma_commit(&seg_bar);
             }
+            // every MMA issued has completed before TMEM is released
+            umma_commit(&final_bar);
+            if (!mbar_wait(&final_bar, 0, status)) abort_sh = 1;
+        }
+    } else {
+        // drain / epilogue: warp w reads TMEM lanes (rows) 32 (w % 4) .. 32 (w % 4) + 31
+        const int quarter = warp & 3;
+        const int row = m0 + quarter * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+        long long acc[NCHUNK][16];
+#pragma unroll
+        for (int c = 0; c < NCHUNK; ++c)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[c][j] = 0;
+        bool ok = true;
+        for (int seg = 0; seg < nseg; ++seg) {
+            const bool w = mbar_wait(&seg_bar, seg & 1, status);
+            ok = __all_sync(0xffffffffu, w) && !*(volatile int*)&abort_sh;
+            if (!ok) break;
             tc_fence_after();
-            const uint32_t sa = smem_u32(smem + st * (A_BLOCK + B_BLOCK));
-            const uint32_t sb = sa + A_BLOCK;
 #pragma unroll
-            for (int ks = 0; ks < SPLIT_KB / 16; ++ks) {
+            for (int c = 0; c < NCHUNK; ++c) {
+                if (16 * c >= nt) break;
 #pragma unroll
-                for (int s = 0; s < SPLIT_NSLICE; ++s) {
-                    const uint64_t ad = smem_desc(sa + s * A_SLICE + ks * 256, 128, (SPLIT_KB / 8) * 128);
+                for (int dg = 0; dg < SPLIT_NSLICE; ++dg) {
+                    uint32_t r[16];
+                    tmem_ld16(lane_base + dg * tb + 16 * c, r);
+                    tmem_ld_wait();
+                    // acc += G_d 2^(BETA (NSLICE-2-d)) (>> xs); the last diagonal is rounded down BETA bits
 #pragma unroll
-                    for (int t = 0; t < SPLIT_NSLICE - s; ++t) {
-                        const int dg = s + t;
-                        const uint64_t bd = smem_desc(sb + t * B_SLICE + ks * 256, 128, (SPLIT_KB / 8) * 128);
-                        umma_bf16(tmem + dg * SPLIT_TB, ad, bd, idesc, started[dg] ? 1u : 0u);
-                        started[dg] = true;
-                    }
-                }
-            }
-            umma_commit(&empty_bar[st]);  // the stage is free once these MMAs have read it
-        }
-        umma_commit(&done_bar);
-    }
-    __syncwarp();
-    // epilogue: all four warps; warp w owns TMEM lanes (rows) 32w .. 32w+31
-    const bool waited = mbar_wait(&done_bar, 0, status);
-    tc_fence_after();
-    // one decision for the whole CTA before the warp-collective TMEM loads
-    const bool ok = __syncthreads_and(waited && !abort_sh) != 0;
-    if (ok) {
-        const int row = m0 + warp * 32 + lane;
-        const bool rlive = row < P.M;
-        const int ea = rlive ? reinterpret_cast<const int*>(ws + P.a_exp)[row] : 0;
-        const int* eb_tab = reinterpret_cast<const int*>(ws + P.b_exp);
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c0 = 0; c0 < nt; c0 += 16) {
-            long long acc[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) acc[j] = 0;
-#pragma unroll
-            for (int dg = 0; dg < SPLIT_NSLICE; ++dg) {
-                uint32_t r[16];
-                tmem_ld16(lane_base + dg * SPLIT_TB + c0, r);
-                tmem_ld_wait();
-                // acc = sum_d G_d 2^(BETA (NSLICE-2-d)); the last diagonal is rounded down BETA bits
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const long long g = (long long)__float2int_rn(__uint_as_float(r[j]));
-                    if (dg < SPLIT_NSLICE - 1)
-                        acc[j] += g << (SPLIT_BETA * (SPLIT_NSLICE - 2 - dg));
-                    else
-                        acc[j] += (g + (1ll << (SPLIT_BETA - 1))) >> SPLIT_BETA;
-                }
-            }
-            if (rlive) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = n0 + c0 + j;
-                    if (col < P.N) {
-                        // D = 2^(eA + eB - 2W + BETA NSLICE) * acc
-                        const int scale = ea + eb_tab[col] - 2 * SPLIT_W + SPLIT_BETA * SPLIT_NSLICE;
-                        const double v = i64_to_f64_scaled(acc[j], scale);
-                        if (P.transpose)
-                            cbase[P.c_off + (int64_t)col * P.ldc + row] = v;
+                    for (int j = 0; j < 16; ++j) {
+                        const long long g = (long long)__float2int_rn(__uint_as_float(r[j]));
+                        long long v;
+                        if (dg < SPLIT_NSLICE - 1)
+                            v = g << (SPLIT_BETA * (SPLIT_NSLICE - 2 - dg));
                         else
-                            cbase[P.c_off + (int64_t)row * P.ldc + col] = v;
+                            v = (g + (1ll << (SPLIT_BETA - 1))) >> SPLIT_BETA;
+                        acc[c][j] += xs ? (v + (1ll << (xs - 1))) >> xs : v;
                     }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&drained_bar);
+        }
+        if (ok) {
+            // every MMA has completed and every copy has been consumed: the operand stages are
+            // free, so the sums go through shared memory and the conversion loop stays rolled
+            long long* stage = reinterpret_cast<long long*>(smem) + (int64_t)(quarter * 32 + lane) * SPLIT_TB;
+#pragma unroll
+            for (int c = 0; c < NCHUNK; ++c)
+#pragma unroll
+                for (int j = 0; j < 16; ++j) stage[16 * c + j] = acc[c][j];
+            if (row < P.M) {
+                const int ea = reinterpret_cast<const int*>(ws + P.a_exp)[row];
+                const int* eb_tab = reinterpret_cast<const int*>(ws + P.b_exp);
+                for (int j = 0; j < nt; ++j) {
+                    const int col = n0 + j;
+                    // D = 2^(eA + eB - 2W + BETA NSLICE + xs) * acc
+                    const int scale = ea + eb_tab[col] - 2 * SPLIT_W + SPLIT_BETA * SPLIT_NSLICE + xs;
+                    const double v = i64_to_f64_scaled(stage[j], scale);
+                    if (P.transpose)
+                        cbase[P.c_off + (int64_t)col * P.ldc + row] = v;
+                    else
+                        cbase[P.c_off + (int64_t)row * P.ldc + col] = v;
                 }
             }
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+    if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
 }
 
 }  // namespace
@@ -631,7 +696,7 @@ cudaError_t init_split_kernels(const int* host_tuv) {
 cudaError_t launch_split_gemm(const SplitGemmDesc* probs, const WorkItem* items, int nitems, const char* ws,
                               double* cbase, unsigned* status, cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
-    split_gemm_kernel<<<nitems, 128, SMEM_BYTES, st>>>(probs, items, ws, cbase, status);
+    split_gemm_kernel<<<nitems, GEMM_THREADS, SMEM_BYTES, st>>>(probs, items, ws, cbase, status);
     return cudaGetLastError();
 }
 

@@ -13,7 +13,8 @@ constexpr int SPLIT_BETA = 8;                        // bits per digit
 constexpr int SPLIT_W = SPLIT_NSLICE * SPLIT_BETA;   // fixed-point bits kept (48)
 constexpr int SPLIT_KB = 32;                         // K block (elements) of one pipeline stage
 constexpr int SPLIT_TA = 128;                        // A row tile = MMA M
-constexpr int SPLIT_TB = 80;                         // B row tile = largest MMA N (6 x 80 TMEM columns)
+constexpr int SPLIT_TB = 80;                         // largest B row tile (6 diagonals x 80 TMEM columns)
+constexpr int SPLIT_SEG_KB = 4;                      // K blocks accumulated in TMEM between int64 drains
 
 // One matrix whose rows are split: src at (double*)base + src_off, row stride ld.  Before
 // splitting, column k is multiplied by 2^(shift_sign * shift[k]) (exact; shift_off < 0: none).
@@ -50,13 +51,22 @@ struct SplitQuartet {
     int nkb1, nkb2;
 };
 
-// D = A B^T: A digits (row tiles of SPLIT_TA), B digits (row tiles of SPLIT_TB), both with nkb
-// K blocks; D written to (double*)C + c_off with row stride ldc (transpose: D[m][n] -> C[n][m]).
+// D = A B^T: A digits (row tiles of SPLIT_TA), B digits (row tiles of tb = split_tb(N)), both
+// with nkb K blocks; D written to (double*)C + c_off with row stride ldc (transpose: D[m][n] ->
+// C[n][m]).
 struct SplitGemmDesc {
     int64_t a_dig, a_exp, b_dig, b_exp;
     int64_t c_off;
-    int M, N, nkb, ldc, transpose, pad;
+    int M, N, nkb, ldc, transpose, tb;
 };
+
+// B row tile for an operand of N rows: as many tiles as SPLIT_TB rows need, made as even as
+// a multiple of 16 allows (169 rows -> 3 tiles of 64 rather than 80 + 80 + 9).
+__host__ __device__ inline int split_tb(int N) {
+    const int tiles = (N + SPLIT_TB - 1) / SPLIT_TB;
+    const int t = (N + tiles - 1) / tiles;
+    return (t + 15) / 16 * 16;
+}
 
 __host__ __device__ inline int split_rowpad(int rows, int T) { return (rows + T - 1) / T * T; }
 __host__ __device__ inline int split_nkb(int K) { return (K + SPLIT_KB - 1) / SPLIT_KB; }

@@ -3,8 +3,9 @@
 lx_split_gemm (C = A B^T) is checked first on integer-valued matrices whose split is exact,
 so the tensor-core result must equal the FP64 product bit for bit (this pins the operand
 layout, the descriptors and the recombination), then on random matrices against the
-error bound of 40-bit operands.  The ERI split path is checked against the oracle at the
-spec bound (max abs error 1e-10) on split-path classes."""
+error bound of 48-bit operands, and on long positive rows, where the FP32 tensor-core
+accumulators would round unless they are drained to 64-bit integers often enough.  The ERI
+split path is checked against the oracle at max abs error 1e-10 on split-path classes."""
 import numpy as np
 import pytest
 
@@ -27,7 +28,7 @@ SHAPES = [(1, 1, 1), (128, 96, 32), (129, 97, 33), (300, 200, 455), (455, 169, 4
 
 @pytest.mark.parametrize("M,N,K", SHAPES)
 def test_split_gemm_exact_on_integer_rows(M, N, K):
-    # rows: integers |x| < 2^12 times a per-row power of two -> 40-bit split is exact and every
+    # rows: integers |x| < 2^12 times a per-row power of two -> the 48-bit split is exact and every
     # partial sum stays exact, so C must equal the FP64 product exactly
     rng = np.random.default_rng(M * 1000 + N + K)
     A = rng.integers(-4095, 4096, (M, K)).astype(np.float64) * np.exp2(rng.integers(-20, 20, (M, 1)))
@@ -39,15 +40,31 @@ def test_split_gemm_exact_on_integer_rows(M, N, K):
 
 @pytest.mark.parametrize("M,N,K", SHAPES)
 def test_split_gemm_random_within_bound(M, N, K):
-    # 40-bit operands and the dropped digit products (s + t >= 5): worst case
-    # |C - AB^T| <= K * 2^-36 * max_k|A_ik| * max_k|B_jk|
+    # 48-bit operands (x = q 2^(e-48), |x| < 2^e <= 2|x|max) and the dropped digit products
+    # (s + t >= 6) cost at most ~2.3 units of 2^(eA+eB-48) per k:
+    # |C - AB^T| <= K * 2^-43 * max_k|A_ik| * max_k|B_jk| with room to spare
     rng = np.random.default_rng(7 + M + N + K)
     A = rng.normal(size=(M, K)) * np.exp(rng.uniform(-5, 5, (M, 1)))
     B = rng.normal(size=(N, K)) * np.exp(rng.uniform(-5, 5, (N, 1)))
     ref = A @ B.T
     C = lx.split_gemm(torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda")).cpu().numpy()
-    bound = K * 2.0 ** -36 * np.outer(np.abs(A).max(1), np.abs(B).max(1))
+    bound = K * 2.0 ** -43 * np.outer(np.abs(A).max(1), np.abs(B).max(1))
     assert np.all(np.abs(C - ref) <= bound)
+
+
+@pytest.mark.parametrize("K", [300, 4096, 20000])
+def test_split_gemm_long_positive_rows_stay_exact(K):
+    # entries in [1, 2): every leading digit is 128..256, so one diagonal grows by ~2^15 per k
+    # and passes 2^24 after a few hundred k.  Rounding there would cost ~1e-6 relative; the
+    # periodic int64 drains keep the error at the 48-bit bound (K = 20000 also takes the
+    # extra shift that keeps the 64-bit sum clear of overflow).
+    rng = np.random.default_rng(K)
+    A = rng.uniform(1.0, 2.0, (40, K))
+    B = rng.uniform(1.0, 2.0, (24, K))
+    ref = A @ B.T
+    C = lx.split_gemm(torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda")).cpu().numpy()
+    bound = K * 2.0 ** -43 * np.outer(np.abs(A).max(1), np.abs(B).max(1))
+    assert np.all(np.abs(C - ref) <= bound), f"max rel err {np.abs(C / ref - 1).max():.3e}"
 
 
 def _split_vs_oracle(basis, quartets, solid):
