@@ -92,9 +92,10 @@ int ensure_device(unsigned** status) {
         std::vector<int> tuv(NHERM_TOT);
         make_tuv_table(tuv.data());
         if ((e = init_boys_table(boys.data())) != cudaSuccess) return cuda_fail(e);
-        std::vector<SolidClassTab> cls(LMAX + 1);
-        make_solid_classes(solid.data(), cls.data());
-        if ((e = init_prep_tables(solid.data(), tuv.data(), cls.data())) != cudaSuccess) return cuda_fail(e);
+        static FoldHost fold;  // identical for every device; built once
+        static const bool fold_ok = make_fold_lists(solid.data(), fold);
+        if (!fold_ok) return LX_ERR_SIZE;
+        if ((e = init_prep_tables(solid.data(), tuv.data(), &fold)) != cudaSuccess) return cuda_fail(e);
         if ((e = init_tuv_table(tuv.data())) != cudaSuccess) return cuda_fail(e);
         if ((e = init_split_kernels(tuv.data())) != cudaSuccess) return cuda_fail(e);
         if ((e = init_router_kernels()) != cudaSuccess) return cuda_fail(e);
@@ -663,7 +664,7 @@ int plan_batch(const lx_shell* shells, int32_t nshell, const double* exps, const
 // bytes to upload (pageable, or pinned for graph capture).
 int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector<const char*>& blob_src, double* out,
                   void* workspace, unsigned* status, cudaStream_t st, bool time_stages) {
-    const bool split = B.flags & LX_PATH_SPLIT;
+    const bool split = B.flags & LX_PATH_SPLIT, solid = B.flags & LX_SOLID;
     const int nshell = B.nshell;
     char* wsb = static_cast<char*>(workspace);
     double* ws = static_cast<double*>(workspace);
@@ -689,8 +690,8 @@ int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector
         const WorkItem* d_ig1 = reinterpret_cast<const WorkItem*>(base + P.off_g1);
         const WorkItem* d_ig2 = reinterpret_cast<const WorkItem*>(base + P.off_g2);
         if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
-        if ((e = launch_pair_h(d_pairs, d_ih, (int)P.items_h.size(), d_sh, d_exps, d_ncoef, ws, ws, status, st)) !=
-            cudaSuccess)
+        if ((e = launch_pair_h(d_pairs, d_ih, (int)P.items_h.size(), d_sh, d_exps, d_ncoef, ws, ws, solid, status,
+                               st)) != cudaSuccess)
             return cuda_fail(e);
         if ((e = tm.end(LX_STAGE_PAIR, 1)) != cudaSuccess) return cuda_fail(e);
         if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
@@ -1192,7 +1193,8 @@ int lx_hermite_H(const lx_shell* shells, int32_t nshell, const double* exps, con
     if ((e = launch_norm(d_sh, nshell, d_exps, d_coefs, d_ncoef, status, st)) != cudaSuccess) return cuda_fail(e);
     if ((e = launch_pair_h(reinterpret_cast<const DPair*>(scratch + o_pairs),
                            reinterpret_cast<const WorkItem*>(scratch + o_items), (int)items.size(), d_sh, d_exps,
-                           d_ncoef, H, reinterpret_cast<double*>(scratch + o_info), status, st)) != cudaSuccess)
+                           d_ncoef, H, reinterpret_cast<double*>(scratch + o_info), solid, status, st)) !=
+        cudaSuccess)
         return cuda_fail(e);
     if ((e = cudaFreeAsync(scratch, st)) != cudaSuccess) return cuda_fail(e);
     return LX_OK;

@@ -72,15 +72,16 @@ struct WorkItem {  // generic work descriptor: owner + two tile indices
 // ----------------------------------------------------------------- per-TU launchers
 // Tables (called once per device with that device current).
 cudaError_t init_boys_table(const double* host_table);      // lx_boys_r.cu
-cudaError_t init_prep_tables(const double* host_coefs, const int* host_tuv, const void* host_classes);  // lx_prep.cu
+cudaError_t init_prep_tables(const double* host_coefs, const int* host_tuv,
+                             const void* host_fold);  // lx_prep.cu (host_fold: const FoldHost*)
 cudaError_t init_tuv_table(const int* host_tuv);           // lx_gemm.cu
 
 cudaError_t launch_norm(const DShell* sh, int nshell, const double* exps, const double* coefs, double* ncoef,
                         unsigned* status, cudaStream_t st);
 // H blocks at ws + h_off, pair scalars at ws_info + info_off.
 cudaError_t launch_pair_h(const DPair* pairs, const WorkItem* items, int nitems, const DShell* sh,
-                          const double* exps, const double* ncoef, double* ws, double* ws_info, unsigned* status,
-                          cudaStream_t st);
+                          const double* exps, const double* ncoef, double* ws, double* ws_info, bool solid,
+                          unsigned* status, cudaStream_t st);
 cudaError_t launch_boys_r(const DQuartet* qd, const DPair* pairs, const WorkItem* items, int nitems, double* ws,
                           unsigned* status, cudaStream_t st);
 // items grouped by tile shape: counts[v] items of shape v, in shape order; counters[v] is the
@@ -110,14 +111,32 @@ constexpr int GEMM_BK = 16;
 
 // Real solid harmonics have fixed parities of the x, y, z exponents, so the matrix C of one
 // shell is block diagonal over the (at most 4) parity classes of its Cartesian components.
-constexpr int SC_MAXA = 10;  // Cartesian components in one class (l <= 6)
-constexpr int SC_MAXM = 4;   // solid functions in one class (l <= 6)
-struct SolidClassTab {
-    int ncls;
-    int na[4], nm[4];
-    int comp[4][SC_MAXA];  // packed exponents ax | ay << 8 | az << 16
-    int mind[4][SC_MAXM];  // m + l of each solid function
-    double c[4][SC_MAXM][SC_MAXA];
+
+// Factorised solid fold of one primitive pair (la, lb), per solid function m_b of b:
+//   Q[ay az bx u v]   = sum_by C_b[m_b][bx by bz] E^y_{ay by u} E^z_{az bz v}   (bz = lb - bx - by)
+//   W[a u v t]        = sum_bx E^x_{ax bx t} Q[ay az bx u v]
+//   H[m_a m_b][t u v] = sum_a C_a[m_a][a] W[a t u v]
+// Only entries that can be nonzero (t <= ax + bx, u <= ay + by, v <= az + bz, nonzero C) are
+// kept.  Each stage's rows are sorted by length and stored in groups of 32 (one per warp):
+// entry j of row 32 g + i is ent[gptr[g] + 32 j + i], for j < (gptr[g+1] - gptr[g]) / 32, and
+// short rows are padded with null entries that multiply by an explicit zero.
+//   Q entry: coefficient index (m_b ncart(lb) + b) | E^y index << 9 | E^z index << 19
+//   W entry: E^x index | Q row << 10
+//   H entry: coefficient index (m_a ncart(la) + a) | W row << 9; h_out[row] = m_a | p << 4
+// E^d index = (i (lb+1) + j) (la+lb+1) + t for exponents (i, j) on a and b.  Coefficient
+// index FOLD_CMAX and Q row FOLD_QMAX hold zeros.
+constexpr int FOLD_QMAX = 3304;   // largest Q row count of one m_b (la = lb = 6)
+constexpr int FOLD_WMAX = 7490;   // largest W row count of one m_b (la = lb = 6)
+constexpr int FOLD_CMAX = NSOL_MAX * NCART_MAX;  // coefficients of one shell (364)
+constexpr int FOLD_QNULL = FOLD_CMAX;                         // Q null entry
+constexpr int FOLD_WNULL = FOLD_QMAX << 10;                   // W null entry
+constexpr int FOLD_HNULL = FOLD_CMAX;                         // H null entry
+struct FoldSeg {
+    int q_grp0, q_nrow, w_grp0, w_nrow, h_grp0, h_row0;  // first group of each stage; h_out offset
+};
+struct FoldPairTab {
+    int seg0;  // segments seg0 .. seg0 + 2 lb (one per m_b)
+    int maxq, maxw;
 };
 
 // Host-side table generators (lx_tables.cpp).
@@ -125,6 +144,16 @@ void make_boys_table(double* table);        // BOYS_NROW * BOYS_NPT
 void make_solid_coefs(double* coefs);       // packed: l = 0..LMAX, (2l+1) x ncart(l) each
 int solid_offset(int l);                    // offset of shell l's block in the packed array
 void make_tuv_table(int* tuv);              // NHERM_TOT entries: t | u << 8 | v << 16
-void make_solid_classes(const double* coefs, SolidClassTab* tab);  // tab[LMAX + 1]
+}  // namespace lx
+
+#include <vector>
+namespace lx {
+struct FoldHost {
+    std::vector<int> q_gptr, q_ent, w_gptr, w_ent, h_gptr, h_ent, h_out;
+    std::vector<FoldSeg> segs;
+    FoldPairTab pair[LMAX + 1][LMAX + 1];
+};
+// Compressed fold lists for every (la, lb); false if a count exceeds FOLD_QMAX / FOLD_WMAX.
+bool make_fold_lists(const double* coefs, FoldHost& F);
 
 }  // namespace lx

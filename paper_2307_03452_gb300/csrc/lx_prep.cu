@@ -13,7 +13,13 @@ constexpr int NSOLID_PACKED = 840;  // sum over l = 0..6 of (2l+1) ncart(l)
 __constant__ double c_solid[NSOLID_PACKED];
 __constant__ int c_solid_off[LMAX + 2];
 __device__ int g_tuv_prep[NHERM_TOT];
-__constant__ SolidClassTab c_cls[LMAX + 1];
+
+struct FoldDev {
+    const int *q_gptr, *q_ent, *w_gptr, *w_ent, *h_gptr, *h_ent, *h_out;
+    const FoldSeg* segs;
+    FoldPairTab pair[LMAX + 1][LMAX + 1];
+};
+__constant__ FoldDev c_fold;
 
 constexpr double PI = 3.141592653589793238462643383279502884;
 
@@ -62,80 +68,33 @@ __global__ void norm_kernel(const DShell* __restrict__ sh, int nshell, const dou
     for (int i = 0; i < K; ++i) ncoef[o + i] = coefs[o + i] * prim_norm(l, exps[o + i]) * sc;
 }
 
-// Solid fold of one (class of a, class of b, p) item with exactly NMA x NMB solid functions:
-// for each a of the class, u[jb] = sum_b C_b[jb][b] E_ab^p over the class of b (the E product
-// formed once per b), then acc[ja][jb] += C_a[ja][a] u[jb].  The class sizes are template
-// arguments so that no padded FP64 operation is issued.
-template <int NMA, int NMB>
-__device__ inline void fold_item(const SolidClassTab& TA, const SolidClassTab& TB, int ca, int cb, int px, int py,
-                                 int pz, const double* Ex, const double* Ey, const double* Ez, int sb1, int nt,
-                                 double (&out)[SC_MAXM][SC_MAXM]) {
-    double acc[NMA][NMB];
-#pragma unroll
-    for (int x = 0; x < NMA; ++x)
-#pragma unroll
-        for (int y = 0; y < NMB; ++y) acc[x][y] = 0.0;
-    const int na = TA.na[ca], nb = TB.na[cb];
-    for (int ia = 0; ia < na; ++ia) {
-        const int ac = TA.comp[ca][ia];
-        const double* ex = Ex + ((ac & 255) * sb1) * nt + px;
-        const double* ey = Ey + (((ac >> 8) & 255) * sb1) * nt + py;
-        const double* ez = Ez + ((ac >> 16) * sb1) * nt + pz;
-        double u[NMB];
-#pragma unroll
-        for (int y = 0; y < NMB; ++y) u[y] = 0.0;
-        for (int ib = 0; ib < nb; ++ib) {
-            const int bc = TB.comp[cb][ib];
-            const double v = ex[(bc & 255) * nt] * ey[((bc >> 8) & 255) * nt] * ez[(bc >> 16) * nt];
-#pragma unroll
-            for (int y = 0; y < NMB; ++y) u[y] += TB.c[cb][y][ib] * v;
-        }
-#pragma unroll
-        for (int x = 0; x < NMA; ++x) {
-            const double c = TA.c[ca][x][ia];
-#pragma unroll
-            for (int y = 0; y < NMB; ++y) acc[x][y] += c * u[y];
-        }
-    }
-#pragma unroll
-    for (int x = 0; x < NMA; ++x)
-#pragma unroll
-        for (int y = 0; y < NMB; ++y) out[x][y] = acc[x][y];
-}
-
 constexpr int PAIR_THREADS = 128;
+constexpr int PAIR_SOLID_THREADS = 512;
 constexpr int ETAB = (LMAX + 1) * (LMAX + 1) * (2 * LMAX + 1);  // 637 per direction
+constexpr int FOLD_SMEM_BYTES = (3 * ETAB + 2 * (FOLD_CMAX + 1) + FOLD_QMAX + 1 + FOLD_WMAX) * (int)sizeof(double);
 
-// One CTA per primitive pair (item.q = pair id, item.a = primitive pair kp).
-// Writes pair scalars (zeta_p, P) and the H block columns of this primitive pair.
-__global__ void __launch_bounds__(PAIR_THREADS) pair_h_kernel(const DPair* __restrict__ pairs,
-                                                               const WorkItem* __restrict__ items,
-                                                               const DShell* __restrict__ sh,
-                                                               const double* __restrict__ exps,
-                                                               const double* __restrict__ ncoef,
-                                                               double* __restrict__ ws, double* __restrict__ ws_info,
-                                                               unsigned* status) {
-    __shared__ double E[3][ETAB];
-    __shared__ double s_pref;
-    const WorkItem it = items[blockIdx.x];
-    const DPair pr = pairs[it.q];
+// Hermite expansion coefficients of primitive pair kp into E[3][ETAB] (zero beyond t <= i+j),
+// one warp per Cartesian direction, lanes over t:
+//   E^t_{i+1,j} = E^{t-1}_{ij}/(2 zeta_p) + (P - A) E^t_{ij} + (t+1) E^{t+1}_{ij}
+//   E^t_{i,j+1} = E^{t-1}_{ij}/(2 zeta_p) + (P - B) E^t_{ij} + (t+1) E^{t+1}_{ij}
+// Thread 96 writes the pair scalars (zeta_p, P) and leaves exp(-mu |AB|^2) c'_a c'_b in
+// *s_pref.  Needs at least 97 threads; ends with a CTA barrier.
+__device__ __forceinline__ void pair_setup(const DPair& pr, int kp, const DShell* __restrict__ sh, const double* __restrict__ exps,
+                           const double* __restrict__ ncoef, double* __restrict__ ws_info, double* E,
+                           double* s_pref) {
     const DShell sa = sh[pr.sa], sb = sh[pr.sb];
-    const int la = sa.l, lb = sb.l, lsum = la + lb, nt = lsum + 1;
-    const int kp = it.a, ia = kp / sb.K, ib = kp - ia * sb.K;
+    const int la = sa.l, lb = sb.l, nt = la + lb + 1;
+    const int ia = kp / sb.K, ib = kp - ia * sb.K;
     const double za = exps[sa.prim_off + ia], zb = exps[sb.prim_off + ib], zp = za + zb;
-
-    for (int i = threadIdx.x; i < 3 * ETAB; i += blockDim.x) (&E[0][0])[i] = 0.0;
+    for (int i = threadIdx.x; i < 3 * ETAB; i += blockDim.x) E[i] = 0.0;
     __syncthreads();
-    // Hermite expansion coefficients, one warp per Cartesian direction, lanes over t:
-    //   E^t_{i+1,j} = E^{t-1}_{ij}/(2 zeta_p) + (P - A) E^t_{ij} + (t+1) E^{t+1}_{ij}
-    //   E^t_{i,j+1} = E^{t-1}_{ij}/(2 zeta_p) + (P - B) E^t_{ij} + (t+1) E^{t+1}_{ij}
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp < 3) {
         const int d = warp;
         const double Ad = sh[pr.sa].A[d], Bd = sh[pr.sb].A[d];
         const double P = (za * Ad + zb * Bd) / zp;
         const double PA = P - Ad, PB = P - Bd, oo2p = 0.5 / zp;
-        double* Ed = E[d];
+        double* Ed = E + d * ETAB;
 #define EIJ(i, j, t) Ed[((i) * (lb + 1) + (j)) * nt + (t)]
         if (lane == 0) EIJ(0, 0, 0) = 1.0;
         __syncwarp();
@@ -176,9 +135,27 @@ __global__ void __launch_bounds__(PAIR_THREADS) pair_h_kernel(const DPair* __res
             info[1 + d] = (za * sa.A[d] + zb * sb.A[d]) / zp;
             AB2 += (sa.A[d] - sb.A[d]) * (sa.A[d] - sb.A[d]);
         }
-        s_pref = exp(-za * zb / zp * AB2) * ncoef[sa.prim_off + ia] * ncoef[sb.prim_off + ib];
+        *s_pref = exp(-za * zb / zp * AB2) * ncoef[sa.prim_off + ia] * ncoef[sb.prim_off + ib];
     }
     __syncthreads();
+}
+
+// One CTA per primitive pair (item.q = pair id, item.a = primitive pair kp), Cartesian rows.
+// Writes pair scalars (zeta_p, P) and the H block columns of this primitive pair.
+__global__ void __launch_bounds__(PAIR_THREADS) pair_h_kernel(const DPair* __restrict__ pairs,
+                                                               const WorkItem* __restrict__ items,
+                                                               const DShell* __restrict__ sh,
+                                                               const double* __restrict__ exps,
+                                                               const double* __restrict__ ncoef,
+                                                               double* __restrict__ ws, double* __restrict__ ws_info,
+                                                               unsigned* status) {
+    __shared__ double E[3][ETAB];
+    __shared__ double s_pref;
+    const WorkItem it = items[blockIdx.x];
+    const DPair pr = pairs[it.q];
+    const int la = sh[pr.sa].l, lb = sh[pr.sb].l, nt = la + lb + 1;
+    const int kp = it.a;
+    pair_setup(pr, kp, sh, exps, ncoef, ws_info, &E[0][0], &s_pref);
 
     const int np = pr.np;
     const int64_t ldh = (int64_t)pr.Kab * np;
@@ -190,62 +167,108 @@ __global__ void __launch_bounds__(PAIR_THREADS) pair_h_kernel(const DPair* __res
     const double* Ez = E[2];
     const int sb1 = lb + 1;
 
-    if (!pr.solid) {
-        // H[ab][p] = pref * sign(p) * Ex[ax bx px] Ey[ay by py] Ez[az bz pz]
-        const int total = nca * ncb * np;
-        for (int i = threadIdx.x; i < total; i += blockDim.x) {
-            const int ab = i / np, p = i - ab * np;
-            const int a = ab / ncb, b = ab - a * ncb;
-            int ax, ay, az, bx, by, bz;
-            cart_of(a, la, ax, ay, az);
-            cart_of(b, lb, bx, by, bz);
-            const int tuv = g_tuv_prep[p];
-            const int px = tuv & 255, py = (tuv >> 8) & 255, pz = tuv >> 16;
-            double v = Ex[(ax * sb1 + bx) * nt + px] * Ey[(ay * sb1 + by) * nt + py] * Ez[(az * sb1 + bz) * nt + pz];
-            if (pr.sign && ((px + py + pz) & 1)) v = -v;
-            H[(int64_t)ab * ldh + p] = pref * v;
-        }
-    } else {
-        // H[ma mb][p] = pref * sign(p) * sum_a C_a[ma][a] sum_b C_b[mb][b] E_ab^p.
-        // C is block diagonal over parity classes, so one work item is (class of a, class of
-        // b, p): the E products of the class's b components are formed once per a and shared
-        // by all of its m_b; the a-sum accumulates a (<= 4) x (<= 4) register block.
-        const SolidClassTab& TA = c_cls[la];
-        const SolidClassTab& TB = c_cls[lb];
-        const int nsb = 2 * lb + 1;
-        const int ncb_cls = TB.ncls;
-        const int total = TA.ncls * ncb_cls * np;
-        for (int i = threadIdx.x; i < total; i += blockDim.x) {
-            const int g = i / np, p = i - g * np;
-            const int ca = g / ncb_cls, cb = g - ca * ncb_cls;
-            const int tuv = g_tuv_prep[p];
-            const int px = tuv & 255, py = (tuv >> 8) & 255, pz = tuv >> 16;
-            const int nma = TA.nm[ca], nmb = TB.nm[cb];
-            double acc[SC_MAXM][SC_MAXM];
-#define LX_FOLD(A, B) \
-    case (A) * 8 + (B): fold_item<A, B>(TA, TB, ca, cb, px, py, pz, Ex, Ey, Ez, sb1, nt, acc); break;
-            switch (nma * 8 + nmb) {
-                LX_FOLD(1, 1) LX_FOLD(1, 2) LX_FOLD(1, 3) LX_FOLD(1, 4)
-                LX_FOLD(2, 1) LX_FOLD(2, 2) LX_FOLD(2, 3) LX_FOLD(2, 4)
-                LX_FOLD(3, 1) LX_FOLD(3, 2) LX_FOLD(3, 3) LX_FOLD(3, 4)
-                LX_FOLD(4, 1) LX_FOLD(4, 2) LX_FOLD(4, 3) LX_FOLD(4, 4)
-                default: break;
-            }
-#undef LX_FOLD
-            const double sg = (pr.sign && ((px + py + pz) & 1)) ? -pref : pref;
-#pragma unroll
-            for (int ja = 0; ja < SC_MAXM; ++ja)
-#pragma unroll
-                for (int jb = 0; jb < SC_MAXM; ++jb)
-                    if (ja < nma && jb < nmb)
-                        H[(int64_t)(TA.mind[ca][ja] * nsb + TB.mind[cb][jb]) * ldh + p] = sg * acc[ja][jb];
-        }
+    // H[ab][p] = pref * sign(p) * Ex[ax bx px] Ey[ay by py] Ez[az bz pz]
+    const int total = nca * ncb * np;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int ab = i / np, p = i - ab * np;
+        const int a = ab / ncb, b = ab - a * ncb;
+        int ax, ay, az, bx, by, bz;
+        cart_of(a, la, ax, ay, az);
+        cart_of(b, lb, bx, by, bz);
+        const int tuv = g_tuv_prep[p];
+        const int px = tuv & 255, py = (tuv >> 8) & 255, pz = tuv >> 16;
+        double v = Ex[(ax * sb1 + bx) * nt + px] * Ey[(ay * sb1 + by) * nt + py] * Ez[(az * sb1 + bz) * nt + pz];
+        if (pr.sign && ((px + py + pz) & 1)) v = -v;
+        H[(int64_t)ab * ldh + p] = pref * v;
+    }
+}
+
+// Rows of one fold stage, one warp per group of 32 rows (lane = row within the group):
+// acc = sum_j term(ent[gptr[g] + 32 j + lane]); every lane of a group runs the same count.
+template <typename Term, typename Store>
+__device__ __forceinline__ void fold_stage(int grp0, int nrow, const int* __restrict__ gptr,
+                                           const int* __restrict__ ent, Term term, Store store) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int g = warp; 32 * g < nrow; g += nwarp) {
+        const int e0 = __ldg(&gptr[grp0 + g]), e1 = __ldg(&gptr[grp0 + g + 1]);
+        double acc = 0.0;
+#pragma unroll 4
+        for (int e = e0 + lane; e < e1; e += 32) acc += term(__ldg(&ent[e]));
+        const int r = 32 * g + lane;
+        if (r < nrow) store(r, acc);
+    }
+}
+
+// One CTA per primitive pair, solid-harmonic rows:
+//   H[m_a m_b][p] = pref * sign(p) * sum_a C_a[m_a][a] sum_b C_b[m_b][b] E_ab^p
+// by the factorised fold (one Cartesian index at a time, structural zeros skipped; the row
+// groups are built on the host).  Per m_b: the Q stage, a barrier, the W stage, a barrier,
+// then the H stage of m_b together with the Q stage of m_b + 1 (which touch disjoint
+// arrays), a barrier.
+__global__ void __launch_bounds__(PAIR_SOLID_THREADS, 2) pair_h_solid_kernel(
+    const DPair* __restrict__ pairs, const WorkItem* __restrict__ items, const DShell* __restrict__ sh,
+    const double* __restrict__ exps, const double* __restrict__ ncoef, double* __restrict__ ws,
+    double* __restrict__ ws_info, unsigned* status) {
+    extern __shared__ double fold_smem[];
+    double* E = fold_smem;
+    double* Csa = E + 3 * ETAB;         // FOLD_CMAX + 1, last entry zero
+    double* Csb = Csa + FOLD_CMAX + 1;  // FOLD_CMAX + 1, last entry zero
+    double* Q = Csb + FOLD_CMAX + 1;    // FOLD_QMAX + 1, last entry zero
+    double* W = Q + FOLD_QMAX + 1;
+    __shared__ double s_pref;
+    const WorkItem it = items[blockIdx.x];
+    const DPair pr = pairs[it.q];
+    const int la = sh[pr.sa].l, lb = sh[pr.sb].l;
+    const int kp = it.a;
+    const int nca = ncart(la), ncb = ncart(lb), nsb = 2 * lb + 1;
+    for (int i = threadIdx.x; i < (2 * la + 1) * nca; i += blockDim.x) Csa[i] = c_solid[c_solid_off[la] + i];
+    for (int i = threadIdx.x; i < nsb * ncb; i += blockDim.x) Csb[i] = c_solid[c_solid_off[lb] + i];
+    if (threadIdx.x == 0) {
+        Csa[FOLD_CMAX] = 0.0;
+        Csb[FOLD_CMAX] = 0.0;
+        Q[FOLD_QMAX] = 0.0;
+    }
+    pair_setup(pr, kp, sh, exps, ncoef, ws_info, E, &s_pref);
+
+    const int np = pr.np;
+    const int64_t ldh = (int64_t)pr.Kab * np;
+    double* H = ws + pr.h_off + (int64_t)kp * np;
+    const double pref = s_pref;
+    const double* Ex = E;
+    const double* Ey = E + ETAB;
+    const double* Ez = E + 2 * ETAB;
+    const FoldPairTab tab = c_fold.pair[la][lb];
+    const FoldSeg* segs = c_fold.segs + tab.seg0;
+    const int* __restrict__ h_out = c_fold.h_out;
+    const int hrows = (2 * la + 1) * np;
+    const bool sign = pr.sign;
+
+    auto q_term = [=](int x) { return Csb[x & 511] * Ey[(x >> 9) & 1023] * Ez[x >> 19]; };
+    auto q_store = [=](int r, double v) { Q[r] = v; };
+    fold_stage(segs[0].q_grp0, segs[0].q_nrow, c_fold.q_gptr, c_fold.q_ent, q_term, q_store);
+    __syncthreads();
+    for (int mb = 0; mb < nsb; ++mb) {
+        const FoldSeg* sg = segs + mb;
+        fold_stage(sg->w_grp0, sg->w_nrow, c_fold.w_gptr, c_fold.w_ent,
+                   [=](int x) { return Ex[x & 1023] * Q[x >> 10]; }, [=](int r, double v) { W[r] = v; });
+        __syncthreads();
+        const int h_row0 = sg->h_row0;
+        fold_stage(sg->h_grp0, hrows, c_fold.h_gptr, c_fold.h_ent, [=](int x) { return Csa[x & 511] * W[x >> 9]; },
+                   [=](int r, double v) {
+                       const int o = __ldg(&h_out[h_row0 + r]);
+                       const int ma = o & 15, p = o >> 4;
+                       const int tuv = g_tuv_prep[p];
+                       const bool neg = sign && (((tuv & 255) + ((tuv >> 8) & 255) + (tuv >> 16)) & 1);
+                       H[(int64_t)(ma * nsb + mb) * ldh + p] = (neg ? -pref : pref) * v;
+                   });
+        if (mb + 1 < nsb) fold_stage(sg[1].q_grp0, sg[1].q_nrow, c_fold.q_gptr, c_fold.q_ent, q_term, q_store);
+        __syncthreads();
     }
 }
 
 }  // namespace
 
-cudaError_t init_prep_tables(const double* host_coefs, const int* host_tuv, const void* host_classes) {
+cudaError_t init_prep_tables(const double* host_coefs, const int* host_tuv, const void* host_fold) {
     int off[LMAX + 2];
     off[0] = 0;
     for (int l = 0; l <= LMAX; ++l) off[l + 1] = off[l] + (2 * l + 1) * ncart(l);
@@ -254,8 +277,31 @@ cudaError_t init_prep_tables(const double* host_coefs, const int* host_tuv, cons
     if (e != cudaSuccess) return e;
     e = cudaMemcpyToSymbol(c_solid_off, off, sizeof(off));
     if (e != cudaSuccess) return e;
-    e = cudaMemcpyToSymbol(c_cls, host_classes, sizeof(SolidClassTab) * (LMAX + 1));
-    if (e != cudaSuccess) return e;
+    // fold lists: device copies held for the life of the process (one set per device)
+    const FoldHost& F = *static_cast<const FoldHost*>(host_fold);
+    FoldDev d{};
+    const std::vector<int>* src[7] = {&F.q_gptr, &F.q_ent, &F.w_gptr, &F.w_ent, &F.h_gptr, &F.h_ent, &F.h_out};
+    const int** dst[7] = {&d.q_gptr, &d.q_ent, &d.w_gptr, &d.w_ent, &d.h_gptr, &d.h_ent, &d.h_out};
+    for (int k = 0; k < 7; ++k) {
+        int* p = nullptr;
+        const size_t bytes = sizeof(int) * (src[k]->size() + 1);
+        if ((e = cudaMalloc(&p, bytes)) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(p, src[k]->data(), sizeof(int) * src[k]->size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
+        *dst[k] = p;
+    }
+    FoldSeg* segs = nullptr;
+    if ((e = cudaMalloc(&segs, sizeof(FoldSeg) * F.segs.size())) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(segs, F.segs.data(), sizeof(FoldSeg) * F.segs.size(), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return e;
+    d.segs = segs;
+    for (int a = 0; a <= LMAX; ++a)
+        for (int b = 0; b <= LMAX; ++b) d.pair[a][b] = F.pair[a][b];
+    if ((e = cudaMemcpyToSymbol(c_fold, &d, sizeof(d))) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(pair_h_solid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  FOLD_SMEM_BYTES)) != cudaSuccess)
+        return e;
     return cudaMemcpyToSymbol(g_tuv_prep, host_tuv, sizeof(int) * NHERM_TOT);
 }
 
@@ -267,10 +313,14 @@ cudaError_t launch_norm(const DShell* sh, int nshell, const double* exps, const 
 }
 
 cudaError_t launch_pair_h(const DPair* pairs, const WorkItem* items, int nitems, const DShell* sh,
-                          const double* exps, const double* ncoef, double* ws, double* ws_info, unsigned* status,
-                          cudaStream_t st) {
+                          const double* exps, const double* ncoef, double* ws, double* ws_info, bool solid,
+                          unsigned* status, cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
-    pair_h_kernel<<<nitems, PAIR_THREADS, 0, st>>>(pairs, items, sh, exps, ncoef, ws, ws_info, status);
+    if (solid)
+        pair_h_solid_kernel<<<nitems, PAIR_SOLID_THREADS, FOLD_SMEM_BYTES, st>>>(pairs, items, sh, exps, ncoef, ws,
+                                                                                ws_info, status);
+    else
+        pair_h_kernel<<<nitems, PAIR_THREADS, 0, st>>>(pairs, items, sh, exps, ncoef, ws, ws_info, status);
     return cudaGetLastError();
 }
 

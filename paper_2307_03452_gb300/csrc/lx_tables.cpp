@@ -13,6 +13,7 @@
 // values come from the series F_n(T) = exp(-T) sum_k (2T)^k / ((2n+1)(2n+3)...(2n+2k+1))
 // for the top order, summed in long double, and the downward recursion
 // F_n = (2T F_{n+1} + exp(-T)) / (2n+1).
+#include <algorithm>
 #include <cmath>
 #include <map>
 #include <tuple>
@@ -139,42 +140,135 @@ void make_boys_table(double* table) {
     }
 }
 
-void make_solid_classes(const double* coefs, SolidClassTab* tab) {
-    for (int l = 0; l <= LMAX; ++l) {
-        SolidClassTab& T = tab[l];
-        T = SolidClassTab{};
-        const int nc = ncart(l);
-        const double* C = coefs + solid_offset(l);
-        int key_of[NCART_MAX];
-        int keys[4], nk = 0;
-        int k = 0;
-        for (int i = 0; i <= l; ++i)
-            for (int j = 0; j <= i; ++j, ++k) {
-                const int ax = l - i, ay = i - j, az = j;
-                const int key = (ax & 1) | ((ay & 1) << 1) | ((az & 1) << 2);
-                int c = 0;
-                while (c < nk && keys[c] != key) ++c;
-                if (c == nk) keys[nk++] = key;
-                key_of[k] = c;
-                T.comp[c][T.na[c]++] = ax | (ay << 8) | (az << 16);
-            }
-        T.ncls = nk;
-        // each solid function's nonzero coefficients lie in exactly one class
-        for (int m = 0; m < 2 * l + 1; ++m) {
-            int cls = -1;
-            for (int q = 0; q < nc; ++q)
-                if (std::fabs(C[m * nc + q]) > 1e-14) cls = key_of[q];
-            const int jm = T.nm[cls]++;
-            T.mind[cls][jm] = m;
-            for (int ia = 0; ia < T.na[cls]; ++ia) {
-                // ordinal of the class member ia
-                int q = 0, seen = 0;
-                for (; q < nc; ++q)
-                    if (key_of[q] == cls && seen++ == ia) break;
-                T.c[cls][jm][ia] = C[m * nc + q];
+namespace {
+
+// Sort rows by decreasing length (stable) and append them in groups of 32; returns the
+// position of each original row.
+std::vector<int> emit_groups(const std::vector<std::vector<int>>& rows, int null_entry, std::vector<int>& gptr,
+                             std::vector<int>& ent) {
+    const int n = (int)rows.size();
+    std::vector<int> order(n), pos(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return rows[a].size() > rows[b].size(); });
+    for (int i = 0; i < n; ++i) pos[order[i]] = i;
+    for (int g = 0; g < (n + 31) / 32; ++g) {
+        size_t len = 0;
+        for (int i = 32 * g; i < std::min(n, 32 * g + 32); ++i) len = std::max(len, rows[order[i]].size());
+        for (size_t j = 0; j < len; ++j)
+            for (int i = 32 * g; i < 32 * g + 32; ++i)
+                ent.push_back(i < n && j < rows[order[i]].size() ? rows[order[i]][j] : null_entry);
+        gptr.push_back((int)ent.size());
+    }
+    return pos;
+}
+
+}  // namespace
+
+bool make_fold_lists(const double* coefs, FoldHost& F) {
+    F.q_gptr.assign(1, 0);
+    F.w_gptr.assign(1, 0);
+    F.h_gptr.assign(1, 0);
+    F.q_ent.clear();
+    F.w_ent.clear();
+    F.h_ent.clear();
+    F.h_out.clear();
+    F.segs.clear();
+    bool ok = true;
+    for (int la = 0; la <= LMAX; ++la)
+        for (int lb = 0; lb <= LMAX; ++lb) {
+            const int nca = ncart(la), ncb = ncart(lb), nsa = 2 * la + 1, nsb = 2 * lb + 1;
+            const int nt = la + lb + 1, np = pyr(la + lb), sb1 = lb + 1;
+            std::vector<int> ax(nca), ay(nca), az(nca), bidx((lb + 1) * (lb + 1), -1);
+            for (int i = 0, k = 0; i <= la; ++i)
+                for (int j = 0; j <= i; ++j, ++k) {
+                    ax[k] = la - i;
+                    ay[k] = i - j;
+                    az[k] = j;
+                }
+            for (int i = 0, k = 0; i <= lb; ++i)
+                for (int j = 0; j <= i; ++j, ++k) bidx[(lb - i) * (lb + 1) + (i - j)] = k;  // (bx, by) -> b
+            const double* Ca = coefs + solid_offset(la);
+            const double* Cb = coefs + solid_offset(lb);
+            // distinct (ay, az) of shell a, in component order
+            std::vector<std::pair<int, int>> yz;
+            for (int k = 0; k < nca; ++k)
+                if (std::find(yz.begin(), yz.end(), std::make_pair(ay[k], az[k])) == yz.end())
+                    yz.emplace_back(ay[k], az[k]);
+            FoldPairTab& tab = F.pair[la][lb];
+            tab.seg0 = (int)F.segs.size();
+            tab.maxq = tab.maxw = 0;
+            for (int mb = 0; mb < nsb; ++mb) {
+                FoldSeg sg{};
+                sg.q_grp0 = (int)F.q_gptr.size() - 1;
+                sg.w_grp0 = (int)F.w_gptr.size() - 1;
+                sg.h_grp0 = (int)F.h_gptr.size() - 1;
+                sg.h_row0 = (int)F.h_out.size();
+                // Q rows, keyed (ay, az, bx, u, v)
+                std::vector<std::tuple<int, int, int, int, int>> qkey;
+                std::vector<std::vector<int>> qrows;
+                for (const auto& [y, z] : yz)
+                    for (int bx = 0; bx <= lb; ++bx)
+                        for (int u = 0; u <= y + lb - bx; ++u)
+                            for (int v = 0; v <= z + lb - bx; ++v) {
+                                std::vector<int> row;
+                                for (int by = 0; by <= lb - bx; ++by) {
+                                    const int bz = lb - bx - by, b = bidx[bx * (lb + 1) + by];
+                                    if (std::fabs(Cb[mb * ncb + b]) <= 1e-14 || u > y + by || v > z + bz) continue;
+                                    row.push_back((mb * ncb + b) | (((y * sb1 + by) * nt + u) << 9) |
+                                                  (((z * sb1 + bz) * nt + v) << 19));
+                                }
+                                if (row.empty()) continue;
+                                qkey.emplace_back(y, z, bx, u, v);
+                                qrows.push_back(std::move(row));
+                            }
+                sg.q_nrow = (int)qkey.size();
+                if (sg.q_nrow > FOLD_QMAX) return false;
+                const std::vector<int> qpos = emit_groups(qrows, FOLD_QNULL, F.q_gptr, F.q_ent);
+                // W rows, keyed (a, p)
+                std::vector<std::vector<int>> wrows;
+                std::vector<int> wrow((size_t)nca * np, -1);
+                for (int a = 0; a < nca; ++a) {
+                    std::vector<std::vector<int>> rows(np);
+                    for (int qi = 0; qi < (int)qkey.size(); ++qi) {
+                        const auto [y, z, bx, u, v] = qkey[qi];
+                        if (y != ay[a] || z != az[a]) continue;
+                        for (int t = 0; t <= ax[a] + bx; ++t)
+                            rows[hidx(t, u, v)].push_back(((ax[a] * sb1 + bx) * nt + t) | (qpos[qi] << 10));
+                    }
+                    for (int p = 0; p < np; ++p) {
+                        if (rows[p].empty()) continue;
+                        wrow[(size_t)a * np + p] = (int)wrows.size();
+                        wrows.push_back(std::move(rows[p]));
+                    }
+                }
+                sg.w_nrow = (int)wrows.size();
+                if (sg.w_nrow > FOLD_WMAX) return false;
+                const std::vector<int> wpos = emit_groups(wrows, FOLD_WNULL, F.w_gptr, F.w_ent);
+                // H rows (m_a, p); the output position travels with the row
+                std::vector<std::vector<int>> hrows;
+                std::vector<int> hkey;
+                for (int ma = 0; ma < nsa; ++ma)
+                    for (int p = 0; p < np; ++p) {
+                        std::vector<int> row;
+                        for (int a = 0; a < nca; ++a) {
+                            const int w = wrow[(size_t)a * np + p];
+                            if (w < 0 || std::fabs(Ca[ma * nca + a]) <= 1e-14) continue;
+                            row.push_back((ma * nca + a) | (wpos[w] << 9));
+                        }
+                        hrows.push_back(std::move(row));
+                        hkey.push_back(ma | (p << 4));
+                    }
+                const std::vector<int> hpos = emit_groups(hrows, FOLD_HNULL, F.h_gptr, F.h_ent);
+                std::vector<int> out(hrows.size());
+                for (size_t i = 0; i < hrows.size(); ++i) out[hpos[i]] = hkey[i];
+                F.h_out.insert(F.h_out.end(), out.begin(), out.end());
+                tab.maxq = std::max(tab.maxq, sg.q_nrow);
+                tab.maxw = std::max(tab.maxw, sg.w_nrow);
+                F.segs.push_back(sg);
             }
         }
-    }
+    return ok;
 }
 
 void make_tuv_table(int* tuv) {
