@@ -440,6 +440,11 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             for (int m = 0; m < mt2; ++m)
                 for (int n = 0; n < nt2; ++n) P.items_sg2.push_back({i, m, n, 0});
         }
+        // the persistent split GEMM hands items to CTAs in a fixed stride: longest first
+        std::stable_sort(P.items_sg1.begin(), P.items_sg1.end(),
+                         [&](const WorkItem& x, const WorkItem& y) { return P.sq[x.q].nkb1 > P.sq[y.q].nkb1; });
+        std::stable_sort(P.items_sg2.begin(), P.items_sg2.end(),
+                         [&](const WorkItem& x, const WorkItem& y) { return P.sq[x.q].nkb2 > P.sq[y.q].nkb2; });
     }
     // byte layout from the chunk base
     size_t o = 0;

@@ -402,86 +402,54 @@ __global__ void balance_kernel(const BalanceDesc* __restrict__ descs, const Work
 
 // ------------------------------------------------------------------ tcgen05 GEMM
 
-constexpr int STAGES = 2;
+constexpr int STAGES = 3;
+constexpr int NBUF = 2;  // TMEM accumulator sets: one drains while the other accumulates
 constexpr int A_BLOCK = SPLIT_NSLICE * SPLIT_TA * SPLIT_KB * 2;  // bytes of one A block (all slices)
 constexpr int B_BLOCK_MAX = SPLIT_NSLICE * SPLIT_TB * SPLIT_KB * 2;
 constexpr int A_SLICE = SPLIT_TA * SPLIT_KB * 2;
 constexpr int STAGE_BYTES = A_BLOCK + B_BLOCK_MAX;
+constexpr int BUF_COLS = SPLIT_NSLICE * SPLIT_TB;  // TMEM columns of one accumulator set
 constexpr uint32_t TMEM_COLS = 512;
+static_assert(NBUF * BUF_COLS <= (int)TMEM_COLS, "accumulator sets exceed TMEM");
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
-constexpr int GEMM_THREADS = 192;  // warp 0 TMA, warp 1 MMA issue + TMEM, warps 2..5 drain / epilogue
-constexpr int NCHUNK = SPLIT_TB / 16;
-
-// int64 -> FP64 times 2^scale, correctly rounded (round to nearest even), integer ops only.
-__device__ inline double i64_to_f64_scaled(long long v, int scale) {
-    if (v == 0) return 0.0;
-    const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
-    unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-    const int lz = __clzll((long long)a);
-    const int top = 63 - lz;  // index of the leading bit
-    // normalise to 53 bits with round-to-nearest-even
-    unsigned long long m;
-    int ex = top;
-    if (top > 52) {
-        const int sh = top - 52;
-        const unsigned long long rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-        m = a >> sh;
-        if (rem > half || (rem == half && (m & 1))) {
-            ++m;
-            if (m >> 53) {
-                m >>= 1;
-                ++ex;
-            }
-        }
-    } else {
-        m = a << (52 - top);
-    }
-    const int be = ex + scale + 1023;
-    if (be <= 0) return 0.0;  // far below any integral of interest
-    if (be >= 2047) return __longlong_as_double((long long)(sgn | 0x7FF0000000000000ull));
-    return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
-}
+// warp 0 TMA, warp 1 MMA issue + TMEM, warps 2..9 drain / epilogue: two warps per TMEM lane
+// quarter, each owning 16 of the tile's (at most 32) columns
+constexpr int DRAIN_WARPS = 8;
+constexpr int GEMM_THREADS = 32 * (2 + DRAIN_WARPS);
+static_assert(SPLIT_TB == 16 * (DRAIN_WARPS / 4), "each drain warp owns 16 columns");
 
 __device__ inline void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// item.q = problem, item.a = M tile, item.b = N tile.
+// Persistent: CTA b takes work items b, b + gridDim.x, ... (item.q = problem, item.a = M tile,
+// item.b = N tile); the three roles walk the same sequence.  The TMA ring of K blocks runs
+// on across item boundaries, and so do the two TMEM accumulator sets, so one tile's drains
+// and output overlap the next tile's MMAs.
 //
 // Accumulation is exact.  Every digit is an integer with |d_0| <= 2^BETA and |d_s| <= 2^(BETA-1)
 // for s > 0, so one k adds at most 2^17 to any diagonal d = s + t (2 * 2^15 + (d - 1) * 2^14 for
 // d >= 2, 2^16 for d < 2).  The MMAs of SPLIT_SEG_KB K blocks (128 k) therefore leave every
 // FP32 accumulator, and every partial sum on the way, an integer of magnitude <= 2^24, which
-// FP32 holds exactly; the four drain warps then move the diagonals into 64-bit integers and
-// the next segment starts its accumulators from zero.  Per k the combined value is at most
+// FP32 holds exactly; the four drain warps then move the diagonals into 64-bit integers while
+// the next segment accumulates in the other TMEM set.  Per k the combined value is at most
 // 2^(2W - 48) = 2^48, so the 64-bit sum is shifted down by xs bits when K exceeds 2^14.
 //
 // The MMAs of one A slice s and one K step are issued against the B slices 0..NSLICE-1-s at
 // once: slice t lies tb rows after slice t-1 in shared memory and diagonal s + t lies tb TMEM
-// columns after s + t - 1, so A_s [B_0; B_1; ...] lands every product on its diagonal (split
-// into pieces of at most 256 columns, the largest MMA N).
+// columns after s + t - 1, so A_s [B_0; B_1; ...] lands every product on its diagonal in one
+// MMA of N = (NSLICE - s) tb <= 192.
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
-    split_gemm_kernel(const SplitGemmDesc* __restrict__ probs, const WorkItem* __restrict__ items,
+    split_gemm_kernel(const SplitGemmDesc* __restrict__ probs, const WorkItem* __restrict__ items, int nitems,
                       const char* __restrict__ ws, double* __restrict__ cbase, unsigned* status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned operand stages
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], seg_bar, drained_bar, final_bar;
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], seg_full[NBUF], seg_empty[NBUF], final_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const WorkItem it = items[blockIdx.x];
-    const SplitGemmDesc P = probs[it.q];
-    const int tb = P.tb;
-    const int b_block = SPLIT_NSLICE * tb * SPLIT_KB * 2;
-    const int m0 = it.a * SPLIT_TA, n0 = it.b * tb;
-    const int nt = min(tb, P.N - n0);
-    const int nkb = P.nkb;
-    const int nseg = (nkb + SPLIT_SEG_KB - 1) / SPLIT_SEG_KB;
-    const int kpad = nkb * SPLIT_KB;
-    const int xs = max(0, 32 - __clz(kpad - 1) - 14);  // ceil(log2 K) - 14, if positive
-
     if (warp == 1) {
         tmem_alloc(&tmem_base_sh, TMEM_COLS);
         tmem_relinquish();
@@ -491,8 +459,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
-        mbar_init(&seg_bar, 1);
-        mbar_init(&drained_bar, 4);
+        for (int b = 0; b < NBUF; ++b) {
+            mbar_init(&seg_full[b], 1);
+            mbar_init(&seg_empty[b], DRAIN_WARPS);
+        }
         mbar_init(&final_bar, 1);
         abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -502,145 +472,159 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
 
-    const char* a_src = ws + P.a_dig + (int64_t)it.a * nkb * A_BLOCK;
-    const char* b_src = ws + P.b_dig + (int64_t)it.b * nkb * b_block;
-
     if (warp == 0) {
         if (lane == 0) {
-            // producer: stream the A and B blocks of each K block into the ring of stages
-            int issued = 0;
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int st = kb % STAGES, use = kb / STAGES;
-                if (use > 0 && !mbar_wait(&empty_bar[st], (use - 1) & 1, status)) {
-                    abort_sh = 1;
-                    break;
+            // producer: stream the A and B blocks of every K block of every item into the ring
+            int g = 0;  // K blocks issued so far
+            bool ok = true;
+            for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
+                const WorkItem it = items[w];
+                const SplitGemmDesc P = probs[it.q];
+                const int b_block = SPLIT_NSLICE * P.tb * SPLIT_KB * 2;
+                const char* a_src = ws + P.a_dig + (int64_t)it.a * P.nkb * A_BLOCK;
+                const char* b_src = ws + P.b_dig + (int64_t)it.b * P.nkb * b_block;
+                for (int kb = 0; kb < P.nkb; ++kb, ++g) {
+                    const int st = g % STAGES, use = g / STAGES;
+                    if ((use > 0 && !mbar_wait(&empty_bar[st], (use - 1) & 1, status)) || *(volatile int*)&abort_sh) {
+                        abort_sh = 1;
+                        ok = false;
+                        break;
+                    }
+                    unsigned char* sa = smem + st * STAGE_BYTES;
+                    mbar_expect_tx(&full_bar[st], A_BLOCK + b_block);
+                    bulk_g2s(sa, a_src + (int64_t)kb * A_BLOCK, A_BLOCK, &full_bar[st]);
+                    bulk_g2s(sa + A_BLOCK, b_src + (int64_t)kb * b_block, b_block, &full_bar[st]);
                 }
-                if (*(volatile int*)&abort_sh) break;
-                unsigned char* sa = smem + st * STAGE_BYTES;
-                unsigned char* sb = sa + A_BLOCK;
-                mbar_expect_tx(&full_bar[st], A_BLOCK + b_block);
-                bulk_g2s(sa, a_src + (int64_t)kb * A_BLOCK, A_BLOCK, &full_bar[st]);
-                bulk_g2s(sb, b_src + (int64_t)kb * b_block, b_block, &full_bar[st]);
-                issued = kb + 1;
             }
             // no copy may still be landing in shared memory when the CTA exits
-            for (int st = 0; st < STAGES && st < issued; ++st) {
-                const int last = issued - 1 - ((issued - 1 - st) % STAGES);
+            for (int st = 0; st < STAGES && st < g; ++st) {
+                const int last = g - 1 - ((g - 1 - st) % STAGES);
                 if (!mbar_wait(&full_bar[st], (last / STAGES) & 1, status)) abort_sh = 1;
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t sbase = smem_u32(smem);
-            for (int seg = 0; seg < nseg; ++seg) {
-                if (seg > 0) {
-                    if (!mbar_wait(&drained_bar, (seg - 1) & 1, status)) abort_sh = 1;
-                    tc_fence_after();
-                }
-                if (*(volatile int*)&abort_sh) break;
-                const int kb0 = seg * SPLIT_SEG_KB, kb1 = min(nkb, kb0 + SPLIT_SEG_KB);
-                bool ok = true;
-                for (int kb = kb0; kb < kb1; ++kb) {
-                    const int st = kb % STAGES, use = kb / STAGES;
-                    if (!mbar_wait(&full_bar[st], use & 1, status)) {
+            int g = 0, sgc = 0;  // K blocks consumed, segments issued
+            bool ok = true;
+            for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
+                const WorkItem it = items[w];
+                const SplitGemmDesc P = probs[it.q];
+                const int tb = P.tb, nkb = P.nkb;
+                for (int kb0 = 0; kb0 < nkb && ok; kb0 += SPLIT_SEG_KB, ++sgc) {
+                    const int buf = sgc & 1, ub = sgc >> 1;
+                    if (ub > 0) {
+                        if (!mbar_wait(&seg_empty[buf], (ub - 1) & 1, status)) ok = false;
+                        tc_fence_after();
+                    }
+                    if (!ok || *(volatile int*)&abort_sh) {
                         ok = false;
                         break;
                     }
-                    tc_fence_after();
-                    const uint32_t sa = sbase + st * STAGE_BYTES;
-                    const uint32_t sb = sa + A_BLOCK;
+                    const uint32_t dcol = tmem + buf * BUF_COLS;
+                    const int kb1 = min(nkb, kb0 + SPLIT_SEG_KB);
+                    for (int kb = kb0; kb < kb1; ++kb, ++g) {
+                        const int st = g % STAGES;
+                        if (!mbar_wait(&full_bar[st], (g / STAGES) & 1, status)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sa = sbase + st * STAGE_BYTES;
+                        const uint32_t sb = sa + A_BLOCK;
 #pragma unroll
-                    for (int ks = 0; ks < SPLIT_KB / 16; ++ks) {
+                        for (int ks = 0; ks < SPLIT_KB / 16; ++ks) {
+                            const uint64_t bd = smem_desc(sb + ks * 256, 128, (SPLIT_KB / 8) * 128);
 #pragma unroll
-                        for (int s = 0; s < SPLIT_NSLICE; ++s) {
-                            const uint64_t ad = smem_desc(sa + s * A_SLICE + ks * 256, 128, (SPLIT_KB / 8) * 128);
-                            const int rows = (SPLIT_NSLICE - s) * tb;  // B slices 0 .. NSLICE-1-s
-                            for (int r0 = 0; r0 < rows; r0 += 256) {
-                                const int n = min(256, rows - r0);
-                                const uint64_t bd =
-                                    smem_desc(sb + (r0 >> 3) * (SPLIT_KB / 8) * 128 + ks * 256, 128, (SPLIT_KB / 8) * 128);
-                                // the slice-0 MMAs of a segment's first K step cover every diagonal
+                            for (int s = 0; s < SPLIT_NSLICE; ++s) {
+                                const uint64_t ad = smem_desc(sa + s * A_SLICE + ks * 256, 128, (SPLIT_KB / 8) * 128);
+                                // the slice-0 MMA of a segment's first K step covers every diagonal
                                 const uint32_t acc = (kb == kb0 && ks == 0 && s == 0) ? 0u : 1u;
-                                umma_bf16(tmem + s * tb + r0, ad, bd, idesc_bf16(SPLIT_TA, n), acc);
+                                umma_bf16(dcol + s * tb, ad, bd, idesc_bf16(SPLIT_TA, (SPLIT_NSLICE - s) * tb), acc);
                             }
                         }
+                        umma_commit(&empty_bar[st]);  // the stage is free once these MMAs have read it
                     }
-                    umma_commit(&empty_bar[st]);  // the stage is free once these MMAs have read it
+                    if (!ok) break;
+                    umma_commit(&seg_full[buf]);
                 }
-                if (!ok) {
-                    abort_sh = 1;
-                    break;
-                }
-                umma_commit(&seg_bar);
             }
+            if (!ok) abort_sh = 1;
             // every MMA issued has completed before TMEM is released
             umma_commit(&final_bar);
             if (!mbar_wait(&final_bar, 0, status)) abort_sh = 1;
         }
     } else {
-        // drain / epilogue: warp w reads TMEM lanes (rows) 32 (w % 4) .. 32 (w % 4) + 31
-        const int quarter = warp & 3;
-        const int row = m0 + quarter * 32 + lane;
-        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
-        long long acc[NCHUNK][16];
-#pragma unroll
-        for (int c = 0; c < NCHUNK; ++c)
-#pragma unroll
-            for (int j = 0; j < 16; ++j) acc[c][j] = 0;
+        // drain / epilogue: warp w reads TMEM lanes (rows) 32 (w % 4) .. 32 (w % 4) + 31 and the
+        // 16 columns c0 .. c0 + 15 of each diagonal
+        const int quarter = warp & 3, c0 = 16 * ((warp - 2) >> 2);
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + c0;
+        int sgc = 0;
         bool ok = true;
-        for (int seg = 0; seg < nseg; ++seg) {
-            const bool w = mbar_wait(&seg_bar, seg & 1, status);
-            ok = __all_sync(0xffffffffu, w) && !*(volatile int*)&abort_sh;
-            if (!ok) break;
-            tc_fence_after();
+        for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
+            const WorkItem it = items[w];
+            const SplitGemmDesc P = probs[it.q];
+            const int tb = P.tb, nkb = P.nkb;
+            const int m0 = it.a * SPLIT_TA, n0 = it.b * tb;
+            const int nt = min(tb, P.N - n0);
+            const bool mine = c0 < nt;  // warp-uniform
+            const int xs = max(0, 32 - __clz(nkb * SPLIT_KB - 1) - 14);  // ceil(log2 K) - 14, if positive
+            long long acc[16];
 #pragma unroll
-            for (int c = 0; c < NCHUNK; ++c) {
-                if (16 * c >= nt) break;
+            for (int j = 0; j < 16; ++j) acc[j] = 0;
+            for (int kb0 = 0; kb0 < nkb; kb0 += SPLIT_SEG_KB, ++sgc) {
+                const int buf = sgc & 1;
+                const bool got = mbar_wait(&seg_full[buf], (sgc >> 1) & 1, status);
+                ok = __all_sync(0xffffffffu, got) && !*(volatile int*)&abort_sh;
+                if (!ok) break;
+                tc_fence_after();
+                if (mine) {
+                    // all six diagonals in flight before one wait
+                    uint32_t r[SPLIT_NSLICE][16];
 #pragma unroll
-                for (int dg = 0; dg < SPLIT_NSLICE; ++dg) {
-                    uint32_t r[16];
-                    tmem_ld16(lane_base + dg * tb + 16 * c, r);
+                    for (int dg = 0; dg < SPLIT_NSLICE; ++dg) tmem_ld16(lane_base + buf * BUF_COLS + dg * tb, r[dg]);
                     tmem_ld_wait();
-                    // acc += G_d 2^(BETA (NSLICE-2-d)) (>> xs); the last diagonal is rounded down BETA bits
+                    // acc += sum_d G_d 2^(BETA (NSLICE-2-d)) (>> xs); the last diagonal is rounded down BETA bits
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const long long g = (long long)__float2int_rn(__uint_as_float(r[j]));
-                        long long v;
-                        if (dg < SPLIT_NSLICE - 1)
-                            v = g << (SPLIT_BETA * (SPLIT_NSLICE - 2 - dg));
+                        long long v = 0;
+#pragma unroll
+                        for (int dg = 0; dg < SPLIT_NSLICE; ++dg) {
+                            const long long gv = (long long)__float2int_rn(__uint_as_float(r[dg][j]));
+                            if (dg < SPLIT_NSLICE - 1)
+                                v += gv << (SPLIT_BETA * (SPLIT_NSLICE - 2 - dg));
+                            else
+                                v += (gv + (1ll << (SPLIT_BETA - 1))) >> SPLIT_BETA;
+                        }
+                        acc[j] += xs ? (v + (1ll << (xs - 1))) >> xs : v;
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&seg_empty[buf]);
+            }
+            if (!ok) break;
+            const int row = m0 + quarter * 32 + lane;
+            if (mine && row < P.M) {
+                const int ea = reinterpret_cast<const int*>(ws + P.a_exp)[row];
+                const int* eb_tab = reinterpret_cast<const int*>(ws + P.b_exp);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + c0 + j;
+                    if (c0 + j < nt) {
+                        // D = 2^(eA + eB - 2W + BETA NSLICE + xs) * acc: one rounding (int64 -> FP64,
+                        // to nearest even), then an exact power-of-two scaling
+                        const int scale = ea + eb_tab[col] - 2 * SPLIT_W + SPLIT_BETA * SPLIT_NSLICE + xs;
+                        const double v = scale2(__ll2double_rn(acc[j]), scale);
+                        if (P.transpose)
+                            cbase[P.c_off + (int64_t)col * P.ldc + row] = v;
                         else
-                            v = (g + (1ll << (SPLIT_BETA - 1))) >> SPLIT_BETA;
-                        acc[c][j] += xs ? (v + (1ll << (xs - 1))) >> xs : v;
+                            cbase[P.c_off + (int64_t)row * P.ldc + col] = v;
                     }
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&drained_bar);
         }
-        if (ok) {
-            // every MMA has completed and every copy has been consumed: the operand stages are
-            // free, so the sums go through shared memory and the conversion loop stays rolled
-            long long* stage = reinterpret_cast<long long*>(smem) + (int64_t)(quarter * 32 + lane) * SPLIT_TB;
-#pragma unroll
-            for (int c = 0; c < NCHUNK; ++c)
-#pragma unroll
-                for (int j = 0; j < 16; ++j) stage[16 * c + j] = acc[c][j];
-            if (row < P.M) {
-                const int ea = reinterpret_cast<const int*>(ws + P.a_exp)[row];
-                const int* eb_tab = reinterpret_cast<const int*>(ws + P.b_exp);
-                for (int j = 0; j < nt; ++j) {
-                    const int col = n0 + j;
-                    // D = 2^(eA + eB - 2W + BETA NSLICE + xs) * acc
-                    const int scale = ea + eb_tab[col] - 2 * SPLIT_W + SPLIT_BETA * SPLIT_NSLICE + xs;
-                    const double v = i64_to_f64_scaled(stage[j], scale);
-                    if (P.transpose)
-                        cbase[P.c_off + (int64_t)col * P.ldc + row] = v;
-                    else
-                        cbase[P.c_off + (int64_t)row * P.ldc + col] = v;
-                }
-            }
-        }
+        if (!ok) abort_sh = 1;
     }
     tc_fence_before();
     __syncthreads();
@@ -696,7 +680,13 @@ cudaError_t init_split_kernels(const int* host_tuv) {
 cudaError_t launch_split_gemm(const SplitGemmDesc* probs, const WorkItem* items, int nitems, const char* ws,
                               double* cbase, unsigned* status, cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
-    split_gemm_kernel<<<nitems, GEMM_THREADS, SMEM_BYTES, st>>>(probs, items, ws, cbase, status);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    // one CTA per SM (the TMEM allocation and the operand ring take the whole SM)
+    const int grid = nitems < sms ? nitems : sms;
+    split_gemm_kernel<<<grid, GEMM_THREADS, SMEM_BYTES, st>>>(probs, items, nitems, ws, cbase, status);
     return cudaGetLastError();
 }
 

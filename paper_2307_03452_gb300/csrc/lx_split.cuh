@@ -13,7 +13,7 @@ constexpr int SPLIT_BETA = 8;                        // bits per digit
 constexpr int SPLIT_W = SPLIT_NSLICE * SPLIT_BETA;   // fixed-point bits kept (48)
 constexpr int SPLIT_KB = 32;                         // K block (elements) of one pipeline stage
 constexpr int SPLIT_TA = 128;                        // A row tile = MMA M
-constexpr int SPLIT_TB = 80;                         // largest B row tile (6 diagonals x 80 TMEM columns)
+constexpr int SPLIT_TB = 32;                         // largest B row tile (2 sets x 6 diagonals x 32 TMEM columns)
 constexpr int SPLIT_SEG_KB = 4;                      // K blocks accumulated in TMEM between int64 drains
 
 // One matrix whose rows are split: src at (double*)base + src_off, row stride ld.  Before
@@ -60,8 +60,8 @@ struct SplitGemmDesc {
     int M, N, nkb, ldc, transpose, tb;
 };
 
-// B row tile for an operand of N rows: as many tiles as SPLIT_TB rows need, made as even as
-// a multiple of 16 allows (169 rows -> 3 tiles of 64 rather than 80 + 80 + 9).
+// B row tile for an operand of N rows: as few tiles as SPLIT_TB rows allow, each a multiple
+// of 16 rows (169 rows -> 6 tiles of 32, 81 -> 3 of 32, 13 -> 1 of 16).
 __host__ __device__ inline int split_tb(int N) {
     const int tiles = (N + SPLIT_TB - 1) / SPLIT_TB;
     const int t = (N + tiles - 1) / tiles;
