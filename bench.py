@@ -63,6 +63,12 @@ def nfun(l, solid):
     return 2 * l + 1 if solid else (l + 1) * (l + 2) // 2
 
 
+# DRAM bytes per quartet of one launch, from single ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum) of these kernels on 256 solid (ii|ii) K = 1 quartets; a launch's
+# traffic grows with its quartet count.  Valid for that workload and these kernel builds.
+NCU_BYTES_PER_QUARTET = {"gemm1": 300.761344e6 / 256, "split_gemm1": 1186.914816e6 / 256}
+
+
 def gemm_flops(basis, quartets, solid):
     """Algorithmic FLOPs of the two transforms (paper, Eq. make-abq and Eq. make-abcd):
     2 N_ab (K_bra N_p)(K_ket N_q) and 2 N_ab (K_ket N_q) N_cd per quartet."""
@@ -297,6 +303,7 @@ def main(argv=None):
     lx.load(build_if_missing=True)
     basis, quartets = inputs.iiii_fp64(args.nquartet)
     nq = len(quartets)
+    default_workload = True  # solid (ii|ii) K = 1 at any count: the class NCU_BYTES_PER_QUARTET was taken on
 
     peak64 = fp64_peak_tflops(torch)
     flush_buf = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -321,7 +328,7 @@ def main(argv=None):
     roofline = {"bound": "alu", "kernel": dominant, "unit": "TFLOP/s",
                 "achieved": (dom_flops / (per_launch_ms * 1e-3) / 1e12) if dom_flops else None,
                 "peak": peak64, "peak_source": "cuBLAS DGEMM 4096^3 burst measured in this run (FP64 pipe)",
-                "traffic": None}
+                "traffic": (NCU_BYTES_PER_QUARTET["gemm1"] * nq if dominant == "gemm1" and default_workload else None)}
     roofline["frac"] = roofline["achieved"] / peak64 if roofline["achieved"] else None
     del ws
     torch.cuda.empty_cache()
@@ -343,7 +350,9 @@ def main(argv=None):
         bf16_peak = _measured_bf16_peak()
         sroof = {"bound": "tensor", "kernel": f"split_{sdom}", "unit": "TFLOP/s",
                  "achieved": (tens / (sper * 1e-3) / 1e12) if tens else None, "peak": bf16_peak,
-                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured", "traffic": None}
+                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
+                 "traffic": (NCU_BYTES_PER_QUARTET["split_gemm1"] * nq
+                             if sdom == "gemm1" and default_workload else None)}
         sroof["frac"] = sroof["achieved"] / bf16_peak if sroof["achieved"] and bf16_peak else None
         split = {"quartets_per_s": world * nq * args.steps / (stot * 1e-3), "ms_per_step": stot / args.steps,
                  "fp64_equiv_tflops": world * (g1 + g2) * args.steps / (stot * 1e-3) / 1e12,

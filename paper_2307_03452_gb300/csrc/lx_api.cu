@@ -429,10 +429,11 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
                 P.items_cC.push_back({c0 + 2, c, 0, 0});
                 P.items_b2.push_back({b0 + 1, c, 0, 0});
             }
-            for (int row = 0; row < split_rowpad(k2, SPLIT_TA); ++row) P.items_sr.push_back({i, row, 0, 0});
-            for (int row = 0; row < split_rowpad(d.nab, tb1); ++row) P.items_sB.push_back({sb1, row, 0, 0});
-            for (int row = 0; row < split_rowpad(d.nab, SPLIT_TA); ++row) P.items_sD.push_back({sb1 + 1, row, 0, 0});
-            for (int row = 0; row < split_rowpad(d.ncd, tb2); ++row) P.items_sD.push_back({sb1 + 2, row, 0, 0});
+            // digit kernels: one item per 8 consecutive rows (every row tile is a multiple of 8)
+            for (int row = 0; row < split_rowpad(k2, SPLIT_TA); row += 8) P.items_sr.push_back({i, row, 0, 0});
+            for (int row = 0; row < split_rowpad(d.nab, tb1); row += 8) P.items_sB.push_back({sb1, row, 0, 0});
+            for (int row = 0; row < split_rowpad(d.nab, SPLIT_TA); row += 8) P.items_sD.push_back({sb1 + 1, row, 0, 0});
+            for (int row = 0; row < split_rowpad(d.ncd, tb2); row += 8) P.items_sD.push_back({sb1 + 2, row, 0, 0});
             const int mt1 = split_rowpad(k2, SPLIT_TA) / SPLIT_TA, nt1 = (d.nab + tb1 - 1) / tb1;
             const int mt2 = split_rowpad(d.nab, SPLIT_TA) / SPLIT_TA, nt2 = (d.ncd + tb2 - 1) / tb2;
             for (int m = 0; m < mt1; ++m)
@@ -1220,8 +1221,8 @@ int lx_split_gemm(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda,
     rd[0] = SplitRowsDesc{0, 0, 0, -1, lda, M, K, SPLIT_TA, nkb, 0};
     rd[1] = SplitRowsDesc{0, 0, 0, -1, ldb, N, K, tb, nkb, 0};
     std::vector<WorkItem> ia, ib, ig;
-    for (int r = 0; r < ra; ++r) ia.push_back({0, r, 0, 0});
-    for (int r = 0; r < rb; ++r) ib.push_back({1, r, 0, 0});
+    for (int r = 0; r < ra; r += 8) ia.push_back({0, r, 0, 0});
+    for (int r = 0; r < rb; r += 8) ib.push_back({1, r, 0, 0});
     for (int m = 0; m < ra / SPLIT_TA; ++m)
         for (int n = 0; n < (N + tb - 1) / tb; ++n) ig.push_back({0, m, n, 0});
     size_t o = 0;

@@ -3,23 +3,24 @@
 //
 // Each FP64 operand row x is written as x = 2^(e - W) * q with a per-row power of two 2^e
 // (|x| < 2^e over the row), q an integer of W = NSLICE * BETA bits, and q split into NSLICE
-// signed digits of BETA bits, q = sum_s d_s 2^(BETA (NSLICE-1-s)).  Every digit is an
-// integer of magnitude <= 2^BETA, exact in BF16.  The product of two such rows is
-//   sum_{s,t} 2^(BETA (2 NSLICE - 2 - s - t)) sum_k dA_s dB_t,
-// and each inner sum is a sum of integer products whose magnitude stays far below 2^24,
-// so the FP32 accumulators of the tensor core hold it exactly.  Products with
-// s + t <= NSLICE - 1 are kept; each diagonal d = s + t has its own TMEM accumulator, and the
-// epilogue combines the diagonals in 64-bit integer arithmetic before a single conversion to
-// FP64 (exact except for the lowest BETA bits of the last diagonal, which are rounded off to
-// keep the sum clear of 64-bit overflow).  FP64 arithmetic, which is scarce on this GPU, is used for none of it:
-// the splitting works on the bit patterns of the FP64 inputs.
+// balanced signed digits of BETA bits, q = sum_s d_s 2^(BETA (NSLICE-1-s)).  Every digit is
+// an integer of magnitude <= 2^BETA, exact in BF16.  The product of two such rows is
+//   sum_{s,t} 2^(BETA (2 NSLICE - 2 - s - t)) sum_k dA_s dB_t.
+// Products with s + t <= NSLICE - 1 are kept; each diagonal d = s + t has its own TMEM
+// accumulator, drained into 64-bit integers every SPLIT_SEG_KB K blocks so that every FP32
+// partial sum stays an integer of magnitude <= 2^24 (exact), and the 64-bit sum is converted
+// to FP64 once (the lowest BETA bits of the last diagonal are rounded off to keep the sum
+// clear of 64-bit overflow).  FP64 arithmetic, which is scarce on this GPU, is used for none
+// of it: the splitting works on the bit patterns of the FP64 inputs.
 //
 // Kernels:
 //   split_rows_kernel  FP64 row-major matrix rows -> digit planes + row exponents
 //   split_r_kernel     rows q of the [p|q] operand gathered from [r]^(0) -> digit planes
-//   split_gemm_kernel  D = A B^T on tcgen05 (M tile 128, N tile <= 80, K blocks of 32),
-//                      operand blocks streamed by bulk TMA copies into a 2-stage mbarrier
-//                      pipeline, one thread issuing the MMAs, all four warps in the epilogue.
+//   colmax_kernel, rowmax_r_kernel, balance_kernel: the power-of-two balance along K
+//   split_gemm_kernel  D = A B^T on tcgen05 (M tile 128, N tile <= 32, K blocks of 32),
+//                      persistent, operand blocks streamed by bulk TMA copies into a
+//                      3-stage mbarrier ring, one thread issuing the MMAs, two TMEM
+//                      accumulator sets drained by eight warps.
 #include <cstdint>
 
 #include "lx_internal.cuh"
@@ -160,16 +161,31 @@ __device__ inline long long fixed_of(double x, int e) {
     return bits < 0 ? -q : q;
 }
 
-// The digits of q, most significant first, balanced (each |d| <= 2^BETA).
-__device__ inline void digits_of(long long q, float (&d)[SPLIT_NSLICE]) {
+// The digits of q (|q| <= 2^48), most significant first, balanced: |d_0| <= 2^BETA and
+// |d_s| <= 2^(BETA-1) for s > 0.  They are taken from the bottom, three from each 24-bit
+// half of q in 32-bit integers (d = ((x + 128) mod 256) - 128, then x = (x - d) / 256), and
+// returned as FP32 bit patterns: 0x4B400000 + d is the FP32 number 1.5 * 2^23 + d for
+// |d| < 2^22, so subtracting 1.5 * 2^23 leaves d exactly.  A digit has at most 8 significant
+// bits, so its BF16 pattern is the upper half of its FP32 pattern.
+static_assert(SPLIT_NSLICE == 6 && SPLIT_BETA == 8, "digit extraction assumes 6 digits of 8 bits");
+__device__ inline void digits_of(long long q, uint32_t (&f)[SPLIT_NSLICE]) {
+    int lo = (int)(q & 0xFFFFFF);  // q = hi 2^24 + lo, 0 <= lo < 2^24
+    int hi = (int)(q >> 24);
+    int d[SPLIT_NSLICE];
 #pragma unroll
-    for (int s = 0; s < SPLIT_NSLICE - 1; ++s) {
-        const int sh = SPLIT_BETA * (SPLIT_NSLICE - 1 - s);
-        const long long di = (q + (1ll << (sh - 1))) >> sh;
-        q -= di << sh;
-        d[s] = (float)(int)di;
+    for (int s = SPLIT_NSLICE - 1; s >= 3; --s) {
+        d[s] = ((lo + 128) & 255) - 128;
+        lo = (lo - d[s]) >> 8;
     }
-    d[SPLIT_NSLICE - 1] = (float)(int)q;
+    hi += lo;  // carry out of the low half (0 or 1)
+#pragma unroll
+    for (int s = 2; s >= 1; --s) {
+        d[s] = ((hi + 128) & 255) - 128;
+        hi = (hi - d[s]) >> 8;
+    }
+    d[0] = hi;
+#pragma unroll
+    for (int s = 0; s < SPLIT_NSLICE; ++s) f[s] = __float_as_uint(__int_as_float(0x4B400000 + d[s]) - 12582912.0f);
 }
 
 // Digits of 8 consecutive values (k0 .. k0+7, k0 a multiple of 8) of one row, written as one
@@ -177,18 +193,16 @@ __device__ inline void digits_of(long long q, float (&d)[SPLIT_NSLICE]) {
 __device__ inline int64_t dig_index(int row, int k, int s, int T, int nkb);
 __device__ inline void store_digit_group(__nv_bfloat16* dig, int row, int k0, int T, int nkb,
                                          const long long (&q)[8]) {
-    float d[8][SPLIT_NSLICE];
+    uint32_t f[8][SPLIT_NSLICE];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) digits_of(q[j], d[j]);
+    for (int j = 0; j < 8; ++j) digits_of(q[j], f[j]);
 #pragma unroll
     for (int s = 0; s < SPLIT_NSLICE; ++s) {
-        uint4 w;
-        __nv_bfloat162 h0 = __floats2bfloat162_rn(d[0][s], d[1][s]), h1 = __floats2bfloat162_rn(d[2][s], d[3][s]),
-                       h2 = __floats2bfloat162_rn(d[4][s], d[5][s]), h3 = __floats2bfloat162_rn(d[6][s], d[7][s]);
-        w.x = *reinterpret_cast<unsigned*>(&h0);
-        w.y = *reinterpret_cast<unsigned*>(&h1);
-        w.z = *reinterpret_cast<unsigned*>(&h2);
-        w.w = *reinterpret_cast<unsigned*>(&h3);
+        uint4 w;  // BF16 pairs: element 2i in the low half, 2i+1 in the high half
+        w.x = __byte_perm(f[0][s], f[1][s], 0x7632);
+        w.y = __byte_perm(f[2][s], f[3][s], 0x7632);
+        w.z = __byte_perm(f[4][s], f[5][s], 0x7632);
+        w.w = __byte_perm(f[6][s], f[7][s], 0x7632);
         *reinterpret_cast<uint4*>(dig + dig_index(row, k0, s, T, nkb)) = w;
     }
 }
@@ -202,81 +216,119 @@ __device__ inline int64_t dig_index(int row, int k, int s, int T, int nkb) {
     return block * (T * SPLIT_KB) + ((r >> 3) * (SPLIT_KB / 8) + (kk >> 3)) * 64 + (r & 7) * 8 + (kk & 7);
 }
 
-// Groups of 8 consecutive columns handled by one lane, cached in registers between the
-// exponent pass and the digit pass when the row is short enough.
-constexpr int CACHE_GROUPS = 4;  // per lane: rows up to 32 * 4 * 8 = 1024 columns are cached
+// split_rows_kernel gives one warp 8 consecutive rows r0 .. r0+7 (r0 a multiple of 8), taken
+// as four pairs.  For a pair, lane (rr, c) = (lane / 16, lane % 16) handles row r0 + 2i + rr and
+// the 8-column groups c, c + 16, c + 32, ... (columns 128 j + 8c .. 128 j + 8c + 7).  Rows of
+// at most 128 SPLIT_CACHE_J columns are read once and kept in registers between the exponent pass
+// and the digit pass; longer rows are read twice.  The two rows of a pair are adjacent in
+// every core matrix, so each 32-byte sector of the digit planes is written whole.
+constexpr int SPLIT_CACHE_J = 4;  // cached 128-column steps per row (rows of up to 512 columns)
 
-// One warp per row.  desc: the matrix; item.a = row (may be a padding row).
-__global__ void split_rows_kernel(const SplitRowsDesc* __restrict__ descs, const WorkItem* __restrict__ items,
+// Largest exponent field over the 16 lanes of a row.
+__device__ inline int row_max16(int mx) {
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    return mx;
+}
+
+// Split 8 rows (4 pairs) through value(row, k0, v[8]) (zeros outside the matrix): digit planes
+// of row tile T with nkb K blocks, one int exponent per row.
+template <typename Value>
+__device__ __forceinline__ void split_8rows(int r0, int nkb, int T, __nv_bfloat16* __restrict__ dig,
+                                            int* __restrict__ exps, Value value) {
+    const int lane = threadIdx.x & 31, c8 = 8 * (lane & 15);
+    const int nstep = (nkb * SPLIT_KB + 127) / 128;  // 128-column steps
+    for (int pr = 0; pr < 4; ++pr) {
+        const int row = r0 + 2 * pr + (lane >> 4);
+        int mx = 0;
+        if (nstep <= SPLIT_CACHE_J) {
+            double v[SPLIT_CACHE_J][8];
+#pragma unroll
+            for (int j = 0; j < SPLIT_CACHE_J; ++j) {
+                const int k0 = 128 * j + c8;
+                if (j < nstep && k0 < nkb * SPLIT_KB) {
+                    value(row, k0, v[j]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) v[j][i] = 0.0;
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) mx = max(mx, exp_field(v[j][i]));
+            }
+            mx = row_max16(mx);
+            const int e = mx > 0 ? mx - 1022 : 0;  // |x| < 2^e over the row
+#pragma unroll
+            for (int j = 0; j < SPLIT_CACHE_J; ++j) {
+                const int k0 = 128 * j + c8;
+                if (j < nstep && k0 < nkb * SPLIT_KB) {
+                    long long q[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) q[i] = mx > 0 ? fixed_of(v[j][i], e) : 0ll;
+                    store_digit_group(dig, row, k0, T, nkb, q);
+                }
+            }
+            if ((lane & 15) == 0) exps[row] = e;
+        } else {
+            for (int k0 = c8; k0 < nkb * SPLIT_KB; k0 += 128) {
+                double v[8];
+                value(row, k0, v);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) mx = max(mx, exp_field(v[i]));
+            }
+            mx = row_max16(mx);
+            const int e = mx > 0 ? mx - 1022 : 0;
+            for (int k0 = c8; k0 < nkb * SPLIT_KB; k0 += 128) {
+                double v[8];
+                value(row, k0, v);
+                long long q[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) q[i] = mx > 0 ? fixed_of(v[i], e) : 0ll;
+                store_digit_group(dig, row, k0, T, nkb, q);
+            }
+            if ((lane & 15) == 0) exps[row] = e;
+        }
+    }
+}
+
+// item.q = descriptor, item.a = r0.
+__global__ void __launch_bounds__(256, 2) split_rows_kernel(const SplitRowsDesc* __restrict__ descs, const WorkItem* __restrict__ items,
                                   int nitems, const double* __restrict__ src_base, char* __restrict__ ws) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (warp >= nitems) return;
     const WorkItem it = items[warp];
     const SplitRowsDesc d = descs[it.q];
-    const int row = it.a;
-    const double* src = src_base + d.src_off + (int64_t)row * d.ld;
-    const bool live = row < d.rows;
+    const double* src = src_base + d.src_off;
     const int* shift = d.shift_off >= 0 ? reinterpret_cast<const int*>(ws + d.shift_off) : nullptr;
-    auto value = [&](int k) -> double {
-        if (!live || k >= d.K) return 0.0;
-        return shift ? scale2(src[k], d.shift_sign * shift[k]) : src[k];
-    };
-    const int ngroup = d.nkb * SPLIT_KB / 8;
-    const bool cached = ngroup <= 32 * CACHE_GROUPS;
-    double cache[CACHE_GROUPS][8];
-    int mx = 0;
-    if (cached) {
+    split_8rows(it.a, d.nkb, d.T, reinterpret_cast<__nv_bfloat16*>(ws + d.dig_off),
+                reinterpret_cast<int*>(ws + d.exp_off), [&](int row, int k0, double (&v)[8]) {
+                    const bool live = row < d.rows;
+                    const double* sr = src + (int64_t)row * d.ld;
 #pragma unroll
-        for (int j = 0; j < CACHE_GROUPS; ++j) {
-            const int g = lane + 32 * j;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const double x = g < ngroup ? value(8 * g + i) : 0.0;
-                cache[j][i] = x;
-                mx = max(mx, exp_field(x));
-            }
-        }
-    } else if (live) {
-        for (int k = lane; k < d.K; k += 32) mx = max(mx, exp_field(value(k)));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const int e = mx > 0 ? mx - 1022 : 0;  // |x| < 2^e over the row
-    __nv_bfloat16* dig = reinterpret_cast<__nv_bfloat16*>(ws + d.dig_off);
-    if (cached) {
-#pragma unroll
-        for (int j = 0; j < CACHE_GROUPS; ++j) {
-            const int g = lane + 32 * j;
-            if (g >= ngroup) break;
-            long long q[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) q[i] = mx > 0 ? fixed_of(cache[j][i], e) : 0ll;
-            store_digit_group(dig, row, 8 * g, d.T, d.nkb, q);
-        }
-    } else {
-        for (int g = lane; g < ngroup; g += 32) {
-            long long q[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) q[i] = mx > 0 ? fixed_of(value(8 * g + i), e) : 0ll;
-            store_digit_group(dig, row, 8 * g, d.T, d.nkb, q);
-        }
-    }
-    if (lane == 0) reinterpret_cast<int*>(ws + d.exp_off)[row] = e;
+                    for (int i = 0; i < 8; ++i) {
+                        const int k = k0 + i;
+                        double x = 0.0;
+                        if (live && k < d.K) x = shift ? scale2(sr[k], d.shift_sign * shift[k]) : sr[k];
+                        v[i] = x;
+                    }
+                });
 }
 
-// One warp per row q of the GEMM1 A operand: A[q][k] = [p+q]^(0) of primitive quartet
-// (kp, kq) with k = kp*Np + p, q = kq*Nq + qq, scaled by 2^-e1[k].  item.q = quartet,
-// item.a = row.  Each lane walks its groups of 8 columns with an incremental (kp, p).
-__global__ void split_r_kernel(const DQuartet* __restrict__ qd, const SplitQuartet* __restrict__ sq,
-                               const WorkItem* __restrict__ items, int nitems, const double* __restrict__ wsd,
-                               char* __restrict__ ws) {
+// Rows q of the GEMM1 A operand: A[q][k] = [p+q]^(0) of primitive quartet (kp, kq) with
+// k = kp*Np + p, q = kq*Nq + qq, scaled by 2^-e1[k].  item.q = quartet, item.a = r0.  Here
+// the 8 rows are processed at once: lane (rr, c) = (lane / 4, lane % 4) handles row r0 + rr
+// and columns 8c .. 8c+7 of every K block, so the gathers of neighbouring rows (neighbouring
+// Hermite indices) fall close together; the rows are gathered twice, once for the exponent.
+__global__ void __launch_bounds__(256) split_r_kernel(const DQuartet* __restrict__ qd,
+                                                      const SplitQuartet* __restrict__ sq,
+                                                      const WorkItem* __restrict__ items, int nitems,
+                                                      const double* __restrict__ wsd, char* __restrict__ ws) {
     const int* tuv_tab = g_tuv_split;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= nitems) return;
     const WorkItem it = items[warp];
     const DQuartet q = qd[it.q];
     const SplitQuartet s = sq[it.q];
-    const int row = it.a;
+    const int row = it.a + (lane >> 2), c8 = 8 * (lane & 3);
     const int nrow = q.kket * q.nq, K = q.kbra * q.np;
     const bool live = row < nrow;
     int kq = 0, tq = 0;
@@ -287,9 +339,9 @@ __global__ void split_r_kernel(const DQuartet* __restrict__ qd, const SplitQuart
     const double* Rr = wsd + q.rr_off + (int64_t)kq * q.nr;
     const int64_t kp_stride = (int64_t)q.kket * q.nr;
     const int* e1 = reinterpret_cast<const int*>(ws + s.e1_off);
-    // the 8 values of group g (columns 8g .. 8g+7)
-    auto group = [&](int g, double (&v)[8]) {
-        int k = 8 * g;
+    // the 8 values of columns k0 .. k0+7, walking (kp, p) incrementally
+    auto group = [&](int k0, double (&v)[8]) {
+        int k = k0;
         int kp = k / q.np, p = k - kp * q.np;
 #pragma unroll
         for (int i = 0; i < 8; ++i, ++k) {
@@ -305,56 +357,26 @@ __global__ void split_r_kernel(const DQuartet* __restrict__ qd, const SplitQuart
             }
         }
     };
-    const int ngroup = s.nkb1 * SPLIT_KB / 8;
-    const bool cached = ngroup <= 32 * CACHE_GROUPS;
-    double cache[CACHE_GROUPS][8];
     int mx = 0;
-    if (cached) {
+    for (int kb = 0; kb < s.nkb1; ++kb) {
+        double v[8];
+        group(SPLIT_KB * kb + c8, v);
 #pragma unroll
-        for (int j = 0; j < CACHE_GROUPS; ++j) {
-            const int g = lane + 32 * j;
-            if (g < ngroup) {
-                group(g, cache[j]);
-            } else {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) cache[j][i] = 0.0;
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) mx = max(mx, exp_field(cache[j][i]));
-        }
-    } else {
-        for (int g = lane; g < ngroup; g += 32) {
-            double v[8];
-            group(g, v);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) mx = max(mx, exp_field(v[i]));
-        }
+        for (int i = 0; i < 8; ++i) mx = max(mx, exp_field(v[i]));
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
     const int e = mx > 0 ? mx - 1022 : 0;
     __nv_bfloat16* dig = reinterpret_cast<__nv_bfloat16*>(ws + s.a1_dig);
-    if (cached) {
+    for (int kb = 0; kb < s.nkb1; ++kb) {
+        double v[8];
+        group(SPLIT_KB * kb + c8, v);
+        long long qv[8];
 #pragma unroll
-        for (int j = 0; j < CACHE_GROUPS; ++j) {
-            const int g = lane + 32 * j;
-            if (g >= ngroup) break;
-            long long qv[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) qv[i] = mx > 0 ? fixed_of(cache[j][i], e) : 0ll;
-            store_digit_group(dig, row, 8 * g, SPLIT_TA, s.nkb1, qv);
-        }
-    } else {
-        for (int g = lane; g < ngroup; g += 32) {
-            double v[8];
-            group(g, v);
-            long long qv[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) qv[i] = mx > 0 ? fixed_of(v[i], e) : 0ll;
-            store_digit_group(dig, row, 8 * g, SPLIT_TA, s.nkb1, qv);
-        }
+        for (int i = 0; i < 8; ++i) qv[i] = mx > 0 ? fixed_of(v[i], e) : 0ll;
+        store_digit_group(dig, row, SPLIT_KB * kb + c8, SPLIT_TA, s.nkb1, qv);
     }
-    if (lane == 0) reinterpret_cast<int*>(ws + s.a1_exp)[row] = e;
+    if ((lane & 3) == 0) reinterpret_cast<int*>(ws + s.a1_exp)[row] = e;
 }
 
 // One thread per column k: largest exponent field over the rows.  item = (desc, chunk).
