@@ -193,18 +193,19 @@ __device__ inline void digits_of(long long q, uint32_t (&f)[SPLIT_NSLICE]) {
 __device__ inline int64_t dig_index(int row, int k, int s, int T, int nkb);
 __device__ inline void store_digit_group(__nv_bfloat16* dig, int row, int k0, int T, int nkb,
                                          const long long (&q)[8]) {
-    uint32_t f[8][SPLIT_NSLICE];
+    // w[s][i]: BF16 pair of slice s, element 2i in the low half and 2i + 1 in the high half
+    uint32_t w[SPLIT_NSLICE][4];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) digits_of(q[j], f[j]);
+    for (int j = 0; j < 8; j += 2) {
+        uint32_t f0[SPLIT_NSLICE], f1[SPLIT_NSLICE];
+        digits_of(q[j], f0);
+        digits_of(q[j + 1], f1);
 #pragma unroll
-    for (int s = 0; s < SPLIT_NSLICE; ++s) {
-        uint4 w;  // BF16 pairs: element 2i in the low half, 2i+1 in the high half
-        w.x = __byte_perm(f[0][s], f[1][s], 0x7632);
-        w.y = __byte_perm(f[2][s], f[3][s], 0x7632);
-        w.z = __byte_perm(f[4][s], f[5][s], 0x7632);
-        w.w = __byte_perm(f[6][s], f[7][s], 0x7632);
-        *reinterpret_cast<uint4*>(dig + dig_index(row, k0, s, T, nkb)) = w;
+        for (int s = 0; s < SPLIT_NSLICE; ++s) w[s][j >> 1] = __byte_perm(f0[s], f1[s], 0x7632);
     }
+#pragma unroll
+    for (int s = 0; s < SPLIT_NSLICE; ++s)
+        *reinterpret_cast<uint4*>(dig + dig_index(row, k0, s, T, nkb)) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
 }
 
 // Offset (in BF16 elements) of element (row, k) of slice s inside an operand stored as
@@ -218,11 +219,10 @@ __device__ inline int64_t dig_index(int row, int k, int s, int T, int nkb) {
 
 // split_rows_kernel gives one warp 8 consecutive rows r0 .. r0+7 (r0 a multiple of 8), taken
 // as four pairs.  For a pair, lane (rr, c) = (lane / 16, lane % 16) handles row r0 + 2i + rr and
-// the 8-column groups c, c + 16, c + 32, ... (columns 128 j + 8c .. 128 j + 8c + 7).  Rows of
-// at most 128 SPLIT_CACHE_J columns are read once and kept in registers between the exponent pass
-// and the digit pass; longer rows are read twice.  The two rows of a pair are adjacent in
-// every core matrix, so each 32-byte sector of the digit planes is written whole.
-constexpr int SPLIT_CACHE_J = 4;  // cached 128-column steps per row (rows of up to 512 columns)
+// the 8-column groups c, c + 16, c + 32, ... (columns 128 j + 8c .. 128 j + 8c + 7).  A pair is
+// read twice, once for its exponent and once for its digits; the two reads are close enough
+// in time that the second comes from L1 or L2.  The two rows of a pair are adjacent in every
+// core matrix, so each 32-byte sector of the digit planes is written whole.
 
 // Largest exponent field over the 16 lanes of a row.
 __device__ inline int row_max16(int mx) {
@@ -237,61 +237,31 @@ template <typename Value>
 __device__ __forceinline__ void split_8rows(int r0, int nkb, int T, __nv_bfloat16* __restrict__ dig,
                                             int* __restrict__ exps, Value value) {
     const int lane = threadIdx.x & 31, c8 = 8 * (lane & 15);
-    const int nstep = (nkb * SPLIT_KB + 127) / 128;  // 128-column steps
     for (int pr = 0; pr < 4; ++pr) {
         const int row = r0 + 2 * pr + (lane >> 4);
         int mx = 0;
-        if (nstep <= SPLIT_CACHE_J) {
-            double v[SPLIT_CACHE_J][8];
+        for (int k0 = c8; k0 < nkb * SPLIT_KB; k0 += 128) {
+            double v[8];
+            value(row, k0, v);
 #pragma unroll
-            for (int j = 0; j < SPLIT_CACHE_J; ++j) {
-                const int k0 = 128 * j + c8;
-                if (j < nstep && k0 < nkb * SPLIT_KB) {
-                    value(row, k0, v[j]);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) v[j][i] = 0.0;
-                }
-#pragma unroll
-                for (int i = 0; i < 8; ++i) mx = max(mx, exp_field(v[j][i]));
-            }
-            mx = row_max16(mx);
-            const int e = mx > 0 ? mx - 1022 : 0;  // |x| < 2^e over the row
-#pragma unroll
-            for (int j = 0; j < SPLIT_CACHE_J; ++j) {
-                const int k0 = 128 * j + c8;
-                if (j < nstep && k0 < nkb * SPLIT_KB) {
-                    long long q[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) q[i] = mx > 0 ? fixed_of(v[j][i], e) : 0ll;
-                    store_digit_group(dig, row, k0, T, nkb, q);
-                }
-            }
-            if ((lane & 15) == 0) exps[row] = e;
-        } else {
-            for (int k0 = c8; k0 < nkb * SPLIT_KB; k0 += 128) {
-                double v[8];
-                value(row, k0, v);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) mx = max(mx, exp_field(v[i]));
-            }
-            mx = row_max16(mx);
-            const int e = mx > 0 ? mx - 1022 : 0;
-            for (int k0 = c8; k0 < nkb * SPLIT_KB; k0 += 128) {
-                double v[8];
-                value(row, k0, v);
-                long long q[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) q[i] = mx > 0 ? fixed_of(v[i], e) : 0ll;
-                store_digit_group(dig, row, k0, T, nkb, q);
-            }
-            if ((lane & 15) == 0) exps[row] = e;
+            for (int i = 0; i < 8; ++i) mx = max(mx, exp_field(v[i]));
         }
+        mx = row_max16(mx);
+        const int e = mx > 0 ? mx - 1022 : 0;  // |x| < 2^e over the row
+        for (int k0 = c8; k0 < nkb * SPLIT_KB; k0 += 128) {
+            double v[8];
+            value(row, k0, v);
+            long long q[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) q[i] = mx > 0 ? fixed_of(v[i], e) : 0ll;
+            store_digit_group(dig, row, k0, T, nkb, q);
+        }
+        if ((lane & 15) == 0) exps[row] = e;
     }
 }
 
 // item.q = descriptor, item.a = r0.
-__global__ void __launch_bounds__(256, 2) split_rows_kernel(const SplitRowsDesc* __restrict__ descs, const WorkItem* __restrict__ items,
+__global__ void __launch_bounds__(256) split_rows_kernel(const SplitRowsDesc* __restrict__ descs, const WorkItem* __restrict__ items,
                                   int nitems, const double* __restrict__ src_base, char* __restrict__ ws) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (warp >= nitems) return;
