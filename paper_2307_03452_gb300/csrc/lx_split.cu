@@ -496,13 +496,21 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
+            // Descriptors are built once: the start-address field (bits 0-13, address / 16)
+            // of a descriptor is advanced by adding offset / 16, which cannot carry out of
+            // the field since shared memory ends below 2^18 bytes.
             const uint32_t sbase = smem_u32(smem);
+            const uint64_t a_desc0 = smem_desc(sbase, 128, (SPLIT_KB / 8) * 128);
+            const uint64_t b_desc0 = smem_desc(sbase + A_BLOCK, 128, (SPLIT_KB / 8) * 128);
             int g = 0, sgc = 0;  // K blocks consumed, segments issued
             bool ok = true;
             for (int w = blockIdx.x; w < nitems && ok; w += gridDim.x) {
                 const WorkItem it = items[w];
                 const SplitGemmDesc P = probs[it.q];
                 const int tb = P.tb, nkb = P.nkb;
+                uint32_t idesc[SPLIT_NSLICE];
+#pragma unroll
+                for (int s = 0; s < SPLIT_NSLICE; ++s) idesc[s] = idesc_bf16(SPLIT_TA, (SPLIT_NSLICE - s) * tb);
                 for (int kb0 = 0; kb0 < nkb && ok; kb0 += SPLIT_SEG_KB, ++sgc) {
                     const int buf = sgc & 1, ub = sgc >> 1;
                     if (ub > 0) {
@@ -522,17 +530,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t sa = sbase + st * STAGE_BYTES;
-                        const uint32_t sb = sa + A_BLOCK;
+                        const uint64_t st_off = (uint64_t)((st * STAGE_BYTES) >> 4);
+                        const uint64_t ad0 = a_desc0 + st_off, bd0 = b_desc0 + st_off;
 #pragma unroll
                         for (int ks = 0; ks < SPLIT_KB / 16; ++ks) {
-                            const uint64_t bd = smem_desc(sb + ks * 256, 128, (SPLIT_KB / 8) * 128);
 #pragma unroll
                             for (int s = 0; s < SPLIT_NSLICE; ++s) {
-                                const uint64_t ad = smem_desc(sa + s * A_SLICE + ks * 256, 128, (SPLIT_KB / 8) * 128);
                                 // the slice-0 MMA of a segment's first K step covers every diagonal
-                                const uint32_t acc = (kb == kb0 && ks == 0 && s == 0) ? 0u : 1u;
-                                umma_bf16(dcol + s * tb, ad, bd, idesc_bf16(SPLIT_TA, (SPLIT_NSLICE - s) * tb), acc);
+                                const uint32_t acc = (ks == 0 && s == 0 && kb == kb0) ? 0u : 1u;
+                                umma_bf16(dcol + s * tb, ad0 + ((s * A_SLICE + ks * 256) >> 4), bd0 + ((ks * 256) >> 4),
+                                          idesc[s], acc);
                             }
                         }
                         umma_commit(&empty_bar[st]);  // the stage is free once these MMAs have read it
