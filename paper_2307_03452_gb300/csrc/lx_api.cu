@@ -194,7 +194,7 @@ size_t quartet_bytes(const lx_shell* sh, const lx_quartet& q, int flags) {
     const int64_t kbra = (int64_t)a.nprim * b.nprim, kket = (int64_t)c.nprim * d.nprim;
     const int64_t nab = (int64_t)nfun(a.l, solid) * nfun(b.l, solid), ncd = (int64_t)nfun(c.l, solid) * nfun(d.l, solid);
     const int64_t n1 = kket * nq;
-    int64_t items = (kbra * kket + 3) / 4;
+    int64_t items = kbra * kket;
     // + 256 bytes per data block: each block starts on a 256-byte boundary
     size_t bytes = sizeof(DQuartet) + 8 * (size_t)(kbra * kket * pyr(L) + nab * n1) + 512;
     if (!split) {
@@ -273,6 +273,7 @@ struct ChunkPlan {
     std::vector<DPair> pairs;
     std::vector<DQuartet> quartets;
     std::vector<WorkItem> items_h, items_br, items_g1, items_g2;
+    int br_lmax = 0;  // largest L of the chunk's quartets
     size_t off_pairs = 0, off_quartets = 0, off_h = 0, off_br = 0, off_g1 = 0, off_g2 = 0, off_data = 0;
     int g1_counts[GEMM_NVARIANT] = {0, 0, 0, 0}, g2_counts[GEMM_NVARIANT] = {0, 0, 0, 0};
     size_t off_counters = 0;  // 2 x GEMM_NVARIANT work counters, uploaded as zeros with the blob
@@ -299,6 +300,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     P.quartets.clear();
     P.items_h.clear();
     P.items_br.clear();
+    P.br_lmax = 0;
     P.items_g1.clear();
     P.items_g2.clear();
     P.srd.clear();
@@ -353,7 +355,8 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         for (int i = 0; i < (int)P.quartets.size(); ++i) {
             const DQuartet& d = P.quartets[i];
-            for (int k = 0; k < d.kbra * d.kket; k += 4) P.items_br.push_back({i, k, 0, 0});
+            for (int k = 0; k < d.kbra * d.kket; ++k) P.items_br.push_back({i, k, 0, 0});
+            P.br_lmax = std::max(P.br_lmax, d.L);
             if (split) continue;
             int v1 = GEMM_V32x64, v2 = GEMM_V32x64;
             auto f = g_tune.find(tune_key(sh, qs[ch.q_begin + i], solid));
@@ -701,7 +704,8 @@ int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector
             return cuda_fail(e);
         if ((e = tm.end(LX_STAGE_PAIR, 1)) != cudaSuccess) return cuda_fail(e);
         if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
-        if ((e = launch_boys_r(d_q, d_pairs, d_ibr, (int)P.items_br.size(), ws, status, st)) != cudaSuccess)
+        if ((e = launch_boys_r(d_q, d_pairs, d_ibr, (int)P.items_br.size(), P.br_lmax, ws, status, st)) !=
+            cudaSuccess)
             return cuda_fail(e);
         if ((e = tm.end(LX_STAGE_BOYS_R, 1)) != cudaSuccess) return cuda_fail(e);
         if (split) {

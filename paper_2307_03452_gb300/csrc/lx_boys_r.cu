@@ -9,6 +9,8 @@
 // array of pyr(L) doubles, overwriting [r]^(m+1) with [r]^(m) (the paper's in-place
 // scheme, Section 3): within level m the totals n = |r| are processed from L-m down
 // to 1, so the inputs at totals n-1 and n-2 still hold level m+1 when they are read.
+// In the batch kernel each CTA is that one warp, with shared memory for the chunk's
+// largest L, so that as many quartets as shared memory allows run side by side.
 #include <cmath>
 
 #include "lx_internal.cuh"
@@ -18,6 +20,9 @@ namespace lx {
 namespace {
 
 __device__ double g_boys[BOYS_NROW * BOYS_NPT];
+// Within-total position s -> (i, v) with s = i(i+1)/2 + v, packed i | v << 8, s < (LTOT+1)(LTOT+2)/2.
+constexpr int NPOS = (LTOT + 1) * (LTOT + 2) / 2;
+__device__ int g_pos[NPOS];
 
 constexpr double PI = 3.141592653589793238462643383279502884;
 
@@ -64,10 +69,9 @@ __device__ inline void scale_base(int L, double rho, double pref, double* B, int
 
 // Within-total position s (0 <= s < (n+1)(n+2)/2) -> (i, v) with s = i(i+1)/2 + v.
 __device__ inline void split_pos(int s, int& i, int& v) {
-    i = (int)((sqrtf(8.0f * s + 1.0f) - 1.0f) * 0.5f);
-    while ((i + 1) * (i + 2) / 2 <= s) ++i;
-    while (i * (i + 1) / 2 > s) --i;
-    v = s - i * (i + 1) / 2;
+    const int w = __ldg(&g_pos[s]);
+    i = w & 255;
+    v = w >> 8;
 }
 
 // In-place Eq. md1 on R[pyr(L)] (shared memory), by one warp.  B[m] = [0]^(m), m = 0..L.
@@ -105,22 +109,19 @@ __device__ void hermite_r_warp(int L, double X, double Y, double Z, const double
     }
 }
 
-constexpr int BR_WARPS = 4;
+constexpr int BR_WARPS = 4;  // warps per CTA of the stage entry point
 
-// One warp per primitive quartet: item.q = quartet, item.a = first primitive quartet of the
-// CTA's group of BR_WARPS (kpq = kp * kket + kq).
-__global__ void __launch_bounds__(BR_WARPS * 32) boys_r_kernel(const DQuartet* __restrict__ qd,
-                                                               const DPair* __restrict__ pairs,
-                                                               const WorkItem* __restrict__ items,
-                                                               double* __restrict__ ws, unsigned* status) {
+// One single-warp CTA per primitive quartet: item.q = quartet, item.a = kpq = kp * kket + kq.
+__global__ void __launch_bounds__(32) boys_r_kernel(const DQuartet* __restrict__ qd, const DPair* __restrict__ pairs,
+                                                    const WorkItem* __restrict__ items, double* __restrict__ ws,
+                                                    unsigned* status) {
     extern __shared__ double smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
     const WorkItem it = items[blockIdx.x];
     const DQuartet q = qd[it.q];
-    const int kpq = it.a + warp;
-    if (kpq >= q.kbra * q.kket) return;
+    const int kpq = it.a;
     const int nr = q.nr;
-    double* R = smem + warp * (nr + LTOT + 1);
+    double* R = smem;
     double* B = R + nr;
     const int kp = kpq / q.kket, kq = kpq - kp * q.kket;
     const DPair pb = pairs[q.pb], pk = pairs[q.pk];
@@ -182,16 +183,23 @@ size_t br_smem(int L) { return sizeof(double) * BR_WARPS * (size_t)(pyr(L) + LTO
 cudaError_t init_boys_table(const double* host_table) {
     cudaError_t e = cudaMemcpyToSymbol(g_boys, host_table, sizeof(double) * BOYS_NROW * BOYS_NPT);
     if (e != cudaSuccess) return e;
-    const size_t maxsm = br_smem(LTOT);
-    e = cudaFuncSetAttribute(boys_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxsm);
+    int pos[NPOS];
+    for (int i = 0, s = 0; s < NPOS; ++i)
+        for (int v = 0; v <= i && s < NPOS; ++v, ++s) pos[s] = i | (v << 8);
+    if ((e = cudaMemcpyToSymbol(g_pos, pos, sizeof(pos))) != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(boys_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * (pyr(LTOT) + LTOT + 1)));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(hermite_r_stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxsm);
+    return cudaFuncSetAttribute(hermite_r_stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)br_smem(LTOT));
 }
 
-cudaError_t launch_boys_r(const DQuartet* qd, const DPair* pairs, const WorkItem* items, int nitems, double* ws,
-                          unsigned* status, cudaStream_t st) {
+cudaError_t launch_boys_r(const DQuartet* qd, const DPair* pairs, const WorkItem* items, int nitems, int lmax,
+                          double* ws, unsigned* status, cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
-    boys_r_kernel<<<nitems, BR_WARPS * 32, br_smem(LTOT), st>>>(qd, pairs, items, ws, status);
+    if (lmax < 0 || lmax > LTOT) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(double) * (pyr(lmax) + LTOT + 1);
+    boys_r_kernel<<<nitems, 32, smem, st>>>(qd, pairs, items, ws, status);
     return cudaGetLastError();
 }
 

@@ -82,8 +82,8 @@ cudaError_t launch_norm(const DShell* sh, int nshell, const double* exps, const 
 cudaError_t launch_pair_h(const DPair* pairs, const WorkItem* items, int nitems, const DShell* sh,
                           const double* exps, const double* ncoef, double* ws, double* ws_info, bool solid,
                           unsigned* status, cudaStream_t st);
-cudaError_t launch_boys_r(const DQuartet* qd, const DPair* pairs, const WorkItem* items, int nitems, double* ws,
-                          unsigned* status, cudaStream_t st);
+cudaError_t launch_boys_r(const DQuartet* qd, const DPair* pairs, const WorkItem* items, int nitems, int lmax,
+                          double* ws, unsigned* status, cudaStream_t st);  // lmax: largest L of the items
 // items grouped by tile shape: counts[v] items of shape v, in shape order; counters[v] is the
 // zero-initialised work counter of shape v's launch
 cudaError_t launch_gemm1(const DQuartet* qd, const DPair* pairs, const WorkItem* items, const int* counts, double* ws,
