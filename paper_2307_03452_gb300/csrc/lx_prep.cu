@@ -185,17 +185,29 @@ __global__ void __launch_bounds__(PAIR_THREADS) pair_h_kernel(const DPair* __res
 
 // Rows of one fold stage, one warp per group of 32 rows (lane = row within the group):
 // acc = sum_j term(ent[gptr[g] + 32 j + lane]); every lane of a group runs the same count.
+// A warp takes two groups at a time (g and g + nwarp, of similar length since the groups are
+// sorted by length) so that twice as many loads are in flight.
 template <typename Term, typename Store>
 __device__ __forceinline__ void fold_stage(int grp0, int nrow, const int* __restrict__ gptr,
                                            const int* __restrict__ ent, Term term, Store store) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int g = warp; 32 * g < nrow; g += nwarp) {
-        const int e0 = __ldg(&gptr[grp0 + g]), e1 = __ldg(&gptr[grp0 + g + 1]);
-        double acc = 0.0;
-#pragma unroll 4
-        for (int e = e0 + lane; e < e1; e += 32) acc += term(__ldg(&ent[e]));
+    for (int g = warp; 32 * g < nrow; g += 2 * nwarp) {
+        const int g2 = g + nwarp;
+        const bool two = 32 * g2 < nrow;
+        const int a0 = __ldg(&gptr[grp0 + g]), a1 = __ldg(&gptr[grp0 + g + 1]);
+        const int b0 = two ? __ldg(&gptr[grp0 + g2]) : 0, b1 = two ? __ldg(&gptr[grp0 + g2 + 1]) : 0;
+        const int na = (a1 - a0) >> 5, nb = (b1 - b0) >> 5;
+        double acc_a = 0.0, acc_b = 0.0;
+        const int n = na > nb ? na : nb;
+#pragma unroll 2
+        for (int j = 0; j < n; ++j) {
+            if (j < na) acc_a += term(__ldg(&ent[a0 + 32 * j + lane]));
+            if (j < nb) acc_b += term(__ldg(&ent[b0 + 32 * j + lane]));
+        }
         const int r = 32 * g + lane;
-        if (r < nrow) store(r, acc);
+        if (r < nrow) store(r, acc_a);
+        const int r2 = 32 * g2 + lane;
+        if (two && r2 < nrow) store(r2, acc_b);
     }
 }
 
