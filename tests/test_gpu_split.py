@@ -101,3 +101,19 @@ def test_split_and_fp64_paths_agree_on_full_size_iiii():
     a, _ = lx.eri(basis, quartets, solid=True, path="fp64")
     b, _ = lx.eri(basis, quartets, solid=True, path="split")
     assert float((a - b).abs().max()) <= 1e-10
+
+
+def test_both_paths_at_maximum_contraction():
+    # K = 16 on every shell, the library's limit.  The bra reduction of (ff|ss) and the ket
+    # reduction of (ss|ff) are 256 x 84 = 21504 > 2^14 long, so the split path's 64-bit sums
+    # take the extra shift in GEMM1 and in GEMM2; (dd|dd) with K = 8 rides along.
+    b1 = inputs.uniform_class((3, 3, 0, 0), 2, 97, cube=3.0, exps=(0.1, 10.0), kmin=16, kmax=16)
+    b2 = inputs.uniform_class((0, 0, 3, 3), 2, 99, cube=3.0, exps=(0.1, 10.0), kmin=16, kmax=16)
+    b3 = inputs.uniform_class((2, 2, 2, 2), 1, 98, cube=3.0, exps=(0.1, 10.0), kmin=8, kmax=8)
+    basis, quartets = inputs.concat([b1, b2, b3])
+    ref, roff = oracle.eri(basis, quartets, solid=True)
+    for path in ("split", "fp64"):
+        out, off = lx.eri(basis, quartets, solid=True, path=path)
+        assert np.array_equal(off, roff)
+        err = np.abs(out.cpu().numpy() - ref).max()
+        assert err <= 1e-10, f"{path}: max abs err {err:.3e}"
