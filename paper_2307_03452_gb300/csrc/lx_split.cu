@@ -22,6 +22,7 @@
 //                      3-stage mbarrier ring, one thread issuing the MMAs, two TMEM
 //                      accumulator sets drained by eight warps.
 #include <cstdint>
+#include <vector>
 
 #include "lx_internal.cuh"
 #include "lx_split.cuh"
@@ -288,11 +289,20 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const SplitRowsDesc* __
 // the 8 rows are processed at once: lane (rr, c) = (lane / 4, lane % 4) handles row r0 + rr
 // and columns 8c .. 8c+7 of every K block, so the gathers of neighbouring rows (neighbouring
 // Hermite indices) fall close together; the rows are gathered twice, once for the exponent.
+// Hermite triplets are carried as n | i << 8 | v << 16 (n = t+u+v, i = u+v), which add
+// componentwise, and hidx(t, u, v) = n(n+1)(n+2)/6 + i(i+1)/2 + v comes from two small tables.
+__device__ int g_niv_split[NHERM_TOT];
 __global__ void __launch_bounds__(256) split_r_kernel(const DQuartet* __restrict__ qd,
                                                       const SplitQuartet* __restrict__ sq,
                                                       const WorkItem* __restrict__ items, int nitems,
                                                       const double* __restrict__ wsd, char* __restrict__ ws) {
-    const int* tuv_tab = g_tuv_split;
+    __shared__ int tab_n[2 * LTOT + 2], tab_i[2 * LTOT + 2];
+    for (int j = threadIdx.x; j < 2 * LTOT + 2; j += blockDim.x) {
+        tab_n[j] = j * (j + 1) * (j + 2) / 6;
+        tab_i[j] = j * (j + 1) / 2;
+    }
+    __syncthreads();
+    const int* niv = g_niv_split;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (warp >= nitems) return;
     const WorkItem it = items[warp];
@@ -301,38 +311,46 @@ __global__ void __launch_bounds__(256) split_r_kernel(const DQuartet* __restrict
     const int row = it.a + (lane >> 2), c8 = 8 * (lane & 3);
     const int nrow = q.kket * q.nq, K = q.kbra * q.np;
     const bool live = row < nrow;
-    int kq = 0, tq = 0;
+    int kq = 0, nq_ = 0;
     if (live) {
         kq = row / q.nq;
-        tq = tuv_tab[row - kq * q.nq];
+        nq_ = niv[row - kq * q.nq];
     }
     const double* Rr = wsd + q.rr_off + (int64_t)kq * q.nr;
     const int64_t kp_stride = (int64_t)q.kket * q.nr;
     const int* e1 = reinterpret_cast<const int*>(ws + s.e1_off);
-    // the 8 values of columns k0 .. k0+7, walking (kp, p) incrementally
-    auto group = [&](int k0, double (&v)[8]) {
+    // [p+q]^(0) of columns k0 .. k0+7 (unscaled) and their shifts, walking (kp, p)
+    auto group = [&](int k0, double (&v)[8], int (&sh)[8]) {
         int k = k0;
         int kp = k / q.np, p = k - kp * q.np;
 #pragma unroll
         for (int i = 0; i < 8; ++i, ++k) {
             double x = 0.0;
+            int h = 0;
             if (live && k < K) {
-                const int sum = tuv_tab[p] + tq;
-                x = scale2(Rr[kp * kp_stride + hidx(sum & 255, (sum >> 8) & 255, sum >> 16)], -e1[k]);
+                const int w = niv[p] + nq_;
+                x = Rr[kp * kp_stride + tab_n[w & 255] + tab_i[(w >> 8) & 255] + (w >> 16)];
+                h = e1[k];
             }
             v[i] = x;
+            sh[i] = h;
             if (++p == q.np) {
                 p = 0;
                 ++kp;
             }
         }
     };
+    // exponent pass: the exponent field of x 2^-e1 is that of x less e1 (zeros stay zero)
     int mx = 0;
     for (int kb = 0; kb < s.nkb1; ++kb) {
         double v[8];
-        group(SPLIT_KB * kb + c8, v);
+        int sh[8];
+        group(SPLIT_KB * kb + c8, v, sh);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) mx = max(mx, exp_field(v[i]));
+        for (int i = 0; i < 8; ++i) {
+            const int ef = exp_field(v[i]);
+            mx = max(mx, ef > 0 ? max(ef - sh[i], 0) : 0);
+        }
     }
     mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
     mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
@@ -340,10 +358,11 @@ __global__ void __launch_bounds__(256) split_r_kernel(const DQuartet* __restrict
     __nv_bfloat16* dig = reinterpret_cast<__nv_bfloat16*>(ws + s.a1_dig);
     for (int kb = 0; kb < s.nkb1; ++kb) {
         double v[8];
-        group(SPLIT_KB * kb + c8, v);
+        int sh[8];
+        group(SPLIT_KB * kb + c8, v, sh);
         long long qv[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) qv[i] = mx > 0 ? fixed_of(v[i], e) : 0ll;
+        for (int i = 0; i < 8; ++i) qv[i] = mx > 0 ? fixed_of(scale2(v[i], -sh[i]), e) : 0ll;
         store_digit_group(dig, row, SPLIT_KB * kb + c8, SPLIT_TA, s.nkb1, qv);
     }
     if ((lane & 3) == 0) reinterpret_cast<int*>(ws + s.a1_exp)[row] = e;
@@ -673,6 +692,12 @@ cudaError_t launch_balance(const BalanceDesc* descs, const WorkItem* items, int 
 cudaError_t init_split_kernels(const int* host_tuv) {
     cudaError_t e = cudaMemcpyToSymbol(g_tuv_split, host_tuv, sizeof(int) * NHERM_TOT);
     if (e != cudaSuccess) return e;
+    std::vector<int> niv(NHERM_TOT);
+    for (int k = 0; k < NHERM_TOT; ++k) {
+        const int t = host_tuv[k] & 255, u = (host_tuv[k] >> 8) & 255, v = host_tuv[k] >> 16;
+        niv[k] = (t + u + v) | ((u + v) << 8) | (v << 16);
+    }
+    if ((e = cudaMemcpyToSymbol(g_niv_split, niv.data(), sizeof(int) * NHERM_TOT)) != cudaSuccess) return e;
     return cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
 }
 
