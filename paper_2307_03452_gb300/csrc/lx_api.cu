@@ -206,14 +206,14 @@ size_t quartet_bytes(const lx_shell* sh, const lx_quartet& q, int flags) {
         const int ra1 = split_rowpad(k2, SPLIT_TA), rb1 = split_rowpad((int)nab, SPLIT_TB);
         const int ra2 = split_rowpad((int)nab, SPLIT_TA), rb2 = split_rowpad((int)ncd, SPLIT_TB);
         const int c1 = (k1 + 127) / 128, c2 = (k2 + 127) / 128;
-        items += ra1 + rb1 + ra2 + rb2 + 3 * c1 + 3 * c2;
+        items += ra1 + rb1 + ra2 + rb2 + c1 + c2;
         items += (ra1 / SPLIT_TA) * ((nab + SPLIT_TB - 1) / SPLIT_TB);
         items += (ra2 / SPLIT_TA) * ((ncd + SPLIT_TB - 1) / SPLIT_TB);
         bytes += sizeof(SplitQuartet) + 2 * sizeof(SplitGemmDesc) + 3 * sizeof(SplitRowsDesc) +
-                 3 * sizeof(ColMaxDesc) + 2 * sizeof(BalanceDesc);
+                 2 * sizeof(ColMaxDesc);
         bytes += (size_t)split_dig_bytes(k2, k1, SPLIT_TA) + (size_t)split_dig_bytes((int)nab, k1, SPLIT_TB);
         bytes += (size_t)split_dig_bytes((int)nab, k2, SPLIT_TA) + (size_t)split_dig_bytes((int)ncd, k2, SPLIT_TB);
-        bytes += 4 * (size_t)(ra1 + rb1 + ra2 + rb2) + 4 * (size_t)(3 * k1 + 3 * k2) + 14 * 256;
+        bytes += 4 * (size_t)(ra1 + rb1 + ra2 + rb2) + 4 * (size_t)(k1 + k2) + 12 * 256;
     }
     return bytes + items * sizeof(WorkItem);
 }
@@ -277,18 +277,14 @@ struct ChunkPlan {
     size_t off_pairs = 0, off_quartets = 0, off_h = 0, off_br = 0, off_g1 = 0, off_g2 = 0, off_data = 0;
     int g1_counts[GEMM_NVARIANT] = {0, 0, 0, 0}, g2_counts[GEMM_NVARIANT] = {0, 0, 0, 0};
     size_t off_counters = 0;  // 2 x GEMM_NVARIANT work counters, uploaded as zeros with the blob
-    // split path (per quartet: 3 split-row descs B1, A2, B2; 3 column-max descs cmh1, cmh2, cmx;
-    // 2 balance descs e1, e2)
+    // split path (per quartet: 3 split-row descs B1, A2, B2; 2 column-scale descs c1, c2)
     std::vector<SplitRowsDesc> srd;
     std::vector<ColMaxDesc> cmd;
-    std::vector<BalanceDesc> bal;
     std::vector<SplitQuartet> sq;
     std::vector<SplitGemmDesc> sg1, sg2;
-    std::vector<WorkItem> items_cA, items_rm, items_b1, items_sr, items_sB, items_sg1, items_cC, items_b2, items_sD,
-        items_sg2;
-    size_t off_srd = 0, off_cmd = 0, off_bal = 0, off_sq = 0, off_sg1 = 0, off_sg2 = 0;
-    size_t off_icA = 0, off_irm = 0, off_ib1 = 0, off_isr = 0, off_isB = 0, off_isg1 = 0, off_icC = 0, off_ib2 = 0,
-           off_isD = 0, off_isg2 = 0;
+    std::vector<WorkItem> items_cA, items_sr, items_sB, items_sg1, items_sD, items_sg2;
+    size_t off_srd = 0, off_cmd = 0, off_sq = 0, off_sg1 = 0, off_sg2 = 0;
+    size_t off_icA = 0, off_isr = 0, off_isB = 0, off_isg1 = 0, off_isD = 0, off_isg2 = 0;
     size_t total = 0;         // bytes from the chunk base
     std::vector<char> blob;   // descriptor bytes [0, off_data)
 };
@@ -305,12 +301,10 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     P.items_g2.clear();
     P.srd.clear();
     P.cmd.clear();
-    P.bal.clear();
     P.sq.clear();
     P.sg1.clear();
     P.sg2.clear();
-    for (auto* v : {&P.items_cA, &P.items_rm, &P.items_b1, &P.items_sr, &P.items_sB, &P.items_sg1, &P.items_cC,
-                    &P.items_b2, &P.items_sD, &P.items_sg2})
+    for (auto* v : {&P.items_cA, &P.items_sr, &P.items_sB, &P.items_sg1, &P.items_sD, &P.items_sg2})
         v->clear();
     std::unordered_map<PairKey, int, PairKeyHash> pid;
     auto get_pair = [&](int sa, int sb, int side) {
@@ -412,26 +406,15 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             P.sq.push_back(q);
             const int sb1 = (int)P.srd.size();
             const int tb1 = split_tb(d.nab), tb2 = split_tb(d.ncd);
-            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k1, d.nab, k1, tb1, q.nkb1, +1});   // B1: H_bra
-            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k2, d.nab, k2, SPLIT_TA, q.nkb2, +1});   // A2: X
-            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k2, d.ncd, k2, tb2, q.nkb2, -1});   // B2: H_ket
+            // H_bra and H_ket columns scaled into (-1, 1): one pass, e = 0 per row
+            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k1, d.nab, k1, tb1, q.nkb1, -1, 1, 0});        // B1: H_bra
+            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k2, d.nab, k2, SPLIT_TA, q.nkb2, +1, 0, 0});   // A2: X
+            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k2, d.ncd, k2, tb2, q.nkb2, -1, 1, 0});        // B2: H_ket
             const int c0 = (int)P.cmd.size();
-            P.cmd.push_back(ColMaxDesc{0, 0, k1, d.nab, k1, 0});  // cmh1
-            P.cmd.push_back(ColMaxDesc{0, 0, k2, d.ncd, k2, 0});  // cmh2
-            P.cmd.push_back(ColMaxDesc{0, 0, k2, d.nab, k2, 0});  // cmx
-            const int b0 = (int)P.bal.size();
-            P.bal.push_back(BalanceDesc{0, 0, 0, k1, 0});  // e1 = (rmr - cmh1) / 2
-            P.bal.push_back(BalanceDesc{0, 0, 0, k2, 0});  // e2 = (cmh2 - cmx) / 2
-            for (int c = 0; c < c1; ++c) {
-                P.items_cA.push_back({c0, c, 0, 0});
-                P.items_rm.push_back({i, c, 0, 0});
-                P.items_b1.push_back({b0, c, 0, 0});
-            }
-            for (int c = 0; c < c2; ++c) {
-                P.items_cA.push_back({c0 + 1, c, 0, 0});
-                P.items_cC.push_back({c0 + 2, c, 0, 0});
-                P.items_b2.push_back({b0 + 1, c, 0, 0});
-            }
+            P.cmd.push_back(ColMaxDesc{0, 0, k1, d.nab, k1, 0});  // c1: column scales of H_bra
+            P.cmd.push_back(ColMaxDesc{0, 0, k2, d.ncd, k2, 0});  // c2: column scales of H_ket
+            for (int c = 0; c < c1; ++c) P.items_cA.push_back({c0, c, 0, 0});
+            for (int c = 0; c < c2; ++c) P.items_cA.push_back({c0 + 1, c, 0, 0});
             // digit kernels: one item per 8 consecutive rows (every row tile is a multiple of 8)
             for (int row = 0; row < split_rowpad(k2, SPLIT_TA); row += 8) P.items_sr.push_back({i, row, 0, 0});
             for (int row = 0; row < split_rowpad(d.nab, tb1); row += 8) P.items_sB.push_back({sb1, row, 0, 0});
@@ -465,18 +448,14 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     region(P.off_counters, sizeof(int) * 2 * GEMM_NVARIANT);
     region(P.off_srd, sizeof(SplitRowsDesc) * P.srd.size());
     region(P.off_cmd, sizeof(ColMaxDesc) * P.cmd.size());
-    region(P.off_bal, sizeof(BalanceDesc) * P.bal.size());
     region(P.off_sq, sizeof(SplitQuartet) * P.sq.size());
     region(P.off_sg1, sizeof(SplitGemmDesc) * P.sq.size());
     region(P.off_sg2, sizeof(SplitGemmDesc) * P.sq.size());
     region(P.off_icA, sizeof(WorkItem) * P.items_cA.size());
-    region(P.off_irm, sizeof(WorkItem) * P.items_rm.size());
-    region(P.off_ib1, sizeof(WorkItem) * P.items_b1.size());
     region(P.off_isr, sizeof(WorkItem) * P.items_sr.size());
     region(P.off_isB, sizeof(WorkItem) * P.items_sB.size());
     region(P.off_isg1, sizeof(WorkItem) * P.items_sg1.size());
-    region(P.off_icC, sizeof(WorkItem) * P.items_cC.size());
-    region(P.off_ib2, sizeof(WorkItem) * P.items_b2.size());
+
     region(P.off_isD, sizeof(WorkItem) * P.items_sD.size());
     region(P.off_isg2, sizeof(WorkItem) * P.items_sg2.size());
     P.off_data = o;
@@ -508,39 +487,27 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             q.a2_exp = take_bytes(4 * (int64_t)split_rowpad(d.nab, SPLIT_TA));
             q.b2_dig = take_bytes(split_dig_bytes(d.ncd, k2, split_tb(d.ncd)));
             q.b2_exp = take_bytes(4 * (int64_t)split_rowpad(d.ncd, split_tb(d.ncd)));
-            q.rmr_off = take_bytes(4 * (int64_t)k1);
-            q.e1_off = take_bytes(4 * (int64_t)k1);
-            q.e2_off = take_bytes(4 * (int64_t)k2);
-            const int64_t cmh1 = take_bytes(4 * (int64_t)k1), cmh2 = take_bytes(4 * (int64_t)k2),
-                          cmx = take_bytes(4 * (int64_t)k2);
+            q.c1_off = take_bytes(4 * (int64_t)k1);
+            q.c2_off = take_bytes(4 * (int64_t)k2);
             const DPair &pb = P.pairs[d.pb], &pk = P.pairs[d.pk];
             SplitRowsDesc* r = &P.srd[3 * i];
             r[0].src_off = pb.h_off;
             r[0].dig_off = q.b1_dig;
             r[0].exp_off = q.b1_exp;
-            r[0].shift_off = q.e1_off;
+            r[0].shift_off = q.c1_off;
             r[1].src_off = d.x_off;
             r[1].dig_off = q.a2_dig;
             r[1].exp_off = q.a2_exp;
-            r[1].shift_off = q.e2_off;
+            r[1].shift_off = q.c2_off;
             r[2].src_off = pk.h_off;
             r[2].dig_off = q.b2_dig;
             r[2].exp_off = q.b2_exp;
-            r[2].shift_off = q.e2_off;
-            ColMaxDesc* c = &P.cmd[3 * i];
+            r[2].shift_off = q.c2_off;
+            ColMaxDesc* c = &P.cmd[2 * i];
             c[0].src_off = pb.h_off;
-            c[0].out_off = cmh1;
+            c[0].out_off = q.c1_off;
             c[1].src_off = pk.h_off;
-            c[1].out_off = cmh2;
-            c[2].src_off = d.x_off;
-            c[2].out_off = cmx;
-            BalanceDesc* b = &P.bal[2 * i];
-            b[0].a_off = q.rmr_off;
-            b[0].b_off = cmh1;
-            b[0].out_off = q.e1_off;
-            b[1].a_off = cmh2;
-            b[1].b_off = cmx;
-            b[1].out_off = q.e2_off;
+            c[1].out_off = q.c2_off;
             SplitGemmDesc g1{};
             g1.a_dig = q.a1_dig;
             g1.a_exp = q.a1_exp;
@@ -582,18 +549,14 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     put(P.off_g2, P.items_g2.data(), sizeof(WorkItem) * P.items_g2.size());
     put(P.off_srd, P.srd.data(), sizeof(SplitRowsDesc) * P.srd.size());
     put(P.off_cmd, P.cmd.data(), sizeof(ColMaxDesc) * P.cmd.size());
-    put(P.off_bal, P.bal.data(), sizeof(BalanceDesc) * P.bal.size());
     put(P.off_sq, P.sq.data(), sizeof(SplitQuartet) * P.sq.size());
     put(P.off_sg1, P.sg1.data(), sizeof(SplitGemmDesc) * P.sg1.size());
     put(P.off_sg2, P.sg2.data(), sizeof(SplitGemmDesc) * P.sg2.size());
     put(P.off_icA, P.items_cA.data(), sizeof(WorkItem) * P.items_cA.size());
-    put(P.off_irm, P.items_rm.data(), sizeof(WorkItem) * P.items_rm.size());
-    put(P.off_ib1, P.items_b1.data(), sizeof(WorkItem) * P.items_b1.size());
     put(P.off_isr, P.items_sr.data(), sizeof(WorkItem) * P.items_sr.size());
     put(P.off_isB, P.items_sB.data(), sizeof(WorkItem) * P.items_sB.size());
     put(P.off_isg1, P.items_sg1.data(), sizeof(WorkItem) * P.items_sg1.size());
-    put(P.off_icC, P.items_cC.data(), sizeof(WorkItem) * P.items_cC.size());
-    put(P.off_ib2, P.items_b2.data(), sizeof(WorkItem) * P.items_b2.size());
+
     put(P.off_isD, P.items_sD.data(), sizeof(WorkItem) * P.items_sD.size());
     put(P.off_isg2, P.items_sg2.data(), sizeof(WorkItem) * P.items_sg2.size());
 }
@@ -712,34 +675,29 @@ int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector
             auto at = [&](size_t off) { return base + off; };
             const SplitRowsDesc* d_srd = reinterpret_cast<const SplitRowsDesc*>(at(P.off_srd));
             const ColMaxDesc* d_cmd = reinterpret_cast<const ColMaxDesc*>(at(P.off_cmd));
-            const BalanceDesc* d_bal = reinterpret_cast<const BalanceDesc*>(at(P.off_bal));
             const SplitQuartet* d_sq = reinterpret_cast<const SplitQuartet*>(at(P.off_sq));
             const SplitGemmDesc* d_sg1 = reinterpret_cast<const SplitGemmDesc*>(at(P.off_sg1));
             const SplitGemmDesc* d_sg2 = reinterpret_cast<const SplitGemmDesc*>(at(P.off_sg2));
             auto items = [&](size_t off) { return reinterpret_cast<const WorkItem*>(at(off)); };
-            // operands of GEMM1: balance exponents, then digit planes of [p|q]^T and H_bra
+            // operands of GEMM1: column scales of H_bra and H_ket, then digit planes of [p|q]^T
+            // and H_bra
             if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
             if ((e = launch_colmax(d_cmd, items(P.off_icA), (int)P.items_cA.size(), ws, wsb, st)) != cudaSuccess ||
-                (e = launch_rowmax_r(d_q, d_sq, items(P.off_irm), (int)P.items_rm.size(), ws, wsb, st)) !=
-                    cudaSuccess ||
-                (e = launch_balance(d_bal, items(P.off_ib1), (int)P.items_b1.size(), wsb, st)) != cudaSuccess ||
                 (e = launch_split_r(d_q, d_sq, items(P.off_isr), (int)P.items_sr.size(), ws, wsb, st)) !=
                     cudaSuccess ||
                 (e = launch_split_rows(d_srd, items(P.off_isB), (int)P.items_sB.size(), ws, wsb, st)) != cudaSuccess)
                 return cuda_fail(e);
-            if ((e = tm.end(LX_STAGE_SPLIT, 5)) != cudaSuccess) return cuda_fail(e);
+            if ((e = tm.end(LX_STAGE_SPLIT, 3)) != cudaSuccess) return cuda_fail(e);
             if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
             if ((e = launch_split_gemm(d_sg1, items(P.off_isg1), (int)P.items_sg1.size(), wsb, ws, status, st)) !=
                 cudaSuccess)
                 return cuda_fail(e);
             if ((e = tm.end(LX_STAGE_GEMM1, 1)) != cudaSuccess) return cuda_fail(e);
-            // operands of GEMM2: balance exponents, digit planes of [ab|q] and H_ket
+            // operands of GEMM2: digit planes of [ab|q] and H_ket
             if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
-            if ((e = launch_colmax(d_cmd, items(P.off_icC), (int)P.items_cC.size(), ws, wsb, st)) != cudaSuccess ||
-                (e = launch_balance(d_bal, items(P.off_ib2), (int)P.items_b2.size(), wsb, st)) != cudaSuccess ||
-                (e = launch_split_rows(d_srd, items(P.off_isD), (int)P.items_sD.size(), ws, wsb, st)) != cudaSuccess)
+            if ((e = launch_split_rows(d_srd, items(P.off_isD), (int)P.items_sD.size(), ws, wsb, st)) != cudaSuccess)
                 return cuda_fail(e);
-            if ((e = tm.end(LX_STAGE_SPLIT, 3)) != cudaSuccess) return cuda_fail(e);
+            if ((e = tm.end(LX_STAGE_SPLIT, 1)) != cudaSuccess) return cuda_fail(e);
             if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
             if ((e = launch_split_gemm(d_sg2, items(P.off_isg2), (int)P.items_sg2.size(), wsb, out, status, st)) !=
                 cudaSuccess)
@@ -1222,8 +1180,8 @@ int lx_split_gemm(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda,
     const int tb = split_tb(N);
     const int ra = split_rowpad(M, SPLIT_TA), rb = split_rowpad(N, tb);
     std::vector<SplitRowsDesc> rd(2);
-    rd[0] = SplitRowsDesc{0, 0, 0, -1, lda, M, K, SPLIT_TA, nkb, 0};
-    rd[1] = SplitRowsDesc{0, 0, 0, -1, ldb, N, K, tb, nkb, 0};
+    rd[0] = SplitRowsDesc{0, 0, 0, -1, lda, M, K, SPLIT_TA, nkb, 0, 0, 0};
+    rd[1] = SplitRowsDesc{0, 0, 0, -1, ldb, N, K, tb, nkb, 0, 0, 0};
     std::vector<WorkItem> ia, ib, ig;
     for (int r = 0; r < ra; r += 8) ia.push_back({0, r, 0, 0});
     for (int r = 0; r < rb; r += 8) ib.push_back({1, r, 0, 0});

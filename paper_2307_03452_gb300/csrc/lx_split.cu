@@ -16,7 +16,7 @@
 // Kernels:
 //   split_rows_kernel  FP64 row-major matrix rows -> digit planes + row exponents
 //   split_r_kernel     rows q of the [p|q] operand gathered from [r]^(0) -> digit planes
-//   colmax_kernel, rowmax_r_kernel, balance_kernel: the power-of-two balance along K
+//   colmax_kernel      column scales of the H matrices (powers of two along K)
 //   split_gemm_kernel  D = A B^T on tcgen05 (M tile 128, N tile <= 32, K blocks of 32),
 //                      persistent, operand blocks streamed by bulk TMA copies into a
 //                      3-stage mbarrier ring, one thread issuing the MMAs, two TMEM
@@ -33,7 +33,6 @@ namespace {
 
 constexpr unsigned long long WAIT_LIMIT = 1ull << 24;  // bounded spin: then flag and bail out
 
-__device__ int g_tuv_split[NHERM_TOT];
 
 __device__ inline void set_status(unsigned* st, unsigned bit) { atomicOr(st, bit); }
 
@@ -233,21 +232,24 @@ __device__ inline int row_max16(int mx) {
 }
 
 // Split 8 rows (4 pairs) through value(row, k0, v[8]) (zeros outside the matrix): digit planes
-// of row tile T with nkb K blocks, one int exponent per row.
+// of row tile T with nkb K blocks, one int exponent per row.  fixed: every value lies in
+// (-1, 1) and every row takes e = 0, so the exponent pass is skipped.
 template <typename Value>
-__device__ __forceinline__ void split_8rows(int r0, int nkb, int T, __nv_bfloat16* __restrict__ dig,
+__device__ __forceinline__ void split_8rows(int r0, int nkb, int T, bool fixed, __nv_bfloat16* __restrict__ dig,
                                             int* __restrict__ exps, Value value) {
     const int lane = threadIdx.x & 31, c8 = 8 * (lane & 15);
     for (int pr = 0; pr < 4; ++pr) {
         const int row = r0 + 2 * pr + (lane >> 4);
-        int mx = 0;
-        for (int k0 = c8; k0 < nkb * SPLIT_KB; k0 += 128) {
-            double v[8];
-            value(row, k0, v);
+        int mx = fixed ? 1022 : 0;  // 1022: the exponent field bound of values in (-1, 1)
+        if (!fixed) {
+            for (int k0 = c8; k0 < nkb * SPLIT_KB; k0 += 128) {
+                double v[8];
+                value(row, k0, v);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) mx = max(mx, exp_field(v[i]));
+                for (int i = 0; i < 8; ++i) mx = max(mx, exp_field(v[i]));
+            }
+            mx = row_max16(mx);
         }
-        mx = row_max16(mx);
         const int e = mx > 0 ? mx - 1022 : 0;  // |x| < 2^e over the row
         for (int k0 = c8; k0 < nkb * SPLIT_KB; k0 += 128) {
             double v[8];
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const SplitRowsDesc* __
     const SplitRowsDesc d = descs[it.q];
     const double* src = src_base + d.src_off;
     const int* shift = d.shift_off >= 0 ? reinterpret_cast<const int*>(ws + d.shift_off) : nullptr;
-    split_8rows(it.a, d.nkb, d.T, reinterpret_cast<__nv_bfloat16*>(ws + d.dig_off),
+    split_8rows(it.a, d.nkb, d.T, d.fixed != 0, reinterpret_cast<__nv_bfloat16*>(ws + d.dig_off),
                 reinterpret_cast<int*>(ws + d.exp_off), [&](int row, int k0, double (&v)[8]) {
                     const bool live = row < d.rows;
                     const double* sr = src + (int64_t)row * d.ld;
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const SplitRowsDesc* __
 }
 
 // Rows q of the GEMM1 A operand: A[q][k] = [p+q]^(0) of primitive quartet (kp, kq) with
-// k = kp*Np + p, q = kq*Nq + qq, scaled by 2^-e1[k].  item.q = quartet, item.a = r0.  Here
+// k = kp*Np + p, q = kq*Nq + qq, scaled by 2^c1[k].  item.q = quartet, item.a = r0.  Here
 // the 8 rows are processed at once: lane (rr, c) = (lane / 4, lane % 4) handles row r0 + rr
 // and columns 8c .. 8c+7 of every K block, so the gathers of neighbouring rows (neighbouring
 // Hermite indices) fall close together; the rows are gathered twice, once for the exponent.
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(256) split_r_kernel(const DQuartet* __restrict
     }
     const double* Rr = wsd + q.rr_off + (int64_t)kq * q.nr;
     const int64_t kp_stride = (int64_t)q.kket * q.nr;
-    const int* e1 = reinterpret_cast<const int*>(ws + s.e1_off);
+    const int* c1 = reinterpret_cast<const int*>(ws + s.c1_off);
     // [p+q]^(0) of columns k0 .. k0+7 (unscaled) and their shifts, walking (kp, p)
     auto group = [&](int k0, double (&v)[8], int (&sh)[8]) {
         int k = k0;
@@ -330,7 +332,7 @@ __global__ void __launch_bounds__(256) split_r_kernel(const DQuartet* __restrict
             if (live && k < K) {
                 const int w = niv[p] + nq_;
                 x = Rr[kp * kp_stride + tab_n[w & 255] + tab_i[(w >> 8) & 255] + (w >> 16)];
-                h = e1[k];
+                h = c1[k];
             }
             v[i] = x;
             sh[i] = h;
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(256) split_r_kernel(const DQuartet* __restrict
             }
         }
     };
-    // exponent pass: the exponent field of x 2^-e1 is that of x less e1 (zeros stay zero)
+    // exponent pass: the exponent field of x 2^c1 is that of x plus c1 (zeros stay zero)
     int mx = 0;
     for (int kb = 0; kb < s.nkb1; ++kb) {
         double v[8];
@@ -349,7 +351,7 @@ __global__ void __launch_bounds__(256) split_r_kernel(const DQuartet* __restrict
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int ef = exp_field(v[i]);
-            mx = max(mx, ef > 0 ? max(ef - sh[i], 0) : 0);
+            mx = max(mx, ef > 0 ? min(max(ef + sh[i], 0), 2047) : 0);
         }
     }
     mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
@@ -362,13 +364,14 @@ __global__ void __launch_bounds__(256) split_r_kernel(const DQuartet* __restrict
         group(SPLIT_KB * kb + c8, v, sh);
         long long qv[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) qv[i] = mx > 0 ? fixed_of(scale2(v[i], -sh[i]), e) : 0ll;
+        for (int i = 0; i < 8; ++i) qv[i] = mx > 0 ? fixed_of(scale2(v[i], sh[i]), e) : 0ll;
         store_digit_group(dig, row, SPLIT_KB * kb + c8, SPLIT_TA, s.nkb1, qv);
     }
     if ((lane & 3) == 0) reinterpret_cast<int*>(ws + s.a1_exp)[row] = e;
 }
 
-// One thread per column k: largest exponent field over the rows.  item = (desc, chunk).
+// One thread per column k: c_k with |x| < 2^c_k over the column (from the largest exponent
+// field; 0 for a column of zeros).  item = (desc, chunk of 128 columns).
 __global__ void colmax_kernel(const ColMaxDesc* __restrict__ descs, const WorkItem* __restrict__ items,
                               const double* __restrict__ src_base, char* __restrict__ ws) {
     const WorkItem it = items[blockIdx.x];
@@ -378,37 +381,7 @@ __global__ void colmax_kernel(const ColMaxDesc* __restrict__ descs, const WorkIt
     const double* src = src_base + d.src_off + k;
     int mx = 0;
     for (int r = 0; r < d.rows; ++r) mx = max(mx, exp_field(src[(int64_t)r * d.ld]));
-    reinterpret_cast<int*>(ws + d.out_off)[k] = mx;
-}
-
-// One thread per row k = kp*Np + p of [p|q]: largest exponent field over q = kq*Nq + qq.
-__global__ void rowmax_r_kernel(const DQuartet* __restrict__ qd, const SplitQuartet* __restrict__ sq,
-                                const WorkItem* __restrict__ items, const double* __restrict__ wsd,
-                                char* __restrict__ ws) {
-    const WorkItem it = items[blockIdx.x];
-    const DQuartet q = qd[it.q];
-    const int k = it.a * 128 + threadIdx.x;
-    if (k >= q.kbra * q.np) return;
-    const int kp = k / q.np, tp = g_tuv_split[k - kp * q.np];
-    int mx = 0;
-    for (int kq = 0; kq < q.kket; ++kq) {
-        const double* Rr = wsd + q.rr_off + (int64_t)(kp * q.kket + kq) * q.nr;
-        for (int qq = 0; qq < q.nq; ++qq) {
-            const int sum = tp + g_tuv_split[qq];
-            mx = max(mx, exp_field(Rr[hidx(sum & 255, (sum >> 8) & 255, sum >> 16)]));
-        }
-    }
-    reinterpret_cast<int*>(ws + sq[it.q].rmr_off)[k] = mx;
-}
-
-__global__ void balance_kernel(const BalanceDesc* __restrict__ descs, const WorkItem* __restrict__ items,
-                               char* __restrict__ ws) {
-    const WorkItem it = items[blockIdx.x];
-    const BalanceDesc d = descs[it.q];
-    const int k = it.a * 128 + threadIdx.x;
-    if (k >= d.K) return;
-    const int a = reinterpret_cast<const int*>(ws + d.a_off)[k], b = reinterpret_cast<const int*>(ws + d.b_off)[k];
-    reinterpret_cast<int*>(ws + d.out_off)[k] = (a > 0 && b > 0) ? ((a - b) >> 1) : 0;
+    reinterpret_cast<int*>(ws + d.out_off)[k] = mx > 0 ? mx - 1022 : 0;
 }
 
 // ------------------------------------------------------------------ tcgen05 GEMM
@@ -676,22 +649,8 @@ cudaError_t launch_colmax(const ColMaxDesc* descs, const WorkItem* items, int ni
     return cudaGetLastError();
 }
 
-cudaError_t launch_rowmax_r(const DQuartet* qd, const SplitQuartet* sq, const WorkItem* items, int nitems,
-                            const double* wsd, char* ws, cudaStream_t st) {
-    if (nitems <= 0) return cudaSuccess;
-    rowmax_r_kernel<<<nitems, 128, 0, st>>>(qd, sq, items, wsd, ws);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_balance(const BalanceDesc* descs, const WorkItem* items, int nitems, char* ws, cudaStream_t st) {
-    if (nitems <= 0) return cudaSuccess;
-    balance_kernel<<<nitems, 128, 0, st>>>(descs, items, ws);
-    return cudaGetLastError();
-}
-
 cudaError_t init_split_kernels(const int* host_tuv) {
-    cudaError_t e = cudaMemcpyToSymbol(g_tuv_split, host_tuv, sizeof(int) * NHERM_TOT);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
     std::vector<int> niv(NHERM_TOT);
     for (int k = 0; k < NHERM_TOT; ++k) {
         const int t = host_tuv[k] & 255, u = (host_tuv[k] >> 8) & 255, v = host_tuv[k] >> 16;

@@ -18,36 +18,33 @@ constexpr int SPLIT_SEG_KB = 4;                      // K blocks accumulated in 
 
 // One matrix whose rows are split: src at (double*)base + src_off, row stride ld.  Before
 // splitting, column k is multiplied by 2^(shift_sign * shift[k]) (exact; shift_off < 0: none).
+// fixed = 0: each row gets its own power of two (|x| < 2^e over the row); fixed = 1: the
+// scaled values are known to lie in (-1, 1) and every row takes e = 0 (one pass, no maximum).
 struct SplitRowsDesc {
     int64_t src_off;    // doubles
     int64_t dig_off;    // bytes from the workspace base
     int64_t exp_off;    // bytes from the workspace base (int per padded row)
     int64_t shift_off;  // bytes from the workspace base (int per column), or -1
-    int ld, rows, K, T, nkb, shift_sign;
+    int ld, rows, K, T, nkb, shift_sign, fixed, pad;
 };
 
-// out[k] = largest FP64 exponent field in column k of a row-major matrix (0: column of zeros).
+// out[k] = c_k with |x| < 2^c_k over column k of a row-major matrix (0 for a zero column):
+// the column scale of an H matrix.
 struct ColMaxDesc {
     int64_t src_off;  // doubles
     int64_t out_off;  // bytes (int per column)
     int ld, rows, K, pad;
 };
 
-// out[k] = floor((a[k] - b[k]) / 2) when both are nonzero, else 0: the power of two that
-// balances column k of one operand against row k of the other.
-struct BalanceDesc {
-    int64_t a_off, b_off, out_off;  // bytes (int arrays)
-    int K, pad;
-};
-
-// Per-quartet split operands of the two GEMMs.
+// Per-quartet split operands of the two GEMMs.  Column k of H_bra is scaled by 2^-c1[k] into
+// (-1, 1) and column k of [p|q]^T by 2^c1[k] (the product is unchanged); likewise H_ket and
+// [ab|q] with c2.
 struct SplitQuartet {
-    int64_t a1_dig, a1_exp;  // [p|q]^T rows (Kket Nq), K = Kbra Np, columns scaled by 2^-e1
-    int64_t b1_dig, b1_exp;  // H_bra rows (nab), columns scaled by 2^e1
-    int64_t a2_dig, a2_exp;  // [ab|q] rows (nab), K = Kket Nq, columns scaled by 2^e2
-    int64_t b2_dig, b2_exp;  // H_ket rows (ncd), columns scaled by 2^-e2
-    int64_t rmr_off;         // int[Kbra Np]: row-max exponents of [p|q]
-    int64_t e1_off, e2_off;  // int[Kbra Np], int[Kket Nq]
+    int64_t a1_dig, a1_exp;  // [p|q]^T rows (Kket Nq), K = Kbra Np, columns scaled by 2^c1
+    int64_t b1_dig, b1_exp;  // H_bra rows (nab), columns scaled by 2^-c1
+    int64_t a2_dig, a2_exp;  // [ab|q] rows (nab), K = Kket Nq, columns scaled by 2^c2
+    int64_t b2_dig, b2_exp;  // H_ket rows (ncd), columns scaled by 2^-c2
+    int64_t c1_off, c2_off;  // int[Kbra Np], int[Kket Nq]
     int nkb1, nkb2;
 };
 
@@ -83,11 +80,6 @@ cudaError_t launch_split_r(const DQuartet* qd, const SplitQuartet* sq, const Wor
 // item = (desc, chunk of 128 columns)
 cudaError_t launch_colmax(const ColMaxDesc* descs, const WorkItem* items, int nitems, const double* src_base,
                           char* ws, cudaStream_t st);
-// item = (quartet, chunk of 128 rows of [p|q])
-cudaError_t launch_rowmax_r(const DQuartet* qd, const SplitQuartet* sq, const WorkItem* items, int nitems,
-                            const double* wsd, char* ws, cudaStream_t st);
-// item = (desc, chunk of 128 entries)
-cudaError_t launch_balance(const BalanceDesc* descs, const WorkItem* items, int nitems, char* ws, cudaStream_t st);
 cudaError_t launch_split_gemm(const SplitGemmDesc* probs, const WorkItem* items, int nitems, const char* ws,
                               double* cbase, unsigned* status, cudaStream_t st);
 
