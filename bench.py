@@ -359,8 +359,9 @@ def main(argv=None):
                  "max_abs_diff_vs_fp64_path": maxdiff, "speedup_vs_fp64_path": (total_ms / stot),
                  "stage_ms_per_step": {k: v / args.steps for k, v in sstage.items()},
                  "gpu_launches": int(sum(slaunch.values())), "roofline": sroof,
-                 "scheme": "6 BF16 digits of 8 bits per FP64 value, per-row powers of two, power-of-two "
-                           "balancing along the reduction index, 21 digit products, int64 recombination"}
+                 "scheme": "6 BF16 digits of 8 bits per FP64 value, per-row powers of two, H columns scaled "
+                           "into (-1, 1) by powers of two folded into the other operand, 21 digit products, "
+                           "int64 recombination"}
         del wss, outs
         torch.cuda.empty_cache()
 
