@@ -121,8 +121,12 @@ int64_t lx_eri_workspace_min(const lx_shell* shells, int32_t nshell, const lx_qu
  *     holds the per-call descriptors, the H matrices, the [r]^(0) vectors and the
  *     intermediate [ab|q] blocks.  It must not be reused until the stream has passed the work.
  *   cuda_stream: a cudaStream_t of the current device (NULL = legacy default stream).
- * The call validates every input on the host, enqueues the kernels and returns without
- * waiting for them.  Errors found on the device are reported by lx_eri_sync_status.
+ * The call validates every input on the host, plans the batch, copies the planned
+ * descriptors into page-locked staging memory owned by the library (a few buffers per
+ * device, reused once their uploads have completed), enqueues the uploads and the kernels
+ * and returns without waiting for them.  Errors found on the device are reported by
+ * lx_eri_sync_status.  A stream in capture mode is refused (LX_ERR_CUDA): capture a batch
+ * with lx_eri_graph_create.
  */
 int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
                  int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags, double* out,

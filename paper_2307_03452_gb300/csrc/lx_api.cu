@@ -724,6 +724,126 @@ int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector
 
 using namespace lx;
 
+namespace {
+
+// Pinned staging buffers for the descriptor uploads of lx_eri_batch, per device: copies from
+// pageable memory would make every call wait for the stream, so the planned descriptors are
+// copied into a page-locked buffer first.  A buffer is held by one call from stage_acquire to
+// stage_release, then read by that call's uploads until the event recorded after them has
+// completed.  Up to STAGE_POOL buffers are kept per device; when none is free the least
+// recently used one is waited for (more are made only if every buffer is held).
+constexpr int STAGE_POOL = 4;
+struct StageBuf {
+    char* ptr = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    uint64_t stamp = 0;    // order of last use
+    bool held = false;     // between stage_acquire and stage_release
+    bool pending = false;  // uploads enqueued, event not yet seen complete
+};
+std::mutex g_stage_mutex;
+std::vector<StageBuf> g_stage[MAX_DEVICES];
+uint64_t g_stage_clock = 0;
+
+// Hold a pinned buffer of at least `bytes` that no enqueued copy still reads.
+int stage_acquire(int dev, size_t bytes, int& idx, char*& ptr) {
+    std::lock_guard<std::mutex> lock(g_stage_mutex);
+    auto& pool = g_stage[dev];
+    int best = -1, lru = -1;
+    for (int i = 0; i < (int)pool.size(); ++i) {
+        StageBuf& b = pool[i];
+        if (b.held) continue;
+        if (b.pending) {
+            const cudaError_t q = cudaEventQuery(b.done);
+            if (q == cudaSuccess) b.pending = false;
+            else if (q != cudaErrorNotReady) return cuda_fail(q);
+        }
+        if (lru < 0 || b.stamp < pool[lru].stamp) lru = i;
+        if (!b.pending && b.cap >= bytes && (best < 0 || b.cap < pool[best].cap)) best = i;
+    }
+    if (best < 0) {
+        if ((int)pool.size() < STAGE_POOL || lru < 0) {
+            pool.emplace_back();
+            best = (int)pool.size() - 1;
+            cudaError_t e = cudaEventCreateWithFlags(&pool[best].done, cudaEventDisableTiming);
+            if (e != cudaSuccess) {
+                pool.pop_back();
+                return cuda_fail(e);
+            }
+        } else {
+            best = lru;
+        }
+        StageBuf& b = pool[best];
+        if (b.pending) {
+            cudaError_t e = cudaEventSynchronize(b.done);
+            if (e != cudaSuccess) return cuda_fail(e);
+            b.pending = false;
+        }
+        if (b.cap < bytes) {
+            if (b.ptr) {
+                cudaError_t e = cudaFreeHost(b.ptr);
+                if (e != cudaSuccess) return cuda_fail(e);
+                b.ptr = nullptr;
+                b.cap = 0;
+            }
+            const size_t cap = std::max(bytes, (size_t)1 << 20);
+            cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&b.ptr), cap, cudaHostAllocDefault);
+            if (e != cudaSuccess) return cuda_fail(e);
+            b.cap = cap;
+        }
+    }
+    StageBuf& b = pool[best];
+    b.held = true;
+    b.stamp = ++g_stage_clock;
+    idx = best;
+    ptr = b.ptr;
+    return LX_OK;
+}
+
+// Give buffer idx back; its uploads (if any were enqueued) end at an event recorded on st.
+int stage_release(int dev, int idx, cudaStream_t st, bool enqueued) {
+    std::lock_guard<std::mutex> lock(g_stage_mutex);
+    StageBuf& b = g_stage[dev][idx];
+    b.held = false;
+    if (!enqueued) return LX_OK;
+    cudaError_t e = cudaEventRecord(b.done, st);
+    if (e != cudaSuccess) {
+        // the uploads may still be in flight: wait for the stream before the buffer is reused
+        cudaStreamSynchronize(st);
+        return cuda_fail(e);
+    }
+    b.pending = true;
+    return LX_OK;
+}
+
+}  // namespace
+
+namespace lx {
+
+// lx_eri_batch without the pinned staging: the descriptors are uploaded straight from the
+// planner's host vectors (the copies then wait for the stream).  Allocates nothing.
+int eri_batch_unstaged(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
+                       int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags, double* out,
+                       void* workspace, size_t workspace_bytes, void* cuda_stream) {
+    int v = validate(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, true);
+    if (v != LX_OK) return v;
+    if (nquartet == 0) return LX_OK;
+    if (!out) return LX_ERR_NULL;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return LX_ERR_WORKSPACE;
+    unsigned* status = nullptr;
+    if ((v = ensure_device(&status)) != LX_OK) return v;
+    PlannedBatch B;
+    if ((v = plan_batch(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, workspace_bytes,
+                        Overrides(), B)) != LX_OK)
+        return v;
+    std::vector<const char*> blobs;
+    for (const auto& P : B.chunks) blobs.push_back(P.blob.data());
+    return enqueue_batch(B, B.head_blob.data(), blobs, out, workspace, status, static_cast<cudaStream_t>(cuda_stream),
+                         (flags & LX_TIME_STAGES) != 0);
+}
+
+}  // namespace lx
+
 extern "C" {
 
 int64_t lx_eri_out_size(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
@@ -766,16 +886,43 @@ int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, con
     if (nquartet == 0) return LX_OK;
     if (!out) return LX_ERR_NULL;
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return LX_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (cap != cudaStreamCaptureStatusNone) {
+        // the staging buffers are reused by later calls, so a captured upload would replay stale
+        // descriptors: capture goes through lx_eri_graph_create, which owns its copies
+        std::snprintf(t_cuda_msg, sizeof(t_cuda_msg), "lx_eri_batch on a capturing stream: use lx_eri_graph_create");
+        return LX_ERR_CUDA;
+    }
     unsigned* status = nullptr;
     if ((v = ensure_device(&status)) != LX_OK) return v;
     PlannedBatch B;
     if ((v = plan_batch(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, workspace_bytes,
                         Overrides(), B)) != LX_OK)
         return v;
+    // descriptors into a pinned staging buffer, so that the uploads do not wait for the stream
+    size_t total = align256(B.head_blob.size());
+    for (const auto& P : B.chunks) total += align256(P.blob.size());
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
+    int idx = -1;
+    char* stage = nullptr;
+    if ((v = stage_acquire(dev, total, idx, stage)) != LX_OK) return v;
+    size_t o = 0;
+    std::memcpy(stage, B.head_blob.data(), B.head_blob.size());
+    const char* head_src = stage;
+    o = align256(B.head_blob.size());
     std::vector<const char*> blobs;
-    for (const auto& P : B.chunks) blobs.push_back(P.blob.data());
-    return enqueue_batch(B, B.head_blob.data(), blobs, out, workspace, status, static_cast<cudaStream_t>(cuda_stream),
-                         (flags & LX_TIME_STAGES) != 0);
+    for (const auto& P : B.chunks) {
+        std::memcpy(stage + o, P.blob.data(), P.blob.size());
+        blobs.push_back(stage + o);
+        o += align256(P.blob.size());
+    }
+    v = enqueue_batch(B, head_src, blobs, out, workspace, status, st, (flags & LX_TIME_STAGES) != 0);
+    const int r = stage_release(dev, idx, st, true);
+    return v != LX_OK ? v : r;
 }
 
 namespace {

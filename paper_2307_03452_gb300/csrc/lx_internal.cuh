@@ -139,6 +139,12 @@ struct FoldPairTab {
     int maxq, maxw;
 };
 
+// lx_eri_batch with the descriptors uploaded from pageable memory, allocating nothing
+// (lx_api.cu; used by lx_eri_batch_static).
+int eri_batch_unstaged(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
+                       int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags, double* out,
+                       void* workspace, size_t workspace_bytes, void* cuda_stream);
+
 // Host-side table generators (lx_tables.cpp).
 void make_boys_table(double* table);        // BOYS_NROW * BOYS_NPT
 void make_solid_coefs(double* coefs);       // packed: l = 0..LMAX, (2l+1) x ncart(l) each

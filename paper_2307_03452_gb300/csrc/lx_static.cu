@@ -46,7 +46,8 @@ extern "C" int lx_eri_batch_static(const lx_shell* shells, int32_t nshell, const
         ptr = g_scratch_ptr[dev];
     }
     // Nothing in the pipeline reads scratch it has not written in the same call, so the
-    // array's leftover contents from an earlier call need no clearing.
-    return lx_eri_batch(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, out, ptr,
-                        (size_t)LX_STATIC_SCRATCH_BYTES, cuda_stream);
+    // array's leftover contents from an earlier call need no clearing.  The descriptors are
+    // uploaded from pageable memory: no pinned staging buffer is allocated for this call.
+    return lx::eri_batch_unstaged(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, out, ptr,
+                                  (size_t)LX_STATIC_SCRATCH_BYTES, cuda_stream);
 }

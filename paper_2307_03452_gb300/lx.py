@@ -191,8 +191,9 @@ class Batch:
         self.out_size = int(n)
 
     def pin(self):
-        """Move the host descriptors into pinned (page-locked) memory, so that the library's
-        uploads are asynchronous DMA copies."""
+        """Keep the input arrays in pinned (page-locked) memory.  The library stages its own
+        uploads in pinned memory, so calls are asynchronous without this; it only keeps the
+        caller's arrays out of pageable memory."""
         import torch
         self._pinned = []
 

@@ -126,3 +126,29 @@ def test_mixed_contracted_batch_against_oracle():
         assert np.abs(got[pos:pos + n] - ref[pos:pos + n]).max() <= 1e-11 * scale[cls]
         pos += n
     g.close()
+
+
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")
+def test_batch_call_refuses_a_capturing_stream():
+    # lx_eri_batch stages its uploads in reused pinned buffers, so it must not be captured;
+    # it says so before touching the stream, and the capture ends cleanly (empty graph)
+    basis, quartets = inputs.uniform_class((2, 1, 2, 0), 3, 131, cube=3.0, exps=(0.2, 5.0))
+    b = lx.Batch(basis, quartets, solid=True)
+    out = torch.empty(max(b.out_size, 1), dtype=torch.float64, device="cuda")
+    ws = lx.alloc_workspace(b.workspace_size())
+    b.run(out, ws)  # device set up outside the capture
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    s.wait_stream(torch.cuda.current_stream())
+    code = None
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        try:
+            b.run(out, ws, stream=s)
+        except lx.LxError as exc:
+            code = exc.code
+        finally:
+            g.capture_end()
+    torch.cuda.synchronize()
+    assert code == -7
