@@ -66,6 +66,12 @@ typedef struct {
                               tensor cores (FP32 accumulation, integer recombination); Boys,
                               [r]^(m), E and H stay FP64.  Operands carry 48 bits; the absolute
                               error grows with the magnitude of a quartet's intermediates */
+#define LX_PATH_ROUTED 0x4 /* per quartet: the routing network set by lx_router_set predicts log10
+                              of the largest |integral|; quartets predicted at or above its
+                              threshold take LX_PATH_FP64, the rest LX_PATH_SPLIT.  lx_eri_batch
+                              then waits for the stream once, to read the predictions back.
+                              Not with LX_PATH_SPLIT; not for lx_eri_graph_create,
+                              lx_eri_autotune or lx_eri_batch_static */
 #define LX_TIME_STAGES 0x200 /* record CUDA events around each stage (see lx_eri_stage_times) */
 
 /* stages timed with LX_TIME_STAGES */
@@ -92,6 +98,7 @@ typedef struct {
 #define LX_ERR_SIZE (-10)         /* a size argument is negative or too large */
 #define LX_ERR_STATIC_SCRATCH (-11) /* lx_eri_batch_static: the batch needs more scratch than
                                        LX_STATIC_SCRATCH_BYTES even one quartet at a time */
+#define LX_ERR_NO_ROUTER (-12)    /* LX_PATH_ROUTED on a device without lx_router_set */
 
 /*
  * Number of doubles the output buffer needs: max over quartets of out_offset + block size.
@@ -277,6 +284,14 @@ int lx_split_gemm(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda,
  */
 int lx_route_features(const lx_shell* shells, int32_t nshell, const double* exps, int32_t nprim_total,
                       const lx_quartet* quartets, int64_t nquartet, float* feat, void* cuda_stream);
+
+/*
+ * The routing network of LX_PATH_ROUTED on the current device: params_f16 holds the
+ * LX_MLP_NPARAM FP16 parameters (HOST memory, layout as above), tau the threshold on the
+ * predicted log10 max |integral| at or above which a quartet takes the FP64 path.  The
+ * parameters are copied (synchronously); a later call replaces them.
+ */
+int lx_router_set(const void* params_f16, float tau);
 
 /* Inference: out[i] = MLP(feat[i]) with FP16 parameters params_f16 (DEVICE, LX_MLP_NPARAM halves). */
 int lx_mlp_forward(const void* params_f16, const float* feat, int64_t n, float* out, void* cuda_stream);

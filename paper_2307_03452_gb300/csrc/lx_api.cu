@@ -121,7 +121,8 @@ int validate(const lx_shell* shells, int32_t nshell, const double* exps, const d
     if (nshell < 0 || nquartet < 0 || nprim_total < 0) return LX_ERR_SIZE;
     if ((nshell > 0 && !shells) || (nquartet > 0 && !quartets)) return LX_ERR_NULL;
     if (need_prims && nprim_total > 0 && (!exps || !coefs)) return LX_ERR_NULL;
-    if (flags & ~(LX_SOLID | LX_PATH_SPLIT | LX_TIME_STAGES)) return LX_ERR_FLAGS;
+    if (flags & ~(LX_SOLID | LX_PATH_SPLIT | LX_PATH_ROUTED | LX_TIME_STAGES)) return LX_ERR_FLAGS;
+    if ((flags & LX_PATH_ROUTED) && (flags & LX_PATH_SPLIT)) return LX_ERR_FLAGS;
     for (int32_t s = 0; s < nshell; ++s) {
         const lx_shell& d = shells[s];
         if (d.l < 0 || d.l > LX_LMAX || d.nprim < 1 || d.nprim > LX_KMAX || d.reserved != 0) return LX_ERR_SHELL;
@@ -844,6 +845,52 @@ int eri_batch_unstaged(const lx_shell* shells, int32_t nshell, const double* exp
 
 }  // namespace lx
 
+namespace {
+
+// Routing network of LX_PATH_ROUTED per device (FP16 parameters on the device, threshold).
+std::mutex g_router_mutex;
+void* g_router_params[MAX_DEVICES];
+float g_router_tau[MAX_DEVICES];
+
+// Workspace the routed call needs before the batches run: features and predictions.
+size_t routed_scratch_bytes(int64_t n) {
+    return align256(sizeof(float) * LX_MLP_NIN * (size_t)n) + align256(sizeof(float) * (size_t)n);
+}
+
+// Plan one batch, stage its descriptors in pinned memory and enqueue it (inputs validated,
+// device set up, stream not capturing).
+int eri_batch_staged(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
+                     int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags, double* out,
+                     void* workspace, size_t workspace_bytes, cudaStream_t st, unsigned* status) {
+    PlannedBatch B;
+    int v = plan_batch(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, workspace_bytes,
+                       Overrides(), B);
+    if (v != LX_OK) return v;
+    // descriptors into a pinned staging buffer, so that the uploads do not wait for the stream
+    size_t total = align256(B.head_blob.size());
+    for (const auto& P : B.chunks) total += align256(P.blob.size());
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int idx = -1;
+    char* stage = nullptr;
+    if ((v = stage_acquire(dev, total, idx, stage)) != LX_OK) return v;
+    std::memcpy(stage, B.head_blob.data(), B.head_blob.size());
+    const char* head_src = stage;
+    size_t o = align256(B.head_blob.size());
+    std::vector<const char*> blobs;
+    for (const auto& P : B.chunks) {
+        std::memcpy(stage + o, P.blob.data(), P.blob.size());
+        blobs.push_back(stage + o);
+        o += align256(P.blob.size());
+    }
+    v = enqueue_batch(B, head_src, blobs, out, workspace, status, st, (flags & LX_TIME_STAGES) != 0);
+    const int r = stage_release(dev, idx, st, true);
+    return v != LX_OK ? v : r;
+}
+
+}  // namespace
+
 extern "C" {
 
 int64_t lx_eri_out_size(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
@@ -864,8 +911,14 @@ int64_t lx_eri_workspace_size(const lx_shell* shells, int32_t nshell, const lx_q
                               int32_t flags) {
     const int v = validate(shells, nshell, nullptr, nullptr, 0, quartets, nquartet, flags, false);
     if (v != LX_OK) return v;
-    return (int64_t)(head_bytes(nshell, (int32_t)prim_count(shells, nshell)) +
-                     chunk_estimate(shells, quartets, 0, nquartet, flags & (LX_SOLID | LX_PATH_SPLIT)));
+    const size_t head = head_bytes(nshell, (int32_t)prim_count(shells, nshell));
+    if (flags & LX_PATH_ROUTED) {
+        // either path may get every quartet; the predictions come first
+        const size_t a = chunk_estimate(shells, quartets, 0, nquartet, flags & LX_SOLID);
+        const size_t b = chunk_estimate(shells, quartets, 0, nquartet, (flags & LX_SOLID) | LX_PATH_SPLIT);
+        return (int64_t)std::max(head + std::max(a, b), routed_scratch_bytes(nquartet));
+    }
+    return (int64_t)(head + chunk_estimate(shells, quartets, 0, nquartet, flags & (LX_SOLID | LX_PATH_SPLIT)));
 }
 
 int64_t lx_eri_workspace_min(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
@@ -873,9 +926,11 @@ int64_t lx_eri_workspace_min(const lx_shell* shells, int32_t nshell, const lx_qu
     const int v = validate(shells, nshell, nullptr, nullptr, 0, quartets, nquartet, flags, false);
     if (v != LX_OK) return v;
     size_t mx = CHUNK_SLACK;
-    for (int64_t i = 0; i < nquartet; ++i)
-        mx = std::max(mx, chunk_estimate(shells, quartets, i, i + 1, flags & (LX_SOLID | LX_PATH_SPLIT)));
-    return (int64_t)(head_bytes(nshell, (int32_t)prim_count(shells, nshell)) + mx);
+    // a routed quartet may take the split path, which needs more room
+    const int32_t f = (flags & LX_PATH_ROUTED) ? (flags & LX_SOLID) | LX_PATH_SPLIT : flags & (LX_SOLID | LX_PATH_SPLIT);
+    for (int64_t i = 0; i < nquartet; ++i) mx = std::max(mx, chunk_estimate(shells, quartets, i, i + 1, f));
+    const int64_t need = (int64_t)(head_bytes(nshell, (int32_t)prim_count(shells, nshell)) + mx);
+    return (flags & LX_PATH_ROUTED) ? std::max(need, (int64_t)routed_scratch_bytes(nquartet)) : need;
 }
 
 int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
@@ -898,31 +953,68 @@ int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, con
     }
     unsigned* status = nullptr;
     if ((v = ensure_device(&status)) != LX_OK) return v;
-    PlannedBatch B;
-    if ((v = plan_batch(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, workspace_bytes,
-                        Overrides(), B)) != LX_OK)
-        return v;
-    // descriptors into a pinned staging buffer, so that the uploads do not wait for the stream
-    size_t total = align256(B.head_blob.size());
-    for (const auto& P : B.chunks) total += align256(P.blob.size());
+    if (!(flags & LX_PATH_ROUTED))
+        return eri_batch_staged(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, out, workspace,
+                                workspace_bytes, st, status);
+    // routed: predictions into the (still unused) workspace, read back, then one staged batch
+    // per path over the same output and workspace
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
-    int idx = -1;
-    char* stage = nullptr;
-    if ((v = stage_acquire(dev, total, idx, stage)) != LX_OK) return v;
-    size_t o = 0;
-    std::memcpy(stage, B.head_blob.data(), B.head_blob.size());
-    const char* head_src = stage;
-    o = align256(B.head_blob.size());
-    std::vector<const char*> blobs;
-    for (const auto& P : B.chunks) {
-        std::memcpy(stage + o, P.blob.data(), P.blob.size());
-        blobs.push_back(stage + o);
-        o += align256(P.blob.size());
+    const void* params = nullptr;
+    float tau = 0.f;
+    {
+        std::lock_guard<std::mutex> lock(g_router_mutex);
+        params = g_router_params[dev];
+        tau = g_router_tau[dev];
     }
-    v = enqueue_batch(B, head_src, blobs, out, workspace, status, st, (flags & LX_TIME_STAGES) != 0);
-    const int r = stage_release(dev, idx, st, true);
-    return v != LX_OK ? v : r;
+    if (!params) return LX_ERR_NO_ROUTER;
+    if (workspace_bytes < routed_scratch_bytes(nquartet)) return LX_ERR_WORKSPACE;
+    float* feat = static_cast<float*>(workspace);
+    float* pred = reinterpret_cast<float*>(static_cast<char*>(workspace) +
+                                           align256(sizeof(float) * LX_MLP_NIN * (size_t)nquartet));
+    if ((v = lx_route_features(shells, nshell, exps, nprim_total, quartets, nquartet, feat, cuda_stream)) != LX_OK)
+        return v;
+    if ((e = launch_mlp_forward(params, feat, nquartet, pred, st)) != cudaSuccess) return cuda_fail(e);
+    std::vector<float> hp(nquartet);
+    if ((e = cudaMemcpyAsync(hp.data(), pred, sizeof(float) * nquartet, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e);
+    std::vector<lx_quartet> q64, qsp;
+    for (int64_t i = 0; i < nquartet; ++i) (hp[i] >= tau ? q64 : qsp).push_back(quartets[i]);
+    const int32_t base = flags & ~LX_PATH_ROUTED;
+    if (!q64.empty() && (v = eri_batch_staged(shells, nshell, exps, coefs, nprim_total, q64.data(),
+                                              (int64_t)q64.size(), base, out, workspace, workspace_bytes, st,
+                                              status)) != LX_OK)
+        return v;
+    if (!qsp.empty() && (v = eri_batch_staged(shells, nshell, exps, coefs, nprim_total, qsp.data(),
+                                              (int64_t)qsp.size(), base | LX_PATH_SPLIT, out, workspace,
+                                              workspace_bytes, st, status)) != LX_OK)
+        return v;
+    return LX_OK;
+}
+
+int lx_router_set(const void* params_f16, float tau) {
+    if (!params_f16) return LX_ERR_NULL;
+    if (!std::isfinite(tau)) return LX_ERR_SIZE;
+    unsigned* status = nullptr;
+    int v = ensure_device(&status);
+    if (v != LX_OK) return v;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    std::lock_guard<std::mutex> lock(g_router_mutex);
+    if (!g_router_params[dev]) {
+        void* p = nullptr;
+        if ((e = cudaMalloc(&p, 2 * (size_t)LX_MLP_NPARAM)) != cudaSuccess) return cuda_fail(e);
+        g_router_params[dev] = p;
+    }
+    // synchronous: no batch on any stream may read the parameters while they are replaced
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e);
+    if ((e = cudaMemcpy(g_router_params[dev], params_f16, 2 * (size_t)LX_MLP_NPARAM, cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return cuda_fail(e);
+    g_router_tau[dev] = tau;
+    return LX_OK;
 }
 
 namespace {
@@ -960,7 +1052,7 @@ int lx_eri_graph_create(const lx_shell* shells, int32_t nshell, const double* ex
                         double* out, void* workspace, size_t workspace_bytes, void** handle) {
     if (!handle) return LX_ERR_NULL;
     *handle = nullptr;
-    if (flags & LX_TIME_STAGES) return LX_ERR_FLAGS;
+    if (flags & (LX_TIME_STAGES | LX_PATH_ROUTED)) return LX_ERR_FLAGS;
     int v = validate(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, true);
     if (v != LX_OK) return v;
     if (!out) return LX_ERR_NULL;
@@ -1036,6 +1128,7 @@ int lx_eri_autotune(const lx_shell* shells, int32_t nshell, const double* exps, 
                     void* cuda_stream) {
     int v = validate(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, true);
     if (v != LX_OK) return v;
+    if (flags & LX_PATH_ROUTED) return LX_ERR_FLAGS;
     if (flags & LX_PATH_SPLIT) return LX_OK;  // the split path has one tile shape
     if (max_keys < 1 || samples < 1 || out_doubles < 0) return LX_ERR_SIZE;
     if (!out || !workspace) return LX_ERR_NULL;

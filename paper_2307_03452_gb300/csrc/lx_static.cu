@@ -28,6 +28,7 @@ void* g_scratch_ptr[MAX_DEVICES];
 extern "C" int lx_eri_batch_static(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
                                    int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags,
                                    double* out, void* cuda_stream) {
+    if (flags & LX_PATH_ROUTED) return LX_ERR_FLAGS;  // routing needs scratch this entry does not have
     // The smallest workspace this batch can run in (it is processed in chunks that fit).
     const int64_t need = lx_eri_workspace_min(shells, nshell, quartets, nquartet, flags);
     if (need < 0) return (int)need;

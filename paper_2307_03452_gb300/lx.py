@@ -34,13 +34,16 @@ EXPORTS = sorted(["lx_eri_out_size", "lx_eri_workspace_size", "lx_eri_workspace_
                   "lx_eri_sync_status", "lx_eri_stage_times", "lx_strerror", "lx_last_cuda_error", "lx_boys",
                   "lx_hermite_R", "lx_hermite_H", "lx_split_gemm", "lx_route_features", "lx_mlp_forward",
                   "lx_mlp_grad", "lx_mlp_adam", "lx_eri_graph_create", "lx_eri_graph_launch",
-                  "lx_eri_graph_destroy", "lx_eri_autotune", "lx_tune_export", "lx_tune_import", "lx_tune_clear"])
+                  "lx_eri_graph_destroy", "lx_eri_autotune", "lx_tune_export", "lx_tune_import", "lx_tune_clear",
+                  "lx_router_set"])
 TILE_SHAPES = ["32x64", "64x32", "32x32", "64x64"]
 MLP_NIN = 20
 MLP_WIDTH = 64
 MLP_NPARAM = MLP_WIDTH * MLP_NIN + MLP_WIDTH + MLP_WIDTH * MLP_WIDTH + MLP_WIDTH + MLP_WIDTH + 1
 LX_PATH_SPLIT = 0x2
+LX_PATH_ROUTED = 0x4
 LX_TIME_STAGES = 0x200
+PATH_FLAGS = {"fp64": 0, "split": LX_PATH_SPLIT, "routed": LX_PATH_ROUTED}
 STAGES = ["norm", "pair_h", "boys_r", "gemm1", "gemm2", "split"]
 
 
@@ -115,6 +118,8 @@ def load(build_if_missing: bool = True):
         lib.lx_tune_clear.restype = ctypes.c_int
         lib.lx_route_features.argtypes = [c_vp, c_i32, c_vp, c_i32, c_vp, c_i64, c_vp, c_vp]
         lib.lx_route_features.restype = ctypes.c_int
+        lib.lx_router_set.argtypes = [c_vp, ctypes.c_float]
+        lib.lx_router_set.restype = ctypes.c_int
         lib.lx_mlp_forward.argtypes = [c_vp, c_vp, c_i64, c_vp, c_vp]
         lib.lx_mlp_forward.restype = ctypes.c_int
         lib.lx_mlp_grad.argtypes = [c_vp, c_vp, c_vp, c_i64, c_vp, c_vp, c_vp]
@@ -175,11 +180,11 @@ class Batch:
     """Host descriptors of one batch, packed once (the planner's input)."""
 
     def __init__(self, basis: dict, quartets, solid: bool, out_off=None, path: str = "fp64"):
-        if path not in ("fp64", "split"):
+        if path not in PATH_FLAGS:
             raise ValueError(f"unknown path {path!r}")
         self.solid = bool(solid)
         self.path = path
-        self.flags = (LX_SOLID if solid else LX_CART) | (LX_PATH_SPLIT if path == "split" else 0)
+        self.flags = (LX_SOLID if solid else LX_CART) | PATH_FLAGS[path]
         self.shells = pack_shells(basis)
         self.exps = np.ascontiguousarray(basis["exps"], dtype=np.float64)
         self.coefs = np.ascontiguousarray(basis["coefs"], dtype=np.float64)
@@ -361,7 +366,8 @@ def eri(basis: dict, quartets, solid: bool = True, device="cuda", workspace_limi
     """Evaluate (ab|cd) for every quartet on the GPU; returns (out, out_offsets) with out a
     float64 CUDA tensor holding each quartet's row-major (a,b,c,d) block.  path "fp64" runs
     every step in FP64; "split" runs the two transforms as BF16 slice products on the
-    tensor cores."""
+    tensor cores; "routed" sends each quartet to one of the two by the network installed
+    with router_set."""
     import torch
     b = Batch(basis, quartets, solid, path=path)
     need = b.workspace_size()
@@ -372,6 +378,22 @@ def eri(basis: dict, quartets, solid: bool = True, device="cuda", workspace_limi
     b.run(out, ws, stream)
     sync_status(stream)
     return out[: b.out_size], b.quartets["out_offset"].copy()
+
+
+def router_set(params_f16, tau: float):
+    """Install the routing network of path "routed" on the current device: params_f16 holds
+    the MLP_NPARAM FP16 parameters (any array or tensor; copied), tau the threshold on the
+    predicted log10 max |integral| at or above which a quartet takes the FP64 path."""
+    try:
+        import torch
+        if isinstance(params_f16, torch.Tensor):
+            params_f16 = params_f16.detach().to("cpu").numpy()
+    except ImportError:
+        pass
+    p = np.ascontiguousarray(np.asarray(params_f16, dtype=np.float16))
+    if p.size != MLP_NPARAM:
+        raise ValueError(f"expected {MLP_NPARAM} parameters, got {p.size}")
+    _check(load().lx_router_set(_ptr(p), ctypes.c_float(float(tau))), "lx_router_set")
 
 
 def split_gemm(A, B, stream=None):

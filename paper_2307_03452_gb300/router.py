@@ -108,23 +108,16 @@ def labels(basis, quartets, solid=True):
 
 
 def routed_eri(basis, quartets, router: Router, solid=True, tau=None, device="cuda",
-               workspace_limit: int = 16 << 30):
-    """Evaluate with per-quartet routing; returns (out, offsets, route mask: True = FP64).
-    Each of the two sub-batches is chunked to fit workspace_limit bytes of scratch (or the
-    smallest workspace that holds its largest quartet, if that is more)."""
-    import torch
+               workspace_limit: int = 16 << 30, return_mask: bool = True):
+    """Evaluate with per-quartet routing in one library call (path "routed", after installing
+    this network); returns (out, offsets, route mask: True = FP64) or (out, offsets) when
+    return_mask is False.  The batch is chunked to fit workspace_limit bytes of scratch (or
+    the smallest workspace that holds its largest quartet, if that is more).  The mask is
+    recomputed here from the same features and network, for reporting."""
     tau = router.tau if tau is None else tau
-    feat = lx.route_features(basis, quartets, device=device)
-    pred = router.predict(feat)
-    to_fp64 = (pred >= tau).cpu().numpy()
-    qs = np.asarray(quartets, dtype=np.int32).reshape(-1, 4)
-    full = lx.Batch(basis, qs, solid)
-    off = full.quartets["out_offset"].copy()
-    out = torch.empty(max(full.out_size, 1), dtype=torch.float64, device=device)
-    for mask, path in ((to_fp64, "fp64"), (~to_fp64, "split")):
-        if mask.any():
-            b = lx.Batch(basis, qs[mask], solid, out_off=off[mask], path=path)
-            need = max(min(b.workspace_size(), int(workspace_limit)), b.workspace_min())
-            b.run(out, lx.alloc_workspace(need, device))
-    lx.sync_status()
-    return out[: full.out_size], off, to_fp64
+    lx.router_set(router.p16, tau)
+    out, off = lx.eri(basis, quartets, solid=solid, device=device, workspace_limit=workspace_limit, path="routed")
+    if not return_mask:
+        return out, off
+    to_fp64 = (router.predict(lx.route_features(basis, quartets, device=device)) >= tau).cpu().numpy()
+    return out, off, to_fp64

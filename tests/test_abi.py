@@ -162,3 +162,17 @@ def test_tuning_table_round_trip(tmp_path):
     with pytest.raises(lx.LxError):
         lx.tune_import(np.array([[4, 4, 4, 4, 1, 1, 1, 9, 0]], dtype=np.int32))  # bad shape id
     lx.tune_clear()
+
+
+def test_routed_flag_combinations():
+    # routing picks the path itself: it cannot be combined with the split flag
+    basis, quartets = inputs.uniform_class((1, 1, 1, 1), 2, 5)
+    b = lx.Batch(basis, quartets, True)
+    lib = lx.load()
+    bad = lx.LX_SOLID | lx.LX_PATH_SPLIT | lx.LX_PATH_ROUTED
+    assert lib.lx_eri_workspace_size(lx._ptr(b.shells), len(b.shells), lx._ptr(b.quartets), len(b.quartets), bad) == -5
+    ok = lx.LX_SOLID | lx.LX_PATH_ROUTED
+    need = lib.lx_eri_workspace_size(lx._ptr(b.shells), len(b.shells), lx._ptr(b.quartets), len(b.quartets), ok)
+    split = lib.lx_eri_workspace_size(lx._ptr(b.shells), len(b.shells), lx._ptr(b.quartets), len(b.quartets),
+                                      lx.LX_SOLID | lx.LX_PATH_SPLIT)
+    assert need >= split > 0

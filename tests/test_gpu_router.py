@@ -116,3 +116,31 @@ def test_routed_result_against_cpu_oracle():
     routed, off, _ = rt.routed_eri(basis, quartets, r)
     ref, roff = oracle.eri(basis, quartets, solid=True)
     assert np.abs(routed.cpu().numpy() - ref).max() <= 1e-10
+
+
+@pytest.mark.skipif(not os.path.exists(rt.WEIGHTS), reason="no trained router weights")
+def test_routed_library_call_partitions_exactly():
+    # one "routed" call = the FP64 path on the quartets predicted >= tau plus the split path on
+    # the rest, bit for bit; tau far above or below every prediction gives one path alone
+    r = rt.Router.load()
+    basis, quartets = inputs.spread_distances(300, seed=779, kmax=2)
+    qs = np.asarray(quartets, dtype=np.int32)
+    a64, off = lx.eri(basis, qs, solid=True, path="fp64")
+    asp, _ = lx.eri(basis, qs, solid=True, path="split")
+    for tau, ref in ((1e30, asp), (-1e30, a64)):
+        lx.router_set(r.p16, tau)
+        got, goff = lx.eri(basis, qs, solid=True, path="routed")
+        assert np.array_equal(goff, off)
+        assert torch.equal(got, ref)
+    pred = r.predict(lx.route_features(basis, qs)).cpu().numpy()
+    tau = float(np.median(pred))  # about half each way
+    lx.router_set(r.p16, tau)
+    got, _ = lx.eri(basis, qs, solid=True, path="routed")
+    mask = pred >= tau
+    assert 0 < mask.sum() < len(mask)
+    comp = torch.zeros_like(got)
+    for m, path in ((mask, "fp64"), (~mask, "split")):
+        b = lx.Batch(basis, qs[m], True, out_off=off[m], path=path)
+        b.run(comp, lx.alloc_workspace(b.workspace_size()))
+    torch.cuda.synchronize()
+    assert torch.equal(got, comp)
