@@ -224,7 +224,9 @@ size_t pair_bytes(const lx_shell* sh, int sa, int sb, int flags) {
     const lx_shell &a = sh[sa], &b = sh[sb];
     const int64_t kab = (int64_t)a.nprim * b.nprim;
     const int64_t rows = (int64_t)nfun(a.l, solid) * nfun(b.l, solid);
-    (void)split;  // the split path keeps its digit planes per quartet (the balancing depends on it)
+    // the split path keeps the digit planes of H with each quartet (they could be shared by
+    // the quartets of one pair, since H's column scales depend on H alone)
+    (void)split;
     return sizeof(DPair) + kab * sizeof(WorkItem) + 8 * (size_t)(kab * 4 + rows * kab * pyr(a.l + b.l)) + 512;
 }
 

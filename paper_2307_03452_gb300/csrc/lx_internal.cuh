@@ -50,8 +50,6 @@ struct DPair {  // one shell pair on one side of the quartet
     int pad;
     int64_t h_off;     // H block (doubles): [nrow][Kab*np]
     int64_t info_off;  // pair scalars (doubles): [Kab][4] = zeta_p, P
-    int64_t dig_off;   // split path: digit planes of H (bytes from the workspace base)
-    int64_t exp_off;   // split path: row exponents of H (bytes)
 };
 
 struct DQuartet {
