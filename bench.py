@@ -50,6 +50,9 @@ def parse_args(argv=None):
     p.add_argument("--no-routed", action="store_true", help="skip the routed-workload sample")
     p.add_argument("--routed-quartets", type=int, default=4000)
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
+    p.add_argument("--sweep", action="store_true",
+                   help="instead of the benchmark line: one JSON line per integral class (dd|dd)..(ii|ii) "
+                        "and total contraction degree 1, 5, 25, both paths, with per-stage shares")
     return p.parse_args(argv)
 
 
@@ -289,10 +292,59 @@ def run_reference(args):
     return 0
 
 
+SWEEP_CLASSES = [(2, 2, 2, 2), (3, 3, 3, 3), (4, 4, 4, 4), (5, 5, 5, 5), (6, 6, 6, 6)]
+# total contraction degree K_bra K_ket -> per-shell degrees (a, b, c, d)
+SWEEP_K = {1: (1, 1, 1, 1), 5: (5, 1, 1, 1), 25: (5, 1, 5, 1)}
+
+
+def run_sweep(args):
+    """Per class and total contraction degree: quartets/s, FP64-equivalent TFLOP/s and the
+    share of each stage, on both paths (the paper's class x K table and stage breakdown)."""
+    import torch
+
+    from paper_2307_03452_gb300 import inputs, lx
+    torch.cuda.set_device(0)
+    lx.load(build_if_missing=True)
+    flush_buf = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    names = "spdfghi"
+    for cls in SWEEP_CLASSES:
+        for ktot, ks in SWEEP_K.items():
+            la, lb, lc, ld = cls
+            # about 0.25 s of FP64-path GEMM work at 1 TFLOP/s, between 64 and 65536 quartets
+            b1, q1 = inputs.class_sweep(cls, 1, ks, 1)
+            g1, g2, _ = gemm_flops(b1, q1, True)
+            nq = int(min(65536, max(64, 0.25e12 / (g1 + g2))))
+            basis, quartets = inputs.class_sweep(cls, nq, ks, 4100 + 10 * la + ktot)
+            g1, g2, nint = gemm_flops(basis, quartets, True)
+            line = {"class": "(" + names[la] + names[lb] + "|" + names[lc] + names[ld] + ")", "K_total": ktot,
+                    "K_per_shell": list(ks), "nquartet": nq, "solid": True}
+            ref = None
+            for path in ("fp64", "split"):
+                b = lx.Batch(basis, quartets, solid=True, path=path)
+                out = torch.empty(b.out_size, dtype=torch.float64, device="cuda")
+                ws = lx.alloc_workspace(max(b.workspace_min(), min(b.workspace_size(), 64 << 30)))
+                ms, stage, _ = time_steps(torch, lx, b, out, ws, 3, 2, flush_buf, 1)
+                t = sum(ms) / len(ms)
+                tot = sum(stage.values())
+                line[path] = {"quartets_per_s": nq / (t * 1e-3), "integrals_per_s": nint / (t * 1e-3),
+                              "ms_per_step": t, "fp64_equiv_tflops": (g1 + g2) / (t * 1e-3) / 1e12,
+                              "stage_share": {k: v / tot for k, v in stage.items() if v > 0}}
+                if path == "fp64":
+                    ref = out.clone()
+                else:
+                    line[path]["max_abs_diff_vs_fp64_path"] = float((out - ref).abs().max())
+                del b, out, ws
+                torch.cuda.empty_cache()
+            print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     import numpy as np
     import torch
 

@@ -67,6 +67,26 @@ def uniform_class(cls, nquartet, seed, cube=10.0, exps=(0.1, 10.0), kmin=1, kmax
     return basis, quartets
 
 
+def class_sweep(cls, nquartet, k_per_shell, seed, cube=20.0, exps=(0.05, 20.0)):
+    """nquartet quartets of one class with fixed contraction degrees (K_a, K_b, K_c, K_d):
+    centers uniform in a cube of side `cube` bohr; per shell one exponent log-uniform in
+    `exps`, its K primitives spaced by factors of 3 around it; raw coefficients uniform in
+    (0, 1] (1 for K = 1).  The paper's class x contraction table uses such batches."""
+    rng = np.random.default_rng(seed)
+    nsh = 4 * nquartet
+    ls = np.tile(np.asarray(cls, dtype=np.int32), nquartet)
+    ks = np.tile(np.asarray(k_per_shell, dtype=np.int32), nquartet)
+    centers = rng.uniform(0.0, cube, (nsh, 3))
+    mid = _loguniform(rng, exps[0], exps[1], nsh)
+    off = np.zeros(nsh, dtype=np.int32)
+    off[1:] = np.cumsum(ks)[:-1]
+    spread = [3.0 ** (np.arange(k) - (k - 1) / 2.0) for k in range(max(k_per_shell) + 1)]
+    e = np.concatenate([mid[i] * spread[ks[i]] for i in range(nsh)])
+    c = np.where(np.repeat(ks, ks) > 1, 1.0 - rng.uniform(0.0, 1.0, int(ks.sum())), 1.0)
+    basis = {"l": ls, "nprim": ks, "prim_off": off, "center": centers, "exps": e, "coefs": c}
+    return basis, np.arange(nsh, dtype=np.int32).reshape(nquartet, 4)
+
+
 def mixed_classes(nquartet, seed, classes=MIXED_CLASSES, cube=20.0, exps=(0.05, 50.0), kmin=1, kmax=5):
     """Quartets drawn uniformly over `classes`, K per shell uniform in kmin..kmax,
     exponents log-uniform, raw coefficients uniform in (0, 1]."""

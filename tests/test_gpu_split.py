@@ -117,3 +117,29 @@ def test_both_paths_at_maximum_contraction():
         assert np.array_equal(off, roff)
         err = np.abs(out.cpu().numpy() - ref).max()
         assert err <= 1e-10, f"{path}: max abs err {err:.3e}"
+
+
+def test_split_and_routed_on_degenerate_geometry():
+    # all four shells on one center (T = 0, P = A) with exponents from 0.05 to 50, plus a pair
+    # of coincident centers far from the other pair: split and routed paths against the oracle
+    ls = [6, 6, 5, 4]
+    basis = {"l": np.asarray(ls, np.int32), "nprim": np.array([1, 2, 1, 1], np.int32),
+             "prim_off": np.array([0, 1, 3, 4], np.int32), "center": np.zeros((4, 3)),
+             "exps": np.array([50.0, 0.05, 3.0, 0.05, 20.0]), "coefs": np.array([1.0, 0.3, 0.7, 1.0, 1.0])}
+    far = {k: v.copy() for k, v in basis.items()}
+    far["center"] = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, 0.0], [9.0, 0.0, 0.0], [9.0, 0.0, 0.0]])
+    b, q = inputs.concat([(basis, np.array([[0, 1, 2, 3], [3, 2, 1, 0]], np.int32)),
+                          (far, np.array([[0, 1, 2, 3]], np.int32))])
+    ref, roff = oracle.eri(b, q, solid=True)
+    from paper_2307_03452_gb300 import router as rt
+    import os
+    paths = ["split"] + (["routed"] if os.path.exists(rt.WEIGHTS) else [])
+    for path in paths:
+        if path == "routed":
+            r = rt.Router.load()
+            lx.router_set(r.p16, r.tau)
+        out, off = lx.eri(b, q, solid=True, path=path)
+        assert np.array_equal(off, roff)
+        got = out.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert np.abs(got - ref).max() <= 1e-10, f"{path}: {np.abs(got - ref).max():.3e}"
