@@ -68,10 +68,13 @@ typedef struct {
                               error grows with the magnitude of a quartet's intermediates */
 #define LX_PATH_ROUTED 0x4 /* per quartet: the routing network set by lx_router_set predicts log10
                               of the largest |integral|; quartets predicted at or above its
-                              threshold take LX_PATH_FP64, the rest LX_PATH_SPLIT.  lx_eri_batch
-                              then waits for the stream once, to read the predictions back.
-                              Not with LX_PATH_SPLIT; not for lx_eri_graph_create,
-                              lx_eri_autotune or lx_eri_batch_static */
+                              threshold take LX_PATH_FP64, and so do quartets whose two
+                              transforms need fewer than LX_ROUTE_SPLIT_MIN_FLOP FLOPs (too
+                              small for the split path to be faster); the rest take
+                              LX_PATH_SPLIT.  lx_eri_batch then waits for the stream once, to
+                              read the predictions back.  Not with LX_PATH_SPLIT; not for
+                              lx_eri_graph_create, lx_eri_autotune or lx_eri_batch_static */
+#define LX_ROUTE_SPLIT_MIN_FLOP 1.0e6 /* 2 N_ab (K_bra N_p)(K_ket N_q) + 2 N_ab (K_ket N_q) N_cd */
 #define LX_TIME_STAGES 0x200 /* record CUDA events around each stage (see lx_eri_stage_times) */
 
 /* stages timed with LX_TIME_STAGES */

@@ -982,7 +982,15 @@ int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, con
         return cuda_fail(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e);
     std::vector<lx_quartet> q64, qsp;
-    for (int64_t i = 0; i < nquartet; ++i) (hp[i] >= tau ? q64 : qsp).push_back(quartets[i]);
+    const bool solid = flags & LX_SOLID;
+    for (int64_t i = 0; i < nquartet; ++i) {
+        const lx_quartet& q = quartets[i];
+        const lx_shell &a = shells[q.s[0]], &b = shells[q.s[1]], &c = shells[q.s[2]], &d = shells[q.s[3]];
+        const double nab = (double)nfun(a.l, solid) * nfun(b.l, solid), ncd = (double)nfun(c.l, solid) * nfun(d.l, solid);
+        const double kp = (double)a.nprim * b.nprim * pyr(a.l + b.l), kq = (double)c.nprim * d.nprim * pyr(c.l + d.l);
+        const double flop = 2.0 * nab * kp * kq + 2.0 * nab * kq * ncd;
+        (hp[i] >= tau || flop < LX_ROUTE_SPLIT_MIN_FLOP ? q64 : qsp).push_back(q);
+    }
     const int32_t base = flags & ~LX_PATH_ROUTED;
     if (!q64.empty() && (v = eri_batch_staged(shells, nshell, exps, coefs, nprim_total, q64.data(),
                                               (int64_t)q64.size(), base, out, workspace, workspace_bytes, st,

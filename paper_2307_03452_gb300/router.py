@@ -120,4 +120,21 @@ def routed_eri(basis, quartets, router: Router, solid=True, tau=None, device="cu
     if not return_mask:
         return out, off
     to_fp64 = (router.predict(lx.route_features(basis, quartets, device=device)) >= tau).cpu().numpy()
-    return out, off, to_fp64
+    return out, off, to_fp64 | (transform_flops(basis, quartets, solid) < ROUTE_SPLIT_MIN_FLOP)
+
+
+#: quartets whose two transforms take fewer FLOPs than this go to the FP64 path (as in the library)
+ROUTE_SPLIT_MIN_FLOP = 1.0e6
+
+
+def transform_flops(basis, quartets, solid=True):
+    """2 N_ab (K_bra N_p)(K_ket N_q) + 2 N_ab (K_ket N_q) N_cd per quartet."""
+    q = np.asarray(quartets, dtype=np.int64).reshape(-1, 4)
+    l, k = np.asarray(basis["l"]), np.asarray(basis["nprim"]).astype(np.float64)
+    nf = (2 * l + 1) if solid else (l + 1) * (l + 2) // 2
+    pyr = lambda n: (n + 1) * (n + 2) * (n + 3) / 6.0  # noqa: E731
+    nab = nf[q[:, 0]] * nf[q[:, 1]] * 1.0
+    ncd = nf[q[:, 2]] * nf[q[:, 3]] * 1.0
+    kp = k[q[:, 0]] * k[q[:, 1]] * pyr(l[q[:, 0]] + l[q[:, 1]])
+    kq = k[q[:, 2]] * k[q[:, 3]] * pyr(l[q[:, 2]] + l[q[:, 3]])
+    return 2.0 * nab * kp * kq + 2.0 * nab * kq * ncd

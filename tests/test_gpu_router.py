@@ -136,7 +136,7 @@ def test_routed_library_call_partitions_exactly():
     tau = float(np.median(pred))  # about half each way
     lx.router_set(r.p16, tau)
     got, _ = lx.eri(basis, qs, solid=True, path="routed")
-    mask = pred >= tau
+    mask = (pred >= tau) | (rt.transform_flops(basis, qs) < rt.ROUTE_SPLIT_MIN_FLOP)
     assert 0 < mask.sum() < len(mask)
     comp = torch.zeros_like(got)
     for m, path in ((mask, "fp64"), (~mask, "split")):
@@ -144,3 +144,24 @@ def test_routed_library_call_partitions_exactly():
         b.run(comp, lx.alloc_workspace(b.workspace_size()))
     torch.cuda.synchronize()
     assert torch.equal(got, comp)
+
+
+@pytest.mark.skipif(not os.path.exists(rt.WEIGHTS), reason="no trained router weights")
+def test_routed_small_quartets_take_the_fp64_path():
+    # (dd|dd) at K = 1 is below the split path's break-even size: with the threshold set so that
+    # every prediction says "split", routing still sends these quartets to the FP64 path, while
+    # the (gg|gg) quartets beside them take the split path
+    r = rt.Router.load()
+    small = inputs.uniform_class((2, 2, 2, 2), 6, 780, cube=4.0, exps=(0.1, 10.0))
+    big = inputs.uniform_class((4, 4, 4, 4), 3, 781, cube=4.0, exps=(0.1, 10.0))
+    basis, qs = inputs.concat([small, big])
+    qs = np.asarray(qs, dtype=np.int32)
+    assert np.all(rt.transform_flops(basis, qs[:6]) < rt.ROUTE_SPLIT_MIN_FLOP)
+    assert np.all(rt.transform_flops(basis, qs[6:]) >= rt.ROUTE_SPLIT_MIN_FLOP)
+    a64, off = lx.eri(basis, qs, solid=True, path="fp64")
+    asp, _ = lx.eri(basis, qs, solid=True, path="split")
+    lx.router_set(r.p16, 1e30)
+    got, _ = lx.eri(basis, qs, solid=True, path="routed")
+    n_small = int(off[6])
+    assert torch.equal(got[:n_small], a64[:n_small])
+    assert torch.equal(got[n_small:], asp[n_small:])
