@@ -420,9 +420,10 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             for (int c = 0; c < c2; ++c) P.items_cA.push_back({c0 + 1, c, 0, 0});
             // digit kernels: one item per 8 consecutive rows (every row tile is a multiple of 8)
             for (int row = 0; row < split_rowpad(k2, SPLIT_TA); row += 8) P.items_sr.push_back({i, row, 0, 0});
+            // H_bra and H_ket digit planes go with the GEMM1 operands; X's only after GEMM1
             for (int row = 0; row < split_rowpad(d.nab, tb1); row += 8) P.items_sB.push_back({sb1, row, 0, 0});
+            for (int row = 0; row < split_rowpad(d.ncd, tb2); row += 8) P.items_sB.push_back({sb1 + 2, row, 0, 0});
             for (int row = 0; row < split_rowpad(d.nab, SPLIT_TA); row += 8) P.items_sD.push_back({sb1 + 1, row, 0, 0});
-            for (int row = 0; row < split_rowpad(d.ncd, tb2); row += 8) P.items_sD.push_back({sb1 + 2, row, 0, 0});
             const int mt1 = split_rowpad(k2, SPLIT_TA) / SPLIT_TA, nt1 = (d.nab + tb1 - 1) / tb1;
             const int mt2 = split_rowpad(d.nab, SPLIT_TA) / SPLIT_TA, nt2 = (d.ncd + tb2 - 1) / tb2;
             for (int m = 0; m < mt1; ++m)
@@ -686,17 +687,16 @@ int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector
             // and H_bra
             if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
             if ((e = launch_colmax(d_cmd, items(P.off_icA), (int)P.items_cA.size(), ws, wsb, st)) != cudaSuccess ||
-                (e = launch_split_r(d_q, d_sq, items(P.off_isr), (int)P.items_sr.size(), ws, wsb, st)) !=
-                    cudaSuccess ||
-                (e = launch_split_rows(d_srd, items(P.off_isB), (int)P.items_sB.size(), ws, wsb, st)) != cudaSuccess)
+                (e = launch_split_operands(d_q, d_sq, items(P.off_isr), (int)P.items_sr.size(), d_srd,
+                                           items(P.off_isB), (int)P.items_sB.size(), ws, wsb, st)) != cudaSuccess)
                 return cuda_fail(e);
-            if ((e = tm.end(LX_STAGE_SPLIT, 3)) != cudaSuccess) return cuda_fail(e);
+            if ((e = tm.end(LX_STAGE_SPLIT, 2)) != cudaSuccess) return cuda_fail(e);
             if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
             if ((e = launch_split_gemm(d_sg1, items(P.off_isg1), (int)P.items_sg1.size(), wsb, ws, status, st)) !=
                 cudaSuccess)
                 return cuda_fail(e);
             if ((e = tm.end(LX_STAGE_GEMM1, 1)) != cudaSuccess) return cuda_fail(e);
-            // operands of GEMM2: digit planes of [ab|q] and H_ket
+            // the other operand of GEMM2: digit planes of [ab|q]
             if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
             if ((e = launch_split_rows(d_srd, items(P.off_isD), (int)P.items_sD.size(), ws, wsb, st)) != cudaSuccess)
                 return cuda_fail(e);

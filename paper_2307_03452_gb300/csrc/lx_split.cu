@@ -263,12 +263,9 @@ __device__ __forceinline__ void split_8rows(int r0, int nkb, int T, bool fixed, 
     }
 }
 
-// item.q = descriptor, item.a = r0.
-__global__ void __launch_bounds__(256) split_rows_kernel(const SplitRowsDesc* __restrict__ descs, const WorkItem* __restrict__ items,
-                                  int nitems, const double* __restrict__ src_base, char* __restrict__ ws) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (warp >= nitems) return;
-    const WorkItem it = items[warp];
+// One split_rows item (item.q = descriptor, item.a = r0), by one warp.
+__device__ __forceinline__ void split_rows_item(const SplitRowsDesc* __restrict__ descs, const WorkItem& it,
+                                                const double* __restrict__ src_base, char* __restrict__ ws) {
     const SplitRowsDesc d = descs[it.q];
     const double* src = src_base + d.src_off;
     const int* shift = d.shift_off >= 0 ? reinterpret_cast<const int*>(ws + d.shift_off) : nullptr;
@@ -286,6 +283,14 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const SplitRowsDesc* __
                 });
 }
 
+__global__ void __launch_bounds__(256) split_rows_kernel(const SplitRowsDesc* __restrict__ descs,
+                                                         const WorkItem* __restrict__ items, int nitems,
+                                                         const double* __restrict__ src_base, char* __restrict__ ws) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp >= nitems) return;
+    split_rows_item(descs, items[warp], src_base, ws);
+}
+
 // Rows q of the GEMM1 A operand: A[q][k] = [p+q]^(0) of primitive quartet (kp, kq) with
 // k = kp*Np + p, q = kq*Nq + qq, scaled by 2^c1[k].  item.q = quartet, item.a = r0.  Here
 // the 8 rows are processed at once: lane (rr, c) = (lane / 4, lane % 4) handles row r0 + rr
@@ -294,20 +299,20 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const SplitRowsDesc* __
 // Hermite triplets are carried as n | i << 8 | v << 16 (n = t+u+v, i = u+v), which add
 // componentwise, and hidx(t, u, v) = n(n+1)(n+2)/6 + i(i+1)/2 + v comes from two small tables.
 __device__ int g_niv_split[NHERM_TOT];
-__global__ void __launch_bounds__(256) split_r_kernel(const DQuartet* __restrict__ qd,
-                                                      const SplitQuartet* __restrict__ sq,
-                                                      const WorkItem* __restrict__ items, int nitems,
-                                                      const double* __restrict__ wsd, char* __restrict__ ws) {
-    __shared__ int tab_n[2 * LTOT + 2], tab_i[2 * LTOT + 2];
-    for (int j = threadIdx.x; j < 2 * LTOT + 2; j += blockDim.x) {
+constexpr int NTAB = 2 * LTOT + 2;
+__device__ __forceinline__ void hermite_tables(int* tab_n, int* tab_i) {
+    for (int j = threadIdx.x; j < NTAB; j += blockDim.x) {
         tab_n[j] = j * (j + 1) * (j + 2) / 6;
         tab_i[j] = j * (j + 1) / 2;
     }
-    __syncthreads();
+}
+
+// One split_r item (item.q = quartet, item.a = r0), by one warp; tab_n, tab_i from hermite_tables.
+__device__ __forceinline__ void split_r_item(const DQuartet* __restrict__ qd, const SplitQuartet* __restrict__ sq,
+                                             const WorkItem& it, const double* __restrict__ wsd,
+                                             char* __restrict__ ws, const int* tab_n, const int* tab_i) {
     const int* niv = g_niv_split;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= nitems) return;
-    const WorkItem it = items[warp];
+    const int lane = threadIdx.x & 31;
     const DQuartet q = qd[it.q];
     const SplitQuartet s = sq[it.q];
     const int row = it.a + (lane >> 2), c8 = 8 * (lane & 3);
@@ -368,6 +373,48 @@ __global__ void __launch_bounds__(256) split_r_kernel(const DQuartet* __restrict
         store_digit_group(dig, row, SPLIT_KB * kb + c8, SPLIT_TA, s.nkb1, qv);
     }
     if ((lane & 3) == 0) reinterpret_cast<int*>(ws + s.a1_exp)[row] = e;
+}
+
+__global__ void __launch_bounds__(256) split_r_kernel(const DQuartet* __restrict__ qd,
+                                                      const SplitQuartet* __restrict__ sq,
+                                                      const WorkItem* __restrict__ items, int nitems,
+                                                      const double* __restrict__ wsd, char* __restrict__ ws) {
+    __shared__ int tab_n[NTAB], tab_i[NTAB];
+    hermite_tables(tab_n, tab_i);
+    __syncthreads();
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp >= nitems) return;
+    split_r_item(qd, sq, items[warp], wsd, ws, tab_n, tab_i);
+}
+
+// The operands of GEMM1 and the H operand of GEMM2 in one launch: split_r items ([p|q]^T rows,
+// issue-bound gathers) and split_rows items (H rows, load-latency bound) in alternating blocks,
+// so that the two kinds share the SMs.  8 warps (items) per block.
+__global__ void __launch_bounds__(256) split_operands_kernel(const DQuartet* __restrict__ qd,
+                                                             const SplitQuartet* __restrict__ sq,
+                                                             const WorkItem* __restrict__ items_r, int n_r,
+                                                             const SplitRowsDesc* __restrict__ descs,
+                                                             const WorkItem* __restrict__ items_w, int n_w,
+                                                             const double* __restrict__ wsd, char* __restrict__ ws) {
+    __shared__ int tab_n[NTAB], tab_i[NTAB];
+    hermite_tables(tab_n, tab_i);
+    __syncthreads();
+    const int nb_r = (n_r + 7) / 8, nb_w = (n_w + 7) / 8, m = min(nb_r, nb_w);
+    const int b = blockIdx.x;
+    int kind, idx;  // kind 0: split_r, 1: split_rows
+    if (b < 2 * m) {
+        kind = b & 1;
+        idx = b >> 1;
+    } else {
+        kind = nb_r > nb_w ? 0 : 1;
+        idx = m + (b - 2 * m);
+    }
+    const int w = idx * 8 + (threadIdx.x >> 5);
+    if (kind == 0) {
+        if (w < n_r) split_r_item(qd, sq, items_r[w], wsd, ws, tab_n, tab_i);
+    } else {
+        if (w < n_w) split_rows_item(descs, items_w[w], wsd, ws);
+    }
 }
 
 // One thread per column k: c_k with |x| < 2^c_k over the column (from the largest exponent
@@ -639,6 +686,15 @@ cudaError_t launch_split_r(const DQuartet* qd, const SplitQuartet* sq, const Wor
     const int warps_per_block = 8;
     split_r_kernel<<<(nitems + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
         qd, sq, items, nitems, wsd, ws);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_operands(const DQuartet* qd, const SplitQuartet* sq, const WorkItem* items_r, int n_r,
+                                  const SplitRowsDesc* descs, const WorkItem* items_w, int n_w, const double* wsd,
+                                  char* ws, cudaStream_t st) {
+    const int nb = (n_r + 7) / 8 + (n_w + 7) / 8;
+    if (nb <= 0) return cudaSuccess;
+    split_operands_kernel<<<nb, 256, 0, st>>>(qd, sq, items_r, n_r, descs, items_w, n_w, wsd, ws);
     return cudaGetLastError();
 }
 
