@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define LX_LMAX 6  /* largest shell angular momentum (i shells) */
+#define LX_LMAX 7  /* largest shell angular momentum (k shells) */
 #define LX_KMAX 16 /* largest contraction degree of one shell */
 
 /* One shell: angular momentum l (0..LX_LMAX), nprim primitives whose exponents and raw

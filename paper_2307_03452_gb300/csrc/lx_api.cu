@@ -70,6 +70,9 @@ int cuda_fail(cudaError_t e) {
     return LX_ERR_CUDA;
 }
 
+FoldHost g_fold;  // the solid fold's row lists (host copy), built with the first device
+bool g_fold_ready = false;
+
 // Once per device, with that device current: check the architecture, upload the tables,
 // look up the status word.  Returns LX_OK or an error code; *status receives the word.
 int ensure_device(unsigned** status) {
@@ -87,15 +90,16 @@ int ensure_device(unsigned** status) {
         if (major != 10 || minor != 3) return LX_ERR_ARCH;
         std::vector<double> boys(BOYS_NROW * BOYS_NPT);
         make_boys_table(boys.data());
-        std::vector<double> solid(840);
+        std::vector<double> solid(NSOLID_PACKED);
         make_solid_coefs(solid.data());
         std::vector<int> tuv(NHERM_TOT);
         make_tuv_table(tuv.data());
         if ((e = init_boys_table(boys.data())) != cudaSuccess) return cuda_fail(e);
-        static FoldHost fold;  // identical for every device; built once
-        static const bool fold_ok = make_fold_lists(solid.data(), fold);
-        if (!fold_ok) return LX_ERR_SIZE;
-        if ((e = init_prep_tables(solid.data(), tuv.data(), &fold)) != cudaSuccess) return cuda_fail(e);
+        if (!g_fold_ready) {  // identical for every device; built once
+            if (!make_fold_lists(solid.data(), g_fold)) return LX_ERR_SIZE;
+            g_fold_ready = true;
+        }
+        if ((e = init_prep_tables(solid.data(), tuv.data(), &g_fold)) != cudaSuccess) return cuda_fail(e);
         if ((e = init_tuv_table(tuv.data())) != cudaSuccess) return cuda_fail(e);
         if ((e = init_split_kernels(tuv.data())) != cudaSuccess) return cuda_fail(e);
         if ((e = init_router_kernels()) != cudaSuccess) return cuda_fail(e);
@@ -277,6 +281,7 @@ struct ChunkPlan {
     std::vector<DQuartet> quartets;
     std::vector<WorkItem> items_h, items_br, items_g1, items_g2;
     int br_lmax = 0;  // largest L of the chunk's quartets
+    int fold_lcap = 0, fold_qcap = 0, fold_wcap = 0;  // solid fold: largest l, Q and W rows of the chunk's pairs
     size_t off_pairs = 0, off_quartets = 0, off_h = 0, off_br = 0, off_g1 = 0, off_g2 = 0, off_data = 0;
     int g1_counts[GEMM_NVARIANT] = {0, 0, 0, 0}, g2_counts[GEMM_NVARIANT] = {0, 0, 0, 0};
     size_t off_counters = 0;  // 2 x GEMM_NVARIANT work counters, uploaded as zeros with the blob
@@ -300,6 +305,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     P.items_h.clear();
     P.items_br.clear();
     P.br_lmax = 0;
+    P.fold_lcap = P.fold_qcap = P.fold_wcap = 0;
     P.items_g1.clear();
     P.items_g2.clear();
     P.srd.clear();
@@ -347,6 +353,13 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     // work lists
     for (int i = 0; i < (int)P.pairs.size(); ++i)
         for (int kp = 0; kp < P.pairs[i].Kab; ++kp) P.items_h.push_back({i, kp, 0, 0});
+    if (solid && g_fold_ready)
+        for (const DPair& pr : P.pairs) {
+            const FoldPairTab& t = g_fold.pair[sh[pr.sa].l][sh[pr.sb].l];
+            P.fold_lcap = std::max(P.fold_lcap, std::max(sh[pr.sa].l, sh[pr.sb].l));
+            P.fold_qcap = std::max(P.fold_qcap, t.maxq + 1);
+            P.fold_wcap = std::max(P.fold_wcap, t.maxw);
+        }
     std::vector<int64_t> cost1, cost2;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -666,8 +679,8 @@ int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector
         const WorkItem* d_ig1 = reinterpret_cast<const WorkItem*>(base + P.off_g1);
         const WorkItem* d_ig2 = reinterpret_cast<const WorkItem*>(base + P.off_g2);
         if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
-        if ((e = launch_pair_h(d_pairs, d_ih, (int)P.items_h.size(), d_sh, d_exps, d_ncoef, ws, ws, solid, status,
-                               st)) != cudaSuccess)
+        if ((e = launch_pair_h(d_pairs, d_ih, (int)P.items_h.size(), d_sh, d_exps, d_ncoef, ws, ws, solid,
+                               P.fold_lcap, P.fold_qcap, P.fold_wcap, status, st)) != cudaSuccess)
             return cuda_fail(e);
         if ((e = tm.end(LX_STAGE_PAIR, 1)) != cudaSuccess) return cuda_fail(e);
         if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
@@ -822,6 +835,8 @@ int stage_release(int dev, int idx, cudaStream_t st, bool enqueued) {
 }  // namespace
 
 namespace lx {
+
+const FoldHost* fold_tables() { return g_fold_ready ? &g_fold : nullptr; }
 
 // lx_eri_batch without the pinned staging: the descriptors are uploaded straight from the
 // planner's host vectors (the copies then wait for the stream).  Allocates nothing.
@@ -1409,9 +1424,17 @@ int lx_hermite_H(const lx_shell* shells, int32_t nshell, const double* exps, con
     const double* d_coefs = reinterpret_cast<const double*>(scratch + o_coefs);
     double* d_ncoef = reinterpret_cast<double*>(scratch + o_ncoef);
     if ((e = launch_norm(d_sh, nshell, d_exps, d_coefs, d_ncoef, status, st)) != cudaSuccess) return cuda_fail(e);
+    int lcap = 0, qcap = 0, wcap = 0;
+    if (solid)
+        for (const DPair& pr : dp) {
+            const FoldPairTab& t = g_fold.pair[shells[pr.sa].l][shells[pr.sb].l];
+            lcap = std::max(lcap, std::max(shells[pr.sa].l, shells[pr.sb].l));
+            qcap = std::max(qcap, t.maxq + 1);
+            wcap = std::max(wcap, t.maxw);
+        }
     if ((e = launch_pair_h(reinterpret_cast<const DPair*>(scratch + o_pairs),
                            reinterpret_cast<const WorkItem*>(scratch + o_items), (int)items.size(), d_sh, d_exps,
-                           d_ncoef, H, reinterpret_cast<double*>(scratch + o_info), solid, status, st)) !=
+                           d_ncoef, H, reinterpret_cast<double*>(scratch + o_info), solid, lcap, qcap, wcap, status, st)) !=
         cudaSuccess)
         return cuda_fail(e);
     if ((e = cudaFreeAsync(scratch, st)) != cudaSuccess) return cuda_fail(e);

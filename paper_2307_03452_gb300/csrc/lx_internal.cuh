@@ -8,15 +8,15 @@
 namespace lx {
 
 constexpr int LMAX = LX_LMAX;                       // largest shell l
-constexpr int LTOT = 4 * LMAX;                      // largest total L of a quartet (24)
-constexpr int NCART_MAX = (LMAX + 1) * (LMAX + 2) / 2;  // 28
-constexpr int NSOL_MAX = 2 * LMAX + 1;              // 13
-constexpr int NHERM_TOT = (LTOT + 1) * (LTOT + 2) * (LTOT + 3) / 6;  // pyr(24) = 2925
+constexpr int LTOT = 4 * LMAX;                      // largest total L of a quartet (28)
+constexpr int NCART_MAX = (LMAX + 1) * (LMAX + 2) / 2;  // 36
+constexpr int NSOL_MAX = 2 * LMAX + 1;              // 15
+constexpr int NHERM_TOT = (LTOT + 1) * (LTOT + 2) * (LTOT + 3) / 6;  // pyr(28) = 4495
 
 // Boys table: F_n(T_k), n = 0..BOYS_NROW-1, T_k = k * BOYS_DT for k = 0..BOYS_NPT-1.
 // Taylor expansion of order BOYS_ORDER-1 around the nearest grid point covers T < BOYS_TMAX.
 constexpr int BOYS_ORDER = 8;
-constexpr int BOYS_NROW = LTOT + BOYS_ORDER;        // 32
+constexpr int BOYS_NROW = LTOT + BOYS_ORDER;        // 36
 constexpr int BOYS_NPT = 361;
 constexpr double BOYS_DT = 0.1;
 constexpr double BOYS_TMAX = 36.0;
@@ -79,7 +79,8 @@ cudaError_t launch_norm(const DShell* sh, int nshell, const double* exps, const 
 // H blocks at ws + h_off, pair scalars at ws_info + info_off.
 cudaError_t launch_pair_h(const DPair* pairs, const WorkItem* items, int nitems, const DShell* sh,
                           const double* exps, const double* ncoef, double* ws, double* ws_info, bool solid,
-                          unsigned* status, cudaStream_t st);
+                          int fold_lcap, int fold_qcap, int fold_wcap, unsigned* status,
+                          cudaStream_t st);  // solid fold: largest l of the pairs, Q and W rows
 cudaError_t launch_boys_r(const DQuartet* qd, const DPair* pairs, const WorkItem* items, int nitems, int lmax,
                           double* ws, unsigned* status, cudaStream_t st);  // lmax: largest L of the items
 // items grouped by tile shape: counts[v] items of shape v, in shape order; counters[v] is the
@@ -118,24 +119,29 @@ constexpr int GEMM_BK = 16;
 // kept.  Each stage's rows are sorted by length and stored in groups of 32 (one per warp):
 // entry j of row 32 g + i is ent[gptr[g] + 32 j + i], for j < (gptr[g+1] - gptr[g]) / 32, and
 // short rows are padded with null entries that multiply by an explicit zero.
-//   Q entry: coefficient index (m_b ncart(lb) + b) | E^y index << 9 | E^z index << 19
+//   Q entry: coefficient index (m_b ncart(lb) + b) | E^y index << 10 | E^z index << 20
 //   W entry: E^x index | Q row << 10
-//   H entry: coefficient index (m_a ncart(la) + a) | W row << 9; h_out[row] = m_a | p << 4
-// E^d index = (i (lb+1) + j) (la+lb+1) + t for exponents (i, j) on a and b.  Coefficient
-// index FOLD_CMAX and Q row FOLD_QMAX hold zeros.
-constexpr int FOLD_QMAX = 3304;   // largest Q row count of one m_b (la = lb = 6)
-constexpr int FOLD_WMAX = 7490;   // largest W row count of one m_b (la = lb = 6)
-constexpr int FOLD_CMAX = NSOL_MAX * NCART_MAX;  // coefficients of one shell (364)
-constexpr int FOLD_QNULL = FOLD_CMAX;                         // Q null entry
-constexpr int FOLD_WNULL = FOLD_QMAX << 10;                   // W null entry
-constexpr int FOLD_HNULL = FOLD_CMAX;                         // H null entry
+//   H entry: coefficient index (m_a ncart(la) + a) | W row << 10; h_out[row] = m_a | p << 4
+// E^d index = (i (lb+1) + j) (la+lb+1) + t for exponents (i, j) on a and b.  Short rows are
+// padded with entries that multiply by a zero: coefficient index (2lb+1) ncart(lb) in a Q
+// row, (2la+1) ncart(la) in an H row (one past each shell's coefficients), Q row maxq of the
+// (la, lb) (the row after its largest Q stage) in a W row.
+constexpr int FOLD_QMAX = 8191;   // bound on the Q rows of one m_b (5688 at la = lb = 7)
+constexpr int FOLD_WMAX = 16383;  // bound on the W rows of one m_b (13542 at la = lb = 7)
+constexpr int FOLD_CMAX = NSOL_MAX * NCART_MAX;  // coefficients of one shell (540 at l = 7)
+static_assert(FOLD_CMAX < 1024 && (LMAX + 1) * (LMAX + 1) * (2 * LMAX + 1) <= 1024, "fold entry fields of 10 bits");
 struct FoldSeg {
     int q_grp0, q_nrow, w_grp0, w_nrow, h_grp0, h_row0;  // first group of each stage; h_out offset
 };
 struct FoldPairTab {
     int seg0;  // segments seg0 .. seg0 + 2 lb (one per m_b)
-    int maxq, maxw;
+    int maxq, maxw;  // largest Q and W row counts over the m_b (Q row maxq is the zero row)
 };
+constexpr int NSOLID_PACKED = [] {
+    int n = 0;
+    for (int l = 0; l <= LMAX; ++l) n += (2 * l + 1) * ((l + 1) * (l + 2) / 2);
+    return n;
+}();  // solid-harmonic coefficients of l = 0..LMAX, packed
 
 // lx_eri_batch with the descriptors uploaded from pageable memory, allocating nothing
 // (lx_api.cu; used by lx_eri_batch_static).
@@ -159,5 +165,7 @@ struct FoldHost {
 };
 // Compressed fold lists for every (la, lb); false if a count exceeds FOLD_QMAX / FOLD_WMAX.
 bool make_fold_lists(const double* coefs, FoldHost& F);
+// The fold tables built once for this process (valid after the first device set-up).
+const FoldHost* fold_tables();
 
 }  // namespace lx

@@ -1,6 +1,7 @@
 // Shell-pair preparation: contraction normalisation and the Hermite-to-Cartesian/solid
 // matrices H of each primitive pair (paper, Section 2: the Gaussian product after
 // Eq. cart2herm-2, the E recursions, and the definition of H).
+#include <algorithm>
 #include <cmath>
 
 #include "lx_internal.cuh"
@@ -9,7 +10,6 @@ namespace lx {
 
 namespace {
 
-constexpr int NSOLID_PACKED = 840;  // sum over l = 0..6 of (2l+1) ncart(l)
 __constant__ double c_solid[NSOLID_PACKED];
 __constant__ int c_solid_off[LMAX + 2];
 __device__ int g_tuv_prep[NHERM_TOT];
@@ -70,10 +70,18 @@ __global__ void norm_kernel(const DShell* __restrict__ sh, int nshell, const dou
 
 constexpr int PAIR_THREADS = 128;
 constexpr int PAIR_SOLID_THREADS = 512;
-constexpr int ETAB = (LMAX + 1) * (LMAX + 1) * (2 * LMAX + 1);  // 637 per direction
-constexpr int FOLD_SMEM_BYTES = (3 * ETAB + 2 * (FOLD_CMAX + 1) + FOLD_QMAX + 1 + FOLD_WMAX) * (int)sizeof(double);
+// E entries per Cartesian direction of a pair with la, lb <= l: (l+1)^2 (2l+1)
+__host__ __device__ constexpr int etab_of(int l) { return (l + 1) * (l + 1) * (2 * l + 1); }
+// solid-harmonic coefficients of one shell of angular momentum l: (2l+1) ncart(l)
+__host__ __device__ constexpr int ncoef_of(int l) { return (2 * l + 1) * (l + 1) * (l + 2) / 2; }
+constexpr int ETAB = etab_of(LMAX);  // 960 per direction
+// shared memory of pair_h_solid_kernel for pairs with la, lb <= lcap and fold capacities qcap
+// (Q rows incl. the zero row) and wcap: E[3][etab], C_a and C_b (each with a trailing zero), Q, W
+inline size_t fold_smem_bytes(int lcap, int qcap, int wcap) {
+    return sizeof(double) * (size_t)(3 * etab_of(lcap) + 2 * (ncoef_of(lcap) + 1) + qcap + wcap);
+}
 
-// Hermite expansion coefficients of primitive pair kp into E[3][ETAB] (zero beyond t <= i+j),
+// Hermite expansion coefficients of primitive pair kp into E[3][etab] (zero beyond t <= i+j),
 // one warp per Cartesian direction, lanes over t:
 //   E^t_{i+1,j} = E^{t-1}_{ij}/(2 zeta_p) + (P - A) E^t_{ij} + (t+1) E^{t+1}_{ij}
 //   E^t_{i,j+1} = E^{t-1}_{ij}/(2 zeta_p) + (P - B) E^t_{ij} + (t+1) E^{t+1}_{ij}
@@ -81,12 +89,12 @@ constexpr int FOLD_SMEM_BYTES = (3 * ETAB + 2 * (FOLD_CMAX + 1) + FOLD_QMAX + 1 
 // *s_pref.  Needs at least 97 threads; ends with a CTA barrier.
 __device__ __forceinline__ void pair_setup(const DPair& pr, int kp, const DShell* __restrict__ sh, const double* __restrict__ exps,
                            const double* __restrict__ ncoef, double* __restrict__ ws_info, double* E,
-                           double* s_pref) {
+                           int etab, double* s_pref) {
     const DShell sa = sh[pr.sa], sb = sh[pr.sb];
     const int la = sa.l, lb = sb.l, nt = la + lb + 1;
     const int ia = kp / sb.K, ib = kp - ia * sb.K;
     const double za = exps[sa.prim_off + ia], zb = exps[sb.prim_off + ib], zp = za + zb;
-    for (int i = threadIdx.x; i < 3 * ETAB; i += blockDim.x) E[i] = 0.0;
+    for (int i = threadIdx.x; i < 3 * etab; i += blockDim.x) E[i] = 0.0;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp < 3) {
@@ -94,7 +102,7 @@ __device__ __forceinline__ void pair_setup(const DPair& pr, int kp, const DShell
         const double Ad = sh[pr.sa].A[d], Bd = sh[pr.sb].A[d];
         const double P = (za * Ad + zb * Bd) / zp;
         const double PA = P - Ad, PB = P - Bd, oo2p = 0.5 / zp;
-        double* Ed = E + d * ETAB;
+        double* Ed = E + d * etab;
 #define EIJ(i, j, t) Ed[((i) * (lb + 1) + (j)) * nt + (t)]
         if (lane == 0) EIJ(0, 0, 0) = 1.0;
         __syncwarp();
@@ -155,7 +163,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) pair_h_kernel(const DPair* __res
     const DPair pr = pairs[it.q];
     const int la = sh[pr.sa].l, lb = sh[pr.sb].l, nt = la + lb + 1;
     const int kp = it.a;
-    pair_setup(pr, kp, sh, exps, ncoef, ws_info, &E[0][0], &s_pref);
+    pair_setup(pr, kp, sh, exps, ncoef, ws_info, &E[0][0], ETAB, &s_pref);
 
     const int np = pr.np;
     const int64_t ldh = (int64_t)pr.Kab * np;
@@ -220,13 +228,14 @@ __device__ __forceinline__ void fold_stage(int grp0, int nrow, const int* __rest
 __global__ void __launch_bounds__(PAIR_SOLID_THREADS, 2) pair_h_solid_kernel(
     const DPair* __restrict__ pairs, const WorkItem* __restrict__ items, const DShell* __restrict__ sh,
     const double* __restrict__ exps, const double* __restrict__ ncoef, double* __restrict__ ws,
-    double* __restrict__ ws_info, unsigned* status) {
+    double* __restrict__ ws_info, int lcap, int qcap, unsigned* status) {
     extern __shared__ double fold_smem[];
-    double* E = fold_smem;
-    double* Csa = E + 3 * ETAB;         // FOLD_CMAX + 1, last entry zero
-    double* Csb = Csa + FOLD_CMAX + 1;  // FOLD_CMAX + 1, last entry zero
-    double* Q = Csb + FOLD_CMAX + 1;    // FOLD_QMAX + 1, last entry zero
-    double* W = Q + FOLD_QMAX + 1;
+    const int etab = etab_of(lcap), ccap = ncoef_of(lcap) + 1;
+    double* E = fold_smem;        // 3 etab
+    double* Csa = E + 3 * etab;   // ccap: C_a, then a zero at ncoef(la)
+    double* Csb = Csa + ccap;     // ccap: C_b, then a zero at ncoef(lb)
+    double* Q = Csb + ccap;       // qcap (>= maxq + 1 of this pair's tables); Q[maxq] zero
+    double* W = Q + qcap;
     __shared__ double s_pref;
     const WorkItem it = items[blockIdx.x];
     const DPair pr = pairs[it.q];
@@ -236,26 +245,26 @@ __global__ void __launch_bounds__(PAIR_SOLID_THREADS, 2) pair_h_solid_kernel(
     for (int i = threadIdx.x; i < (2 * la + 1) * nca; i += blockDim.x) Csa[i] = c_solid[c_solid_off[la] + i];
     for (int i = threadIdx.x; i < nsb * ncb; i += blockDim.x) Csb[i] = c_solid[c_solid_off[lb] + i];
     if (threadIdx.x == 0) {
-        Csa[FOLD_CMAX] = 0.0;
-        Csb[FOLD_CMAX] = 0.0;
-        Q[FOLD_QMAX] = 0.0;
+        Csa[ncoef_of(la)] = 0.0;
+        Csb[ncoef_of(lb)] = 0.0;
+        Q[c_fold.pair[la][lb].maxq] = 0.0;
     }
-    pair_setup(pr, kp, sh, exps, ncoef, ws_info, E, &s_pref);
+    pair_setup(pr, kp, sh, exps, ncoef, ws_info, E, etab, &s_pref);
 
     const int np = pr.np;
     const int64_t ldh = (int64_t)pr.Kab * np;
     double* H = ws + pr.h_off + (int64_t)kp * np;
     const double pref = s_pref;
     const double* Ex = E;
-    const double* Ey = E + ETAB;
-    const double* Ez = E + 2 * ETAB;
+    const double* Ey = E + etab;
+    const double* Ez = E + 2 * etab;
     const FoldPairTab tab = c_fold.pair[la][lb];
     const FoldSeg* segs = c_fold.segs + tab.seg0;
     const int* __restrict__ h_out = c_fold.h_out;
     const int hrows = (2 * la + 1) * np;
     const bool sign = pr.sign;
 
-    auto q_term = [=](int x) { return Csb[x & 511] * Ey[(x >> 9) & 1023] * Ez[x >> 19]; };
+    auto q_term = [=](int x) { return Csb[x & 1023] * Ey[(x >> 10) & 1023] * Ez[x >> 20]; };
     auto q_store = [=](int r, double v) { Q[r] = v; };
     fold_stage(segs[0].q_grp0, segs[0].q_nrow, c_fold.q_gptr, c_fold.q_ent, q_term, q_store);
     __syncthreads();
@@ -265,7 +274,7 @@ __global__ void __launch_bounds__(PAIR_SOLID_THREADS, 2) pair_h_solid_kernel(
                    [=](int x) { return Ex[x & 1023] * Q[x >> 10]; }, [=](int r, double v) { W[r] = v; });
         __syncthreads();
         const int h_row0 = sg->h_row0;
-        fold_stage(sg->h_grp0, hrows, c_fold.h_gptr, c_fold.h_ent, [=](int x) { return Csa[x & 511] * W[x >> 9]; },
+        fold_stage(sg->h_grp0, hrows, c_fold.h_gptr, c_fold.h_ent, [=](int x) { return Csa[x & 1023] * W[x >> 10]; },
                    [=](int r, double v) {
                        const int o = __ldg(&h_out[h_row0 + r]);
                        const int ma = o & 15, p = o >> 4;
@@ -311,8 +320,14 @@ cudaError_t init_prep_tables(const double* host_coefs, const int* host_tuv, cons
     for (int a = 0; a <= LMAX; ++a)
         for (int b = 0; b <= LMAX; ++b) d.pair[a][b] = F.pair[a][b];
     if ((e = cudaMemcpyToSymbol(c_fold, &d, sizeof(d))) != cudaSuccess) return e;
+    int qmax = 0, wmax = 0;
+    for (int a = 0; a <= LMAX; ++a)
+        for (int b = 0; b <= LMAX; ++b) {
+            qmax = std::max(qmax, F.pair[a][b].maxq + 1);
+            wmax = std::max(wmax, F.pair[a][b].maxw);
+        }
     if ((e = cudaFuncSetAttribute(pair_h_solid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  FOLD_SMEM_BYTES)) != cudaSuccess)
+                                  (int)fold_smem_bytes(LMAX, qmax, wmax))) != cudaSuccess)
         return e;
     return cudaMemcpyToSymbol(g_tuv_prep, host_tuv, sizeof(int) * NHERM_TOT);
 }
@@ -326,12 +341,13 @@ cudaError_t launch_norm(const DShell* sh, int nshell, const double* exps, const 
 
 cudaError_t launch_pair_h(const DPair* pairs, const WorkItem* items, int nitems, const DShell* sh,
                           const double* exps, const double* ncoef, double* ws, double* ws_info, bool solid,
-                          unsigned* status, cudaStream_t st) {
+                          int fold_lcap, int fold_qcap, int fold_wcap, unsigned* status, cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
-    if (solid)
-        pair_h_solid_kernel<<<nitems, PAIR_SOLID_THREADS, FOLD_SMEM_BYTES, st>>>(pairs, items, sh, exps, ncoef, ws,
-                                                                                ws_info, status);
-    else
+    if (solid) {
+        if (fold_lcap < 0 || fold_lcap > LMAX) return cudaErrorInvalidValue;
+        pair_h_solid_kernel<<<nitems, PAIR_SOLID_THREADS, fold_smem_bytes(fold_lcap, fold_qcap, fold_wcap), st>>>(
+            pairs, items, sh, exps, ncoef, ws, ws_info, fold_lcap, fold_qcap, status);
+    } else
         pair_h_kernel<<<nitems, PAIR_THREADS, 0, st>>>(pairs, items, sh, exps, ncoef, ws, ws_info, status);
     return cudaGetLastError();
 }

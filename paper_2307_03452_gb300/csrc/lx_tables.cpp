@@ -165,6 +165,8 @@ std::vector<int> emit_groups(const std::vector<std::vector<int>>& rows, int null
 
 }  // namespace
 
+constexpr int W_PLACEHOLDER = -1;  // never a real W entry (those are non-negative)
+
 bool make_fold_lists(const double* coefs, FoldHost& F) {
     F.q_gptr.assign(1, 0);
     F.w_gptr.assign(1, 0);
@@ -198,6 +200,7 @@ bool make_fold_lists(const double* coefs, FoldHost& F) {
             FoldPairTab& tab = F.pair[la][lb];
             tab.seg0 = (int)F.segs.size();
             tab.maxq = tab.maxw = 0;
+            const size_t w_first = F.w_ent.size();
             for (int mb = 0; mb < nsb; ++mb) {
                 FoldSeg sg{};
                 sg.q_grp0 = (int)F.q_gptr.size() - 1;
@@ -215,8 +218,8 @@ bool make_fold_lists(const double* coefs, FoldHost& F) {
                                 for (int by = 0; by <= lb - bx; ++by) {
                                     const int bz = lb - bx - by, b = bidx[bx * (lb + 1) + by];
                                     if (std::fabs(Cb[mb * ncb + b]) <= 1e-14 || u > y + by || v > z + bz) continue;
-                                    row.push_back((mb * ncb + b) | (((y * sb1 + by) * nt + u) << 9) |
-                                                  (((z * sb1 + bz) * nt + v) << 19));
+                                    row.push_back((mb * ncb + b) | (((y * sb1 + by) * nt + u) << 10) |
+                                                  (((z * sb1 + bz) * nt + v) << 20));
                                 }
                                 if (row.empty()) continue;
                                 qkey.emplace_back(y, z, bx, u, v);
@@ -224,7 +227,8 @@ bool make_fold_lists(const double* coefs, FoldHost& F) {
                             }
                 sg.q_nrow = (int)qkey.size();
                 if (sg.q_nrow > FOLD_QMAX) return false;
-                const std::vector<int> qpos = emit_groups(qrows, FOLD_QNULL, F.q_gptr, F.q_ent);
+                // padding entries take the zero stored after C_b (coefficient index nsb ncb)
+                const std::vector<int> qpos = emit_groups(qrows, nsb * ncb, F.q_gptr, F.q_ent);
                 // W rows, keyed (a, p)
                 std::vector<std::vector<int>> wrows;
                 std::vector<int> wrow((size_t)nca * np, -1);
@@ -244,7 +248,8 @@ bool make_fold_lists(const double* coefs, FoldHost& F) {
                 }
                 sg.w_nrow = (int)wrows.size();
                 if (sg.w_nrow > FOLD_WMAX) return false;
-                const std::vector<int> wpos = emit_groups(wrows, FOLD_WNULL, F.w_gptr, F.w_ent);
+                // padding entries point at the zero Q row, known once every m_b is built
+                const std::vector<int> wpos = emit_groups(wrows, W_PLACEHOLDER, F.w_gptr, F.w_ent);
                 // H rows (m_a, p); the output position travels with the row
                 std::vector<std::vector<int>> hrows;
                 std::vector<int> hkey;
@@ -254,12 +259,13 @@ bool make_fold_lists(const double* coefs, FoldHost& F) {
                         for (int a = 0; a < nca; ++a) {
                             const int w = wrow[(size_t)a * np + p];
                             if (w < 0 || std::fabs(Ca[ma * nca + a]) <= 1e-14) continue;
-                            row.push_back((ma * nca + a) | (wpos[w] << 9));
+                            row.push_back((ma * nca + a) | (wpos[w] << 10));
                         }
                         hrows.push_back(std::move(row));
                         hkey.push_back(ma | (p << 4));
                     }
-                const std::vector<int> hpos = emit_groups(hrows, FOLD_HNULL, F.h_gptr, F.h_ent);
+                // padding entries take the zero stored after C_a (coefficient index nsa nca)
+                const std::vector<int> hpos = emit_groups(hrows, nsa * nca, F.h_gptr, F.h_ent);
                 std::vector<int> out(hrows.size());
                 for (size_t i = 0; i < hrows.size(); ++i) out[hpos[i]] = hkey[i];
                 F.h_out.insert(F.h_out.end(), out.begin(), out.end());
@@ -267,6 +273,8 @@ bool make_fold_lists(const double* coefs, FoldHost& F) {
                 tab.maxw = std::max(tab.maxw, sg.w_nrow);
                 F.segs.push_back(sg);
             }
+            for (size_t i = w_first; i < F.w_ent.size(); ++i)
+                if (F.w_ent[i] == W_PLACEHOLDER) F.w_ent[i] = tab.maxq << 10;  // E^x[0] times the zero row
         }
     return ok;
 }

@@ -18,7 +18,7 @@ from __future__ import annotations
 
 import numpy as np
 
-L_OF = {"s": 0, "p": 1, "d": 2, "f": 3, "g": 4, "h": 5, "i": 6}
+L_OF = {"s": 0, "p": 1, "d": 2, "f": 3, "g": 4, "h": 5, "i": 6, "k": 7}
 
 #: the mixed classes of the batched workload: (gg|gg), (hh|hh), (ii|ii), (gh|ii), (gi|hh)
 MIXED_CLASSES = [(4, 4, 4, 4), (5, 5, 5, 5), (6, 6, 6, 6), (4, 5, 6, 6), (4, 6, 5, 5)]

@@ -22,7 +22,7 @@ assert SHELL_DTYPE.itemsize == 40 and QUARTET_DTYPE.itemsize == 24
 LX_CART = 0x0
 LX_SOLID = 0x1
 LX_KET_SIGN = 0x100  # lx_hermite_H: multiply column p by (-1)^|p|
-LMAX = 6
+LMAX = 7
 KMAX = 16
 
 _lock = threading.Lock()

@@ -58,7 +58,7 @@ def _call_batch(b, q, flags=lx.LX_SOLID, shells=None, exps=None, coefs=None, qua
 def test_rejects_bad_angular_momentum():
     b, q = _batch()
     sh = lx.pack_shells(b)
-    sh["l"][1] = 7
+    sh["l"][1] = 8
     assert _call_batch(b, q, shells=sh) == -2
     sh["l"][1] = -1
     assert _call_batch(b, q, shells=sh) == -2

@@ -158,7 +158,7 @@ def random_quartet(ls, seed, K=2, spread=2.5):
     return centers, exps, coefs
 
 
-@pytest.mark.parametrize("ls", [(2, 1, 3, 0), (4, 5, 6, 4), (3, 3, 2, 2)])
+@pytest.mark.parametrize("ls", [(2, 1, 3, 0), (4, 5, 6, 4), (3, 3, 2, 2), (7, 3, 7, 1)])
 def test_eightfold_symmetry(ls):
     centers, exps, coefs = random_quartet(ls, 11, K=2 if sum(ls) < 16 else 1)
     ref = eri4(ls, centers, exps, coefs)
@@ -266,7 +266,8 @@ def test_center_derivative_identity(ls):
 
 
 @pytest.mark.parametrize("ls,K", [((1, 2, 0, 3), 3), ((3, 3, 3, 3), 2), ((4, 4, 4, 4), 2), ((5, 5, 5, 5), 1),
-                                  ((4, 5, 6, 6), 1), ((4, 6, 5, 5), 1), ((6, 6, 6, 6), 1)])
+                                  ((4, 5, 6, 6), 1), ((4, 6, 5, 5), 1), ((6, 6, 6, 6), 1),
+                                  ((7, 2, 5, 6), 1), ((7, 7, 7, 7), 1)])
 @pytest.mark.parametrize("seed", [0, 1])
 def test_md_matches_obara_saika(ls, K, seed):
     # The horizontal recursion of the Obara-Saika route cancels badly for separated centers

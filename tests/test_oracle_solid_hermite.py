@@ -75,7 +75,7 @@ def test_solid_harmonic_m_convention(l):
     assert C[l][comps.index((0, 0, l))] > 0
 
 
-@pytest.mark.parametrize("la,lb", [(0, 0), (1, 0), (2, 3), (4, 4), (6, 6), (5, 2)])
+@pytest.mark.parametrize("la,lb", [(0, 0), (1, 0), (2, 3), (4, 4), (6, 6), (5, 2), (7, 7), (3, 7)])
 def test_hermite_expansion_reproduces_product(la, lb):
     # (x-A)^i (x-B)^j exp(-za (x-A)^2 - zb (x-B)^2)
     #   = exp(-mu AB^2) sum_t E^t_ij  d^t/dP^t exp(-zp (x-P)^2),
@@ -101,7 +101,7 @@ def test_hermite_expansion_reproduces_product(la, lb):
             assert np.all(E[i, j, i + j + 1:] == 0)
 
 
-@pytest.mark.parametrize("l,K", [(0, 1), (0, 3), (2, 2), (4, 5), (6, 3)])
+@pytest.mark.parametrize("l,K", [(0, 1), (0, 3), (2, 2), (4, 5), (6, 3), (7, 4)])
 def test_contraction_normalisation(l, K):
     # the normalised contracted x^l exp(-zeta r^2) has unit self-overlap (Gauss-Hermite)
     rng = np.random.default_rng(l * 10 + K)
