@@ -48,6 +48,7 @@ def parse_args(argv=None):
     p.add_argument("--no-split-config", action="store_true",
                    help="skip the (hh|hh)+(ii|ii) K=1..3 split-path workload")
     p.add_argument("--no-routed", action="store_true", help="skip the routed-workload sample")
+    p.add_argument("--no-pairs", action="store_true", help="skip the bra-list x ket-list (engine form) workload")
     p.add_argument("--routed-quartets", type=int, default=4000)
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
     p.add_argument("--sweep", action="store_true",
@@ -563,6 +564,33 @@ def main(argv=None):
             del rout, fout
             torch.cuda.empty_cache()
 
+    # ---- engine form: 64 (ii) bra pairs x 64 (ii) ket pairs, each pair's H (and digit planes)
+    # built once and shared by its 64 quartets
+    pairs = None
+    if not args.no_pairs:
+        pbas, pbra, pket = inputs.iiii_pairs()
+        pq = [(a, b, c, d) for (a, b) in pbra for (c, d) in pket]
+        pg1, pg2, _ = gemm_flops(pbas, pq, True)
+        pairs = {"workload": f"{len(pbra)} (ii) bra pairs x {len(pket)} (ii) ket pairs = {len(pq)} quartets, K = 1, "
+                             "20-bohr cube, exponents log-uniform [0.05, 20], solid harmonics (lx_eri_pairs)"}
+        for path in ("fp64", "split"):
+            pb = lx.PairBatch(pbas, pbra, pket, True, path=path)
+            outp = torch.empty(pb.out_size, dtype=torch.float64, device="cuda")
+            wsp = lx.alloc_workspace(pb.workspace_size())
+            pms, pstage, _ = time_steps(torch, lx, pb, outp, wsp, max(2, min(args.steps, 3)), 2, flush_buf, world)
+            ptot = reduce_max(sum(pms), world)
+            nst = len(pms)
+            pairs[path] = {"quartets_per_s": world * len(pq) * nst / (ptot * 1e-3), "ms_per_step": ptot / nst,
+                           "fp64_equiv_tflops": world * (pg1 + pg2) * nst / (ptot * 1e-3) / 1e12,
+                           "stage_ms_per_step": {k: v / nst for k, v in pstage.items()}}
+            if path == "fp64":
+                ref_p = outp
+            else:
+                pairs["split"]["max_abs_diff_vs_fp64_path"] = float((outp - ref_p).abs().max())
+            del wsp
+        del ref_p, outp
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
         cpu = cpu_baseline(basis, quartets, True, args.cpu_seconds)
@@ -579,7 +607,7 @@ def main(argv=None):
             "fp64_equiv_tflops": fp64_tf, "integrals_per_s": world * nint * args.steps / (total_ms * 1e-3),
             "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
             "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "cartesian": cart,
-            "split": split, "mixed": mixed, "split_config": split_cfg, "routed": routed,
+            "split": split, "mixed": mixed, "split_config": split_cfg, "routed": routed, "pairs": pairs,
             "gpu_launches": int(sum(launches.values())),
         }
         print(json.dumps(line), flush=True)

@@ -102,6 +102,7 @@ typedef struct {
 #define LX_ERR_STATIC_SCRATCH (-11) /* lx_eri_batch_static: the batch needs more scratch than
                                        LX_STATIC_SCRATCH_BYTES even one quartet at a time */
 #define LX_ERR_NO_ROUTER (-12)    /* LX_PATH_ROUTED on a device without lx_router_set */
+#define LX_ERR_PAIR_CLASS (-13)   /* lx_eri_pairs*: the bra (or ket) pairs differ in (l, l') */
 
 /*
  * Number of doubles the output buffer needs: max over quartets of out_offset + block size.
@@ -141,6 +142,30 @@ int64_t lx_eri_workspace_min(const lx_shell* shells, int32_t nshell, const lx_qu
 int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
                  int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags, double* out,
                  void* workspace, size_t workspace_bytes, void* cuda_stream);
+
+/*
+ * Bra-list x ket-list form (Section 3, the library interface): (ab|cd) for every bra pair i
+ * and every ket pair j.
+ *   bra_pairs[2 nbra], ket_pairs[2 nket]: HOST int32 shell indices (a, b) and (c, d).  Every
+ *     bra pair has the same (l_a, l_b) and every ket pair the same (l_c, l_d)
+ *     (LX_ERR_PAIR_CLASS otherwise); contraction degrees may differ.
+ *   out: DEVICE, dense [nbra][nket][n_ab][n_cd] (n(l) functions per shell as for
+ *     lx_eri_batch), lx_eri_pairs_out_size = nbra nket n_ab n_cd doubles.
+ * Otherwise as lx_eri_batch, which it calls with the quartets (i | j) in bra-major order:
+ * within one chunk of the workspace every pair's H matrix (and, on the split path, its
+ * column scales and BF16 digit planes) is built once and shared by all the chunk's quartets
+ * that contain the pair.  nbra nket <= LX_PAIRS_MAX_QUARTETS (LX_ERR_SIZE otherwise).
+ */
+#define LX_PAIRS_MAX_QUARTETS (1ll << 28)
+int64_t lx_eri_pairs_out_size(const lx_shell* shells, int32_t nshell, const int32_t* bra_pairs, int64_t nbra,
+                              const int32_t* ket_pairs, int64_t nket, int32_t flags);
+int64_t lx_eri_pairs_workspace_size(const lx_shell* shells, int32_t nshell, const int32_t* bra_pairs, int64_t nbra,
+                                    const int32_t* ket_pairs, int64_t nket, int32_t flags);
+int64_t lx_eri_pairs_workspace_min(const lx_shell* shells, int32_t nshell, const int32_t* bra_pairs, int64_t nbra,
+                                   const int32_t* ket_pairs, int64_t nket, int32_t flags);
+int lx_eri_pairs(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs, int32_t nprim_total,
+                 const int32_t* bra_pairs, int64_t nbra, const int32_t* ket_pairs, int64_t nket, int32_t flags,
+                 double* out, void* workspace, size_t workspace_bytes, void* cuda_stream);
 
 /*
  * lx_eri_batch without a workspace argument, for callers that cannot allocate device memory

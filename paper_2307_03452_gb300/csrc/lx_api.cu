@@ -207,18 +207,15 @@ size_t quartet_bytes(const lx_shell* sh, const lx_quartet& q, int flags) {
         items += ((nab + 31) / 32) * ((n1 + 31) / 32);
         items += ((nab + 31) / 32) * ((ncd + 31) / 32);
     } else {
+        // [p|q]^T and X digit planes; H's go with the pair (pair_bytes)
         const int k1 = (int)(kbra * np), k2 = (int)n1;
-        const int ra1 = split_rowpad(k2, SPLIT_TA), rb1 = split_rowpad((int)nab, SPLIT_TB);
-        const int ra2 = split_rowpad((int)nab, SPLIT_TA), rb2 = split_rowpad((int)ncd, SPLIT_TB);
-        const int c1 = (k1 + 127) / 128, c2 = (k2 + 127) / 128;
-        items += ra1 + rb1 + ra2 + rb2 + c1 + c2;
+        const int ra1 = split_rowpad(k2, SPLIT_TA), ra2 = split_rowpad((int)nab, SPLIT_TA);
+        items += (ra1 + ra2) / 8;
         items += (ra1 / SPLIT_TA) * ((nab + SPLIT_TB - 1) / SPLIT_TB);
         items += (ra2 / SPLIT_TA) * ((ncd + SPLIT_TB - 1) / SPLIT_TB);
-        bytes += sizeof(SplitQuartet) + 2 * sizeof(SplitGemmDesc) + 3 * sizeof(SplitRowsDesc) +
-                 2 * sizeof(ColMaxDesc);
-        bytes += (size_t)split_dig_bytes(k2, k1, SPLIT_TA) + (size_t)split_dig_bytes((int)nab, k1, SPLIT_TB);
-        bytes += (size_t)split_dig_bytes((int)nab, k2, SPLIT_TA) + (size_t)split_dig_bytes((int)ncd, k2, SPLIT_TB);
-        bytes += 4 * (size_t)(ra1 + rb1 + ra2 + rb2) + 4 * (size_t)(k1 + k2) + 12 * 256;
+        bytes += sizeof(SplitQuartet) + 2 * sizeof(SplitGemmDesc) + sizeof(SplitRowsDesc);
+        bytes += (size_t)split_dig_bytes(k2, k1, SPLIT_TA) + (size_t)split_dig_bytes((int)nab, k2, SPLIT_TA);
+        bytes += 4 * (size_t)(ra1 + ra2) + 4 * 256;
     }
     return bytes + items * sizeof(WorkItem);
 }
@@ -228,10 +225,16 @@ size_t pair_bytes(const lx_shell* sh, int sa, int sb, int flags) {
     const lx_shell &a = sh[sa], &b = sh[sb];
     const int64_t kab = (int64_t)a.nprim * b.nprim;
     const int64_t rows = (int64_t)nfun(a.l, solid) * nfun(b.l, solid);
-    // the split path keeps the digit planes of H with each quartet (they could be shared by
-    // the quartets of one pair, since H's column scales depend on H alone)
-    (void)split;
-    return sizeof(DPair) + kab * sizeof(WorkItem) + 8 * (size_t)(kab * 4 + rows * kab * pyr(a.l + b.l)) + 512;
+    const int64_t k = kab * pyr(a.l + b.l);
+    size_t bytes = sizeof(DPair) + kab * sizeof(WorkItem) + 8 * (size_t)(kab * 4 + rows * k) + 512;
+    if (split) {
+        // H's digit planes (rows padded to at most SPLIT_TB), row exponents, column scales
+        const int rp = split_rowpad((int)rows, SPLIT_TB);
+        bytes += sizeof(SplitRowsDesc) + sizeof(ColMaxDesc) + (size_t)split_dig_bytes((int)rows, (int)k, SPLIT_TB);
+        bytes += 4 * (size_t)(rp + k) + 3 * 256;
+        bytes += sizeof(WorkItem) * (size_t)(rp / 8 + (k + 127) / 128);
+    }
+    return bytes;
 }
 
 constexpr size_t CHUNK_SLACK = 32 * 256;  // alignment padding of the chunk's regions and the work counters
@@ -411,32 +414,34 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     lpt(P.items_g1, cost1, P.g1_counts);
     lpt(P.items_g2, cost2, P.g2_counts);
     if (split) {
-        // split descriptors and work lists (offsets filled in below, with the data layout)
+        // split descriptors and work lists (offsets filled in below, with the data layout).
+        // H's column scales depend on H alone, so each pair's scales and digit planes are made
+        // once per chunk and shared by its quartets: descriptor p (< npair) splits H of pair
+        // p, descriptor npair + i splits X of quartet i.
+        const int npair = (int)P.pairs.size();
+        for (int p = 0; p < npair; ++p) {
+            const DPair& pr = P.pairs[p];
+            const int k = pr.Kab * pr.np, tb = split_tb(pr.nrow);
+            // columns scaled into (-1, 1): one pass, e = 0 per row
+            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k, pr.nrow, k, tb, split_nkb(k), -1, 1, 0});
+            P.cmd.push_back(ColMaxDesc{0, 0, k, pr.nrow, k, 0});
+            for (int c = 0; c < (k + 127) / 128; ++c) P.items_cA.push_back({p, c, 0, 0});
+            // digit kernels: one item per 8 consecutive rows (every row tile is a multiple of 8)
+            for (int row = 0; row < split_rowpad(pr.nrow, tb); row += 8) P.items_sB.push_back({p, row, 0, 0});
+        }
         for (int i = 0; i < (int)P.quartets.size(); ++i) {
             const DQuartet& d = P.quartets[i];
             const int k1 = d.kbra * d.np, k2 = d.kket * d.nq;
-            const int c1 = (k1 + 127) / 128, c2 = (k2 + 127) / 128;
             SplitQuartet q{};
             q.nkb1 = split_nkb(k1);
             q.nkb2 = split_nkb(k2);
             P.sq.push_back(q);
-            const int sb1 = (int)P.srd.size();
             const int tb1 = split_tb(d.nab), tb2 = split_tb(d.ncd);
-            // H_bra and H_ket columns scaled into (-1, 1): one pass, e = 0 per row
-            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k1, d.nab, k1, tb1, q.nkb1, -1, 1, 0});        // B1: H_bra
-            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k2, d.nab, k2, SPLIT_TA, q.nkb2, +1, 0, 0});   // A2: X
-            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k2, d.ncd, k2, tb2, q.nkb2, -1, 1, 0});        // B2: H_ket
-            const int c0 = (int)P.cmd.size();
-            P.cmd.push_back(ColMaxDesc{0, 0, k1, d.nab, k1, 0});  // c1: column scales of H_bra
-            P.cmd.push_back(ColMaxDesc{0, 0, k2, d.ncd, k2, 0});  // c2: column scales of H_ket
-            for (int c = 0; c < c1; ++c) P.items_cA.push_back({c0, c, 0, 0});
-            for (int c = 0; c < c2; ++c) P.items_cA.push_back({c0 + 1, c, 0, 0});
-            // digit kernels: one item per 8 consecutive rows (every row tile is a multiple of 8)
+            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k2, d.nab, k2, SPLIT_TA, q.nkb2, +1, 0, 0});  // A2: X
             for (int row = 0; row < split_rowpad(k2, SPLIT_TA); row += 8) P.items_sr.push_back({i, row, 0, 0});
-            // H_bra and H_ket digit planes go with the GEMM1 operands; X's only after GEMM1
-            for (int row = 0; row < split_rowpad(d.nab, tb1); row += 8) P.items_sB.push_back({sb1, row, 0, 0});
-            for (int row = 0; row < split_rowpad(d.ncd, tb2); row += 8) P.items_sB.push_back({sb1 + 2, row, 0, 0});
-            for (int row = 0; row < split_rowpad(d.nab, SPLIT_TA); row += 8) P.items_sD.push_back({sb1 + 1, row, 0, 0});
+            // X's digit planes only after GEMM1
+            for (int row = 0; row < split_rowpad(d.nab, SPLIT_TA); row += 8)
+                P.items_sD.push_back({npair + i, row, 0, 0});
             const int mt1 = split_rowpad(k2, SPLIT_TA) / SPLIT_TA, nt1 = (d.nab + tb1 - 1) / tb1;
             const int mt2 = split_rowpad(d.nab, SPLIT_TA) / SPLIT_TA, nt2 = (d.ncd + tb2 - 1) / tb2;
             for (int m = 0; m < mt1; ++m)
@@ -492,39 +497,38 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     }
     if (split) {
         auto take_bytes = [&](int64_t bytes) { return 8 * take((bytes + 7) / 8); };
+        const int npair = (int)P.pairs.size();
+        for (int p = 0; p < npair; ++p) {
+            const DPair& pr = P.pairs[p];
+            const int k = pr.Kab * pr.np, tb = split_tb(pr.nrow);
+            SplitRowsDesc& r = P.srd[p];
+            r.src_off = pr.h_off;
+            r.dig_off = take_bytes(split_dig_bytes(pr.nrow, k, tb));
+            r.exp_off = take_bytes(4 * (int64_t)split_rowpad(pr.nrow, tb));
+            r.shift_off = take_bytes(4 * (int64_t)k);
+            P.cmd[p].src_off = pr.h_off;
+            P.cmd[p].out_off = r.shift_off;
+        }
         for (size_t i = 0; i < P.quartets.size(); ++i) {
             const DQuartet& d = P.quartets[i];
             SplitQuartet& q = P.sq[i];
             const int k1 = d.kbra * d.np, k2 = d.kket * d.nq;
+            const SplitRowsDesc &hb = P.srd[d.pb], &hk = P.srd[d.pk];
             q.a1_dig = take_bytes(split_dig_bytes(k2, k1, SPLIT_TA));
             q.a1_exp = take_bytes(4 * (int64_t)split_rowpad(k2, SPLIT_TA));
-            q.b1_dig = take_bytes(split_dig_bytes(d.nab, k1, split_tb(d.nab)));
-            q.b1_exp = take_bytes(4 * (int64_t)split_rowpad(d.nab, split_tb(d.nab)));
+            q.b1_dig = hb.dig_off;
+            q.b1_exp = hb.exp_off;
             q.a2_dig = take_bytes(split_dig_bytes(d.nab, k2, SPLIT_TA));
             q.a2_exp = take_bytes(4 * (int64_t)split_rowpad(d.nab, SPLIT_TA));
-            q.b2_dig = take_bytes(split_dig_bytes(d.ncd, k2, split_tb(d.ncd)));
-            q.b2_exp = take_bytes(4 * (int64_t)split_rowpad(d.ncd, split_tb(d.ncd)));
-            q.c1_off = take_bytes(4 * (int64_t)k1);
-            q.c2_off = take_bytes(4 * (int64_t)k2);
-            const DPair &pb = P.pairs[d.pb], &pk = P.pairs[d.pk];
-            SplitRowsDesc* r = &P.srd[3 * i];
-            r[0].src_off = pb.h_off;
-            r[0].dig_off = q.b1_dig;
-            r[0].exp_off = q.b1_exp;
-            r[0].shift_off = q.c1_off;
-            r[1].src_off = d.x_off;
-            r[1].dig_off = q.a2_dig;
-            r[1].exp_off = q.a2_exp;
-            r[1].shift_off = q.c2_off;
-            r[2].src_off = pk.h_off;
-            r[2].dig_off = q.b2_dig;
-            r[2].exp_off = q.b2_exp;
-            r[2].shift_off = q.c2_off;
-            ColMaxDesc* c = &P.cmd[2 * i];
-            c[0].src_off = pb.h_off;
-            c[0].out_off = q.c1_off;
-            c[1].src_off = pk.h_off;
-            c[1].out_off = q.c2_off;
+            q.b2_dig = hk.dig_off;
+            q.b2_exp = hk.exp_off;
+            q.c1_off = hb.shift_off;
+            q.c2_off = hk.shift_off;
+            SplitRowsDesc& rx = P.srd[npair + i];
+            rx.src_off = d.x_off;
+            rx.dig_off = q.a2_dig;
+            rx.exp_off = q.a2_exp;
+            rx.shift_off = q.c2_off;
             SplitGemmDesc g1{};
             g1.a_dig = q.a1_dig;
             g1.a_exp = q.a1_exp;
@@ -904,6 +908,43 @@ int eri_batch_staged(const lx_shell* shells, int32_t nshell, const double* exps,
     v = enqueue_batch(B, head_src, blobs, out, workspace, status, st, (flags & LX_TIME_STAGES) != 0);
     const int r = stage_release(dev, idx, st, true);
     return v != LX_OK ? v : r;
+}
+
+// The quartet list of the bra-list x ket-list form: quartet i nket + j = (bra pair i | ket
+// pair j), output block i nket + j of a dense [nbra][nket][n_ab][n_cd] array.  Checks the
+// shells (without primitives), the pair indices and that each list has one class.
+int expand_pairs(const lx_shell* shells, int32_t nshell, const int32_t* bra, int64_t nbra, const int32_t* ket,
+                 int64_t nket, int32_t flags, std::vector<lx_quartet>& qs) {
+    qs.clear();
+    int v = validate(shells, nshell, nullptr, nullptr, 0, nullptr, 0, flags, false);
+    if (v != LX_OK) return v;
+    if (nbra < 0 || nket < 0) return LX_ERR_SIZE;
+    if (nbra == 0 || nket == 0) return LX_OK;
+    if (!bra || !ket) return LX_ERR_NULL;
+    if (nbra > LX_PAIRS_MAX_QUARTETS / nket) return LX_ERR_SIZE;
+    auto check = [&](const int32_t* pr, int64_t n) {
+        for (int64_t i = 0; i < 2 * n; ++i)
+            if (pr[i] < 0 || pr[i] >= nshell) return LX_ERR_QUARTET;
+        for (int64_t i = 1; i < n; ++i)
+            if (shells[pr[2 * i]].l != shells[pr[0]].l || shells[pr[2 * i + 1]].l != shells[pr[1]].l)
+                return LX_ERR_PAIR_CLASS;
+        return LX_OK;
+    };
+    if ((v = check(bra, nbra)) != LX_OK || (v = check(ket, nket)) != LX_OK) return v;
+    const bool solid = flags & LX_SOLID;
+    const int64_t block = (int64_t)nfun(shells[bra[0]].l, solid) * nfun(shells[bra[1]].l, solid) *
+                          nfun(shells[ket[0]].l, solid) * nfun(shells[ket[1]].l, solid);
+    qs.resize((size_t)(nbra * nket));
+    for (int64_t i = 0; i < nbra; ++i)
+        for (int64_t j = 0; j < nket; ++j) {
+            lx_quartet& q = qs[(size_t)(i * nket + j)];
+            q.s[0] = bra[2 * i];
+            q.s[1] = bra[2 * i + 1];
+            q.s[2] = ket[2 * j];
+            q.s[3] = ket[2 * j + 1];
+            q.out_offset = (i * nket + j) * block;
+        }
+    return LX_OK;
 }
 
 }  // namespace
@@ -1314,6 +1355,40 @@ int lx_eri_stage_times(double* ms, int64_t* launches, int32_t nstage, void* cuda
     return rc;
 }
 
+int64_t lx_eri_pairs_out_size(const lx_shell* shells, int32_t nshell, const int32_t* bra_pairs, int64_t nbra,
+                              const int32_t* ket_pairs, int64_t nket, int32_t flags) {
+    std::vector<lx_quartet> qs;
+    const int v = expand_pairs(shells, nshell, bra_pairs, nbra, ket_pairs, nket, flags, qs);
+    if (v != LX_OK) return v;
+    return qs.empty() ? 0 : lx_eri_out_size(shells, nshell, qs.data(), (int64_t)qs.size(), flags);
+}
+
+int64_t lx_eri_pairs_workspace_size(const lx_shell* shells, int32_t nshell, const int32_t* bra_pairs, int64_t nbra,
+                                    const int32_t* ket_pairs, int64_t nket, int32_t flags) {
+    std::vector<lx_quartet> qs;
+    const int v = expand_pairs(shells, nshell, bra_pairs, nbra, ket_pairs, nket, flags, qs);
+    if (v != LX_OK) return v;
+    return lx_eri_workspace_size(shells, nshell, qs.data(), (int64_t)qs.size(), flags);
+}
+
+int64_t lx_eri_pairs_workspace_min(const lx_shell* shells, int32_t nshell, const int32_t* bra_pairs, int64_t nbra,
+                                   const int32_t* ket_pairs, int64_t nket, int32_t flags) {
+    std::vector<lx_quartet> qs;
+    const int v = expand_pairs(shells, nshell, bra_pairs, nbra, ket_pairs, nket, flags, qs);
+    if (v != LX_OK) return v;
+    return lx_eri_workspace_min(shells, nshell, qs.data(), (int64_t)qs.size(), flags);
+}
+
+int lx_eri_pairs(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs, int32_t nprim_total,
+                 const int32_t* bra_pairs, int64_t nbra, const int32_t* ket_pairs, int64_t nket, int32_t flags,
+                 double* out, void* workspace, size_t workspace_bytes, void* cuda_stream) {
+    std::vector<lx_quartet> qs;
+    const int v = expand_pairs(shells, nshell, bra_pairs, nbra, ket_pairs, nket, flags, qs);
+    if (v != LX_OK) return v;
+    return lx_eri_batch(shells, nshell, exps, coefs, nprim_total, qs.data(), (int64_t)qs.size(), flags, out,
+                        workspace, workspace_bytes, cuda_stream);
+}
+
 const char* lx_strerror(int code) {
     switch (code) {
         case LX_OK: return "success";
@@ -1328,6 +1403,8 @@ const char* lx_strerror(int code) {
         case LX_ERR_DEVICE_STATUS: return "a kernel reported a bad index or input";
         case LX_ERR_SIZE: return "a size argument is negative or too large";
         case LX_ERR_STATIC_SCRATCH: return "batch needs more scratch than the static array of lx_eri_batch_static holds";
+        case LX_ERR_NO_ROUTER: return "LX_PATH_ROUTED without a routing network (lx_router_set)";
+        case LX_ERR_PAIR_CLASS: return "a pair list mixes angular momenta (every bra pair, and every ket pair, needs the same (l, l'))";
         default: return "unknown error code";
     }
 }

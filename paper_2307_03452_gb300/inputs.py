@@ -164,6 +164,27 @@ def split_hhhh_iiii(nquartet_each=16384, seed=2310):
     return concat([(b1, q1), (b2, q2)])
 
 
+def pair_lists(cls, nbra, nket, seed, cube=20.0, exps=(0.05, 20.0), kmin=1, kmax=1):
+    """Bra-list x ket-list workload (the engine form): nbra pairs of shells with angular
+    momenta (cls[0], cls[1]) and nket pairs with (cls[2], cls[3]), every shell its own,
+    centers uniform in a cube of side `cube` bohr, exponents log-uniform in `exps`, degree per
+    shell uniform in kmin..kmax.  Returns (basis, bra_pairs, ket_pairs)."""
+    rng = np.random.default_rng(seed)
+    ls = [cls[0], cls[1]] * nbra + [cls[2], cls[3]] * nket
+    ks = rng.integers(kmin, kmax + 1, len(ls))
+    centers = rng.uniform(0.0, cube, (len(ls), 3))
+    basis = _assemble(ls, ks, centers, exps[0], exps[1], rng, kmax > 1)
+    bra = np.arange(2 * nbra, dtype=np.int32).reshape(-1, 2)
+    ket = (2 * nbra + np.arange(2 * nket, dtype=np.int32)).reshape(-1, 2)
+    return basis, bra, ket
+
+
+def iiii_pairs(nbra=64, nket=64, seed=2312):
+    """(ii|ii) in the engine form: 64 bra pairs x 64 ket pairs = 4096 quartets, K = 1,
+    20-bohr cube, exponents in [0.05, 20] (the headline class and size)."""
+    return pair_lists((6, 6, 6, 6), nbra, nket, seed)
+
+
 def routed(nquartet=1_000_000, seed=2311):
     """l = 4..6, K = 1..5, bra-ket separations 0-30 bohr (magnitudes over many decades)."""
     return spread_distances(nquartet, seed)

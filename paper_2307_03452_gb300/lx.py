@@ -35,7 +35,8 @@ EXPORTS = sorted(["lx_eri_out_size", "lx_eri_workspace_size", "lx_eri_workspace_
                   "lx_hermite_R", "lx_hermite_H", "lx_split_gemm", "lx_route_features", "lx_mlp_forward",
                   "lx_mlp_grad", "lx_mlp_adam", "lx_eri_graph_create", "lx_eri_graph_launch",
                   "lx_eri_graph_destroy", "lx_eri_autotune", "lx_tune_export", "lx_tune_import", "lx_tune_clear",
-                  "lx_router_set"])
+                  "lx_router_set", "lx_eri_pairs_out_size", "lx_eri_pairs_workspace_size",
+                  "lx_eri_pairs_workspace_min", "lx_eri_pairs"])
 TILE_SHAPES = ["32x64", "64x32", "32x32", "64x64"]
 MLP_NIN = 20
 MLP_WIDTH = 64
@@ -82,6 +83,12 @@ def load(build_if_missing: bool = True):
         lib.lx_eri_workspace_min.restype = c_i64
         lib.lx_eri_batch.argtypes = [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_i64, c_i32, c_vp, c_vp, c_sz, c_vp]
         lib.lx_eri_batch.restype = ctypes.c_int
+        for name in ("lx_eri_pairs_out_size", "lx_eri_pairs_workspace_size", "lx_eri_pairs_workspace_min"):
+            getattr(lib, name).argtypes = [c_vp, c_i32, c_vp, c_i64, c_vp, c_i64, c_i32]
+            getattr(lib, name).restype = c_i64
+        lib.lx_eri_pairs.argtypes = [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_i64, c_vp, c_i64, c_i32, c_vp, c_vp, c_sz,
+                                     c_vp]
+        lib.lx_eri_pairs.restype = ctypes.c_int
         lib.lx_eri_batch_static.argtypes = [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_i64, c_i32, c_vp, c_vp]
         lib.lx_eri_batch_static.restype = ctypes.c_int
         lib.lx_eri_sync_status.argtypes = [c_vp]
@@ -245,6 +252,69 @@ class Batch:
                                  ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(workspace.data_ptr()),
                                  workspace.numel() * workspace.element_size(), ctypes.c_void_p(_stream_ptr(stream)))
         _check(rc, "lx_eri_batch")
+
+
+class PairBatch:
+    """The bra-list x ket-list form: (ab|cd) for every bra pair and every ket pair, into a
+    dense [nbra][nket][n_ab][n_cd] output (lx_eri_pairs)."""
+
+    def __init__(self, basis: dict, bra_pairs, ket_pairs, solid: bool, path: str = "fp64"):
+        if path not in PATH_FLAGS:
+            raise ValueError(f"unknown path {path!r}")
+        self.solid = bool(solid)
+        self.path = path
+        self.flags = (LX_SOLID if solid else LX_CART) | PATH_FLAGS[path]
+        self.shells = pack_shells(basis)
+        self.exps = np.ascontiguousarray(basis["exps"], dtype=np.float64)
+        self.coefs = np.ascontiguousarray(basis["coefs"], dtype=np.float64)
+        self.bra = np.ascontiguousarray(np.asarray(bra_pairs, dtype=np.int32).reshape(-1, 2))
+        self.ket = np.ascontiguousarray(np.asarray(ket_pairs, dtype=np.int32).reshape(-1, 2))
+        l = np.asarray(basis["l"])
+        self.shape = (len(self.bra), len(self.ket),
+                      nfun(int(l[self.bra[0, 0]]), solid) * nfun(int(l[self.bra[0, 1]]), solid) if len(self.bra) else 0,
+                      nfun(int(l[self.ket[0, 0]]), solid) * nfun(int(l[self.ket[0, 1]]), solid) if len(self.ket) else 0)
+        self.out_size = self._size(load().lx_eri_pairs_out_size, "lx_eri_pairs_out_size")
+
+    def _args(self):
+        return (_ptr(self.shells), len(self.shells), _ptr(self.bra), len(self.bra), _ptr(self.ket), len(self.ket),
+                self.flags)
+
+    def _size(self, fn, where):
+        n = fn(*self._args())
+        if n < 0:
+            raise LxError(int(n), where)
+        return int(n)
+
+    def workspace_size(self) -> int:
+        return self._size(load().lx_eri_pairs_workspace_size, "lx_eri_pairs_workspace_size")
+
+    def workspace_min(self) -> int:
+        return self._size(load().lx_eri_pairs_workspace_min, "lx_eri_pairs_workspace_min")
+
+    def run(self, out, workspace, stream=None, time_stages: bool = False):
+        """Enqueue lx_eri_pairs; out and workspace are CUDA tensors (float64 / uint8)."""
+        flags = self.flags | (LX_TIME_STAGES if time_stages else 0)
+        rc = load().lx_eri_pairs(_ptr(self.shells), len(self.shells), _ptr(self.exps), _ptr(self.coefs),
+                                 len(self.exps), _ptr(self.bra), len(self.bra), _ptr(self.ket), len(self.ket), flags,
+                                 ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(workspace.data_ptr()),
+                                 workspace.numel() * workspace.element_size(), ctypes.c_void_p(_stream_ptr(stream)))
+        _check(rc, "lx_eri_pairs")
+
+
+def eri_pairs(basis: dict, bra_pairs, ket_pairs, solid: bool = True, device="cuda",
+              workspace_limit: int | None = None, stream=None, path: str = "fp64"):
+    """(ab|cd) for every bra pair and every ket pair on the GPU: a float64 CUDA tensor of shape
+    (nbra, nket, n_ab, n_cd)."""
+    import torch
+    b = PairBatch(basis, bra_pairs, ket_pairs, solid, path=path)
+    need = b.workspace_size()
+    if workspace_limit is not None:
+        need = max(min(need, int(workspace_limit)), b.workspace_min())
+    out = torch.empty(max(b.out_size, 1), dtype=torch.float64, device=device)
+    ws = alloc_workspace(need, device)
+    b.run(out, ws, stream)
+    sync_status(stream)
+    return out[: b.out_size].view(b.shape)
 
 
 def stage_times(stream=None) -> tuple[dict, dict]:

@@ -30,7 +30,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_error_strings():
     lib = lx.load()
-    for code in [0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10, -11]:
+    for code in [0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10, -11, -12, -13]:
         s = lib.lx_strerror(code).decode()
         assert s and s != "unknown error code"
     assert lib.lx_strerror(12345).decode() == "unknown error code"
@@ -176,3 +176,47 @@ def test_routed_flag_combinations():
     split = lib.lx_eri_workspace_size(lx._ptr(b.shells), len(b.shells), lx._ptr(b.quartets), len(b.quartets),
                                       lx.LX_SOLID | lx.LX_PATH_SPLIT)
     assert need >= split > 0
+
+
+def _pairs_basis():
+    # shells 0-3: h, h, i, i;  4: g
+    rng = np.random.default_rng(5)
+    ls = np.array([5, 5, 6, 6, 4], np.int32)
+    K = np.array([1, 2, 1, 3, 2], np.int32)
+    off = np.concatenate([[0], np.cumsum(K)[:-1]]).astype(np.int32)
+    return {"l": ls, "nprim": K, "prim_off": off, "center": rng.uniform(0, 3, (5, 3)),
+            "exps": np.exp(rng.uniform(-2, 2, K.sum())), "coefs": np.ones(K.sum())}
+
+
+def test_pair_lists_sizes_and_errors():
+    b = _pairs_basis()
+    lib = lx.load()
+    pb = lx.PairBatch(b, [[0, 1], [1, 0], [1, 1]], [[2, 3], [3, 2]], True)
+    assert pb.shape == (3, 2, 121, 169)
+    assert pb.out_size == 3 * 2 * 121 * 169
+    # the pair form is the flat form of the same quartets in bra-major order
+    flat = lx.Batch(b, [[0, 1, 2, 3], [0, 1, 3, 2], [1, 0, 2, 3], [1, 0, 3, 2], [1, 1, 2, 3], [1, 1, 3, 2]], True)
+    assert pb.workspace_size() == flat.workspace_size()
+    assert 0 < pb.workspace_min() <= pb.workspace_size()
+    sh = lx.pack_shells(b)
+
+    def size(bra, ket, flags=lx.LX_SOLID):
+        bra = np.ascontiguousarray(np.asarray(bra, np.int32).reshape(-1, 2))
+        ket = np.ascontiguousarray(np.asarray(ket, np.int32).reshape(-1, 2))
+        return lib.lx_eri_pairs_out_size(sh.ctypes.data_as(ctypes.c_void_p), len(sh),
+                                         bra.ctypes.data_as(ctypes.c_void_p), len(bra),
+                                         ket.ctypes.data_as(ctypes.c_void_p), len(ket), flags)
+    assert size([[0, 1]], [[2, 3]], lx.LX_CART) == 21 * 21 * 28 * 28
+    assert size([[0, 1], [0, 4]], [[2, 3]]) == -13        # bra pairs (h h) and (h g)
+    assert size([[0, 1]], [[2, 3], [4, 2]]) == -13        # ket pairs (i i) and (g i)
+    assert size([[0, 5]], [[2, 3]]) == -4                  # shell index out of range
+    assert size([[0, -1]], [[2, 3]]) == -4
+    assert size(np.zeros((0, 2)), [[2, 3]]) == 0           # no bra pairs: nothing to do
+    assert size([[0, 1]], [[2, 3]], 0x1000) == -5          # unknown flag
+    neg = lib.lx_eri_pairs_out_size(sh.ctypes.data_as(ctypes.c_void_p), len(sh), None, -1, None, 0, 1)
+    assert neg == -10
+    # an empty product enqueues nothing (no device needed)
+    rc = lib.lx_eri_pairs(sh.ctypes.data_as(ctypes.c_void_p), len(sh), b["exps"].ctypes.data_as(ctypes.c_void_p),
+                          b["coefs"].ctypes.data_as(ctypes.c_void_p), len(b["exps"]), None, 0, None, 0, 1, None,
+                          None, 0, None)
+    assert rc == 0
