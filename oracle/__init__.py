@@ -15,6 +15,9 @@ The C sources follow the paper's Section 2 (Formalism) step by step:
 * ``eri_os_oracle.c`` -- an independent Obara-Saika / Head-Gordon-Pople evaluator of
   the same Cartesian integrals, used only to pin the MD oracle.
 
+``jk`` contracts the integral blocks with a density matrix into Coulomb and exchange
+matrices, straight from the definition (numpy).
+
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 (closed forms, brute-force quadrature, invariances, the paper's printed sizes).
 """
@@ -182,6 +185,42 @@ def eri(basis: dict, quartets, solid: bool = False, normalize: bool = True, meth
     if rc != 0:
         raise ValueError("oracle_eri rejected its arguments")
     return out, out_off
+
+
+def function_offsets(basis: dict, solid: bool) -> tuple[np.ndarray, int]:
+    """First basis function of each shell (shells in the given order, n(l) functions each)
+    and the total number of functions."""
+    n = np.array([nsolid(int(x)) if solid else ncart(int(x)) for x in basis["l"]], dtype=np.int64)
+    off = np.zeros(len(n), dtype=np.int64)
+    if len(n):
+        off[1:] = np.cumsum(n)[:-1]
+    return off, int(n.sum())
+
+
+def jk(basis: dict, quartets, D, solid: bool = False) -> tuple[np.ndarray, np.ndarray]:
+    """Coulomb and exchange contributions of a quartet list to a density matrix D
+    (nbf x nbf; Section 3 names this digestion of the integrals into Fock matrix elements):
+    for each listed quartet (ab|cd), with functions mu of a, nu of b, lam of c, sig of d,
+        J[mu, nu]  += sum_{lam, sig} (mu nu | lam sig) D[lam, sig]
+        K[mu, lam] += sum_{nu, sig}  (mu nu | lam sig) D[nu, sig]
+    Each quartet counts once as listed: no permutational images are added."""
+    l = np.asarray(basis["l"])
+    qs = np.asarray(quartets, dtype=np.int64).reshape(-1, 4)
+    bf, nbf = function_offsets(basis, solid)
+    D = np.asarray(D, dtype=np.float64)
+    assert D.shape == (nbf, nbf)
+    J = np.zeros((nbf, nbf))
+    K = np.zeros((nbf, nbf))
+    out, off = eri(basis, qs, solid=solid)
+    nf = [nsolid(int(x)) if solid else ncart(int(x)) for x in l]
+    for i, (a, b, c, d) in enumerate(qs):
+        na, nb, nc, nd = nf[a], nf[b], nf[c], nf[d]
+        blk = out[off[i]:off[i] + na * nb * nc * nd].reshape(na, nb, nc, nd)
+        ra, rb = slice(bf[a], bf[a] + na), slice(bf[b], bf[b] + nb)
+        rc, rd = slice(bf[c], bf[c] + nc), slice(bf[d], bf[d] + nd)
+        J[ra, rb] += np.einsum("abcd,cd->ab", blk, D[rc, rd])
+        K[ra, rc] += np.einsum("abcd,bd->ac", blk, D[rb, rd])
+    return J, K
 
 
 def max_threads() -> int:
