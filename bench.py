@@ -591,6 +591,41 @@ def main(argv=None):
         del ref_p, outp
         torch.cuda.empty_cache()
 
+    # ---- J/K digestion of the same pair-list workload (nbf 3,328): each quartet's block is
+    # digested from the workspace into J and K instead of being returned
+    jk = None
+    if not args.no_pairs:
+        pbas, pbra, pket = inputs.iiii_pairs()
+        pq = np.array([(a, b, c, d) for (a, b) in pbra for (c, d) in pket], np.int32)
+        jb_ = {p_: lx.JKBatch(pbas, pq, True, path=p_) for p_ in ("fp64", "split")}
+        nbf = jb_["fp64"].nbf
+        Dd = torch.randn(nbf, nbf, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(7))
+        Dd = Dd + Dd.T
+        Jd, Kd = torch.zeros_like(Dd), torch.zeros_like(Dd)
+        jk = {"workload": f"J and K of {len(pq)} (ii|ii) quartets ({len(pbra)} x {len(pket)} pair lists, K = 1) "
+                          f"against a dense symmetric density, nbf = {nbf} (lx_eri_jk)"}
+
+        class _JKRun:  # time_steps drives .run(out, ws, stream, time_stages)
+            def __init__(self, b):
+                self.b = b
+
+            def run(self, out, ws_, stream=None, time_stages=False):
+                self.b.run_jk(Dd, Jd, Kd, ws_, stream, time_stages)
+
+        for path in ("fp64", "split"):
+            wsj = lx.alloc_workspace(jb_[path].workspace_size())
+            jms, jstage, _ = time_steps(torch, lx, _JKRun(jb_[path]), None, wsj, max(2, min(args.steps, 3)), 2,
+                                        flush_buf, world)
+            jtot = reduce_max(sum(jms), world)
+            nst = len(jms)
+            blk_bytes = 8 * 169 * 169 * len(pq)
+            jk[path] = {"quartets_per_s": world * len(pq) * nst / (jtot * 1e-3), "ms_per_step": jtot / nst,
+                        "stage_ms_per_step": {k: v / nst for k, v in jstage.items()},
+                        "digest_gbs": blk_bytes / (jstage["digest"] / nst * 1e-3) / 1e9 if jstage["digest"] else None}
+            del wsj
+        del Dd, Jd, Kd
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
         cpu = cpu_baseline(basis, quartets, True, args.cpu_seconds)
@@ -607,7 +642,7 @@ def main(argv=None):
             "fp64_equiv_tflops": fp64_tf, "integrals_per_s": world * nint * args.steps / (total_ms * 1e-3),
             "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
             "roofline": roofline, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu, "cartesian": cart,
-            "split": split, "mixed": mixed, "split_config": split_cfg, "routed": routed, "pairs": pairs,
+            "split": split, "mixed": mixed, "split_config": split_cfg, "routed": routed, "pairs": pairs, "jk": jk,
             "gpu_launches": int(sum(launches.values())),
         }
         print(json.dumps(line), flush=True)

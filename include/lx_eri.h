@@ -84,7 +84,8 @@ typedef struct {
 #define LX_STAGE_GEMM1 3  /* [ab|q] = H_ab [p|q] */
 #define LX_STAGE_GEMM2 4  /* (ab|cd) = [ab|q] H_cd^T */
 #define LX_STAGE_SPLIT 5  /* LX_PATH_SPLIT: FP64 operands -> BF16 digit planes */
-#define LX_NSTAGE 6
+#define LX_STAGE_DIGEST 6 /* lx_eri_jk: blocks digested into J and K */
+#define LX_NSTAGE 7
 
 /* error codes (0 = success) */
 #define LX_OK 0
@@ -166,6 +167,35 @@ int64_t lx_eri_pairs_workspace_min(const lx_shell* shells, int32_t nshell, const
 int lx_eri_pairs(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs, int32_t nprim_total,
                  const int32_t* bra_pairs, int64_t nbra, const int32_t* ket_pairs, int64_t nket, int32_t flags,
                  double* out, void* workspace, size_t workspace_bytes, void* cuda_stream);
+
+/*
+ * Coulomb and exchange digestion (Section 3: Fock matrix elements formed from the integral
+ * batches directly).  Basis functions are numbered shell by shell in the order of shells[]:
+ * shell s owns functions bf(s) .. bf(s) + n(l_s) - 1, bf(s) = sum over s' < s of n(l_s'),
+ * with n(l) = 2l+1 (LX_SOLID) or (l+1)(l+2)/2; lx_nbf returns the total nbf.  For every
+ * listed quartet (ab|cd), mu in a, nu in b, lam in c, sig in d:
+ *     J[mu][nu]  += sum_{lam, sig} (mu nu|lam sig) D[lam][sig]
+ *     K[mu][lam] += sum_{nu, sig}  (mu nu|lam sig) D[nu][sig]
+ * Each quartet counts once as listed (the caller lists the permutational images it wants
+ * and folds their degeneracy into D or the list).
+ *   D: DEVICE, nbf x nbf row-major, read only.  J, K: DEVICE, nbf x nbf row-major, added to
+ *     (atomically: the summation order, and so the last bits, vary from run to run); either
+ *     may be NULL to skip it, not both.
+ *   quartets[].out_offset is not used (it must still be >= 0).
+ *   workspace: as lx_eri_batch, sized by lx_eri_jk_workspace_size / _min: each quartet's
+ *     block is written there by the second transform and streamed once by the digestion
+ *     kernel; nothing is written to a caller output.
+ * Flags, paths (LX_PATH_SPLIT, LX_PATH_ROUTED), staging and stream semantics as
+ * lx_eri_batch; LX_TIME_STAGES times the digestion as LX_STAGE_DIGEST.  nbf <= 2^31 - 1.
+ */
+int64_t lx_nbf(const lx_shell* shells, int32_t nshell, int32_t flags);
+int64_t lx_eri_jk_workspace_size(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets,
+                                 int64_t nquartet, int32_t flags);
+int64_t lx_eri_jk_workspace_min(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets,
+                                int64_t nquartet, int32_t flags);
+int lx_eri_jk(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs, int32_t nprim_total,
+              const lx_quartet* quartets, int64_t nquartet, int32_t flags, const double* D, double* J, double* K,
+              void* workspace, size_t workspace_bytes, void* cuda_stream);
 
 /*
  * lx_eri_batch without a workspace argument, for callers that cannot allocate device memory

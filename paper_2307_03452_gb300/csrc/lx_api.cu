@@ -25,6 +25,9 @@ namespace {
 __device__ unsigned g_status_word;
 
 constexpr int MAX_DEVICES = 64;
+// Planner flag of lx_eri_jk (never accepted from callers): each quartet's block goes to the
+// workspace and is digested into J and K there.
+constexpr int32_t JK_DIGEST = 0x40000000;
 std::mutex g_init_mutex;
 bool g_dev_ready[MAX_DEVICES];
 unsigned* g_status_ptr[MAX_DEVICES];
@@ -202,6 +205,7 @@ size_t quartet_bytes(const lx_shell* sh, const lx_quartet& q, int flags) {
     int64_t items = kbra * kket;
     // + 256 bytes per data block: each block starts on a 256-byte boundary
     size_t bytes = sizeof(DQuartet) + 8 * (size_t)(kbra * kket * pyr(L) + nab * n1) + 512;
+    if (flags & JK_DIGEST) bytes += 8 * (size_t)(nab * ncd) + 256;  // the block, digested in place
     if (!split) {
         // bound: the 32 x 32 tile gives the most work items
         items += ((nab + 31) / 32) * ((n1 + 31) / 32);
@@ -288,7 +292,8 @@ struct ChunkPlan {
     size_t off_pairs = 0, off_quartets = 0, off_h = 0, off_br = 0, off_g1 = 0, off_g2 = 0, off_data = 0;
     int g1_counts[GEMM_NVARIANT] = {0, 0, 0, 0}, g2_counts[GEMM_NVARIANT] = {0, 0, 0, 0};
     size_t off_counters = 0;  // 2 x GEMM_NVARIANT work counters, uploaded as zeros with the blob
-    // split path (per quartet: 3 split-row descs B1, A2, B2; 2 column-scale descs c1, c2)
+    // split path: one split-row and one column-scale desc per pair (H), one split-row desc per
+    // quartet (X)
     std::vector<SplitRowsDesc> srd;
     std::vector<ColMaxDesc> cmd;
     std::vector<SplitQuartet> sq;
@@ -302,7 +307,7 @@ struct ChunkPlan {
 
 void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int flags, size_t chunk_base,
                  ChunkPlan& P, const Overrides& ov = Overrides()) {
-    const bool solid = flags & LX_SOLID, split = flags & LX_PATH_SPLIT;
+    const bool solid = flags & LX_SOLID, split = flags & LX_PATH_SPLIT, jk = flags & JK_DIGEST;
     P.pairs.clear();
     P.quartets.clear();
     P.items_h.clear();
@@ -494,6 +499,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     for (auto& d : P.quartets) {
         d.rr_off = take((int64_t)d.kbra * d.kket * d.nr);
         d.x_off = take((int64_t)d.nab * d.kket * d.nq);
+        if (jk) d.out_off = take((int64_t)d.nab * d.ncd);  // doubles from the workspace base
     }
     if (split) {
         auto take_bytes = [&](int64_t bytes) { return 8 * take((bytes + 7) / 8); };
@@ -625,16 +631,19 @@ int plan_batch(const lx_shell* shells, int32_t nshell, const double* exps, const
     B.nprim = nprim_total;
     B.head = head_bytes(nshell, nprim_total);
     if (workspace_bytes < B.head + CHUNK_SLACK) return LX_ERR_WORKSPACE;
-    const int pflags = flags & (LX_SOLID | LX_PATH_SPLIT);
+    const int pflags = flags & (LX_SOLID | LX_PATH_SPLIT | JK_DIGEST);
     std::vector<Chunk> chunks;
     int v = plan_chunks(shells, quartets, nquartet, pflags, workspace_bytes - B.head, chunks);
     if (v != LX_OK) return v;
     B.head_blob.assign(B.head, 0);
     DShell* dsh = reinterpret_cast<DShell*>(B.head_blob.data());
+    int bf = 0;
     for (int32_t s = 0; s < nshell; ++s) {
         dsh[s].l = shells[s].l;
         dsh[s].K = shells[s].nprim;
         dsh[s].prim_off = shells[s].prim_offset;
+        dsh[s].bf = bf;
+        bf += nfun(shells[s].l, flags & LX_SOLID);
         for (int k = 0; k < 3; ++k) dsh[s].A[k] = shells[s].center[k];
     }
     B.o_exps = align256(sizeof(DShell) * (size_t)nshell);
@@ -652,12 +661,22 @@ int plan_batch(const lx_shell* shells, int32_t nshell, const double* exps, const
     return LX_OK;
 }
 
+// Density and outputs of lx_eri_jk (device pointers; J or K may be null).
+struct JkArgs {
+    const double* D;
+    double* J;
+    double* K;
+    int64_t nbf;
+};
+
 // Enqueue a planned batch on stream st: the head upload, normalisation, then per chunk the
 // descriptor upload and the kernels of the chosen path.  head_src / blob_src are the host
 // bytes to upload (pageable, or pinned for graph capture).
 int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector<const char*>& blob_src, double* out,
-                  void* workspace, unsigned* status, cudaStream_t st, bool time_stages) {
+                  void* workspace, unsigned* status, cudaStream_t st, bool time_stages, const JkArgs* jk) {
     const bool split = B.flags & LX_PATH_SPLIT, solid = B.flags & LX_SOLID;
+    if ((B.flags & JK_DIGEST) && !jk) return LX_ERR_NULL;
+    if (jk) out = static_cast<double*>(workspace);  // blocks at workspace offsets, digested below
     const int nshell = B.nshell;
     char* wsb = static_cast<char*>(workspace);
     double* ws = static_cast<double*>(workspace);
@@ -723,18 +742,25 @@ int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector
                 cudaSuccess)
                 return cuda_fail(e);
             if ((e = tm.end(LX_STAGE_GEMM2, 1)) != cudaSuccess) return cuda_fail(e);
-            continue;
+        } else {
+            if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
+            int* d_counters = reinterpret_cast<int*>(base + P.off_counters);
+            if ((e = launch_gemm1(d_q, d_pairs, d_ig1, P.g1_counts, ws, d_counters, status, st)) != cudaSuccess)
+                return cuda_fail(e);
+            if ((e = tm.end(LX_STAGE_GEMM1, 1)) != cudaSuccess) return cuda_fail(e);
+            if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
+            if ((e = launch_gemm2(d_q, d_pairs, d_ig2, P.g2_counts, ws, out, d_counters + GEMM_NVARIANT, status,
+                                  st)) != cudaSuccess)
+                return cuda_fail(e);
+            if ((e = tm.end(LX_STAGE_GEMM2, 1)) != cudaSuccess) return cuda_fail(e);
         }
-        if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
-        int* d_counters = reinterpret_cast<int*>(base + P.off_counters);
-        if ((e = launch_gemm1(d_q, d_pairs, d_ig1, P.g1_counts, ws, d_counters, status, st)) != cudaSuccess)
-            return cuda_fail(e);
-        if ((e = tm.end(LX_STAGE_GEMM1, 1)) != cudaSuccess) return cuda_fail(e);
-        if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
-        if ((e = launch_gemm2(d_q, d_pairs, d_ig2, P.g2_counts, ws, out, d_counters + GEMM_NVARIANT, status, st)) !=
-            cudaSuccess)
-            return cuda_fail(e);
-        if ((e = tm.end(LX_STAGE_GEMM2, 1)) != cudaSuccess) return cuda_fail(e);
+        if (jk) {
+            if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
+            if ((e = launch_jk_digest(d_q, d_pairs, d_sh, (int)P.quartets.size(), ws, solid, jk->D, jk->nbf, jk->J,
+                                      jk->K, st)) != cudaSuccess)
+                return cuda_fail(e);
+            if ((e = tm.end(LX_STAGE_DIGEST, 1)) != cudaSuccess) return cuda_fail(e);
+        }
     }
     return LX_OK;
 }
@@ -861,7 +887,7 @@ int eri_batch_unstaged(const lx_shell* shells, int32_t nshell, const double* exp
     std::vector<const char*> blobs;
     for (const auto& P : B.chunks) blobs.push_back(P.blob.data());
     return enqueue_batch(B, B.head_blob.data(), blobs, out, workspace, status, static_cast<cudaStream_t>(cuda_stream),
-                         (flags & LX_TIME_STAGES) != 0);
+                         (flags & LX_TIME_STAGES) != 0, nullptr);
 }
 
 }  // namespace lx
@@ -882,7 +908,8 @@ size_t routed_scratch_bytes(int64_t n) {
 // device set up, stream not capturing).
 int eri_batch_staged(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
                      int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags, double* out,
-                     void* workspace, size_t workspace_bytes, cudaStream_t st, unsigned* status) {
+                     void* workspace, size_t workspace_bytes, cudaStream_t st, unsigned* status,
+                     const JkArgs* jk = nullptr) {
     PlannedBatch B;
     int v = plan_batch(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, workspace_bytes,
                        Overrides(), B);
@@ -905,7 +932,7 @@ int eri_batch_staged(const lx_shell* shells, int32_t nshell, const double* exps,
         blobs.push_back(stage + o);
         o += align256(P.blob.size());
     }
-    v = enqueue_batch(B, head_src, blobs, out, workspace, status, st, (flags & LX_TIME_STAGES) != 0);
+    v = enqueue_batch(B, head_src, blobs, out, workspace, status, st, (flags & LX_TIME_STAGES) != 0, jk);
     const int r = stage_release(dev, idx, st, true);
     return v != LX_OK ? v : r;
 }
@@ -947,57 +974,42 @@ int expand_pairs(const lx_shell* shells, int32_t nshell, const int32_t* bra, int
     return LX_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int64_t lx_eri_out_size(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
-                        int32_t flags) {
-    const int v = validate(shells, nshell, nullptr, nullptr, 0, quartets, nquartet, flags, false);
-    if (v != LX_OK) return v;
-    const bool solid = flags & LX_SOLID;
-    int64_t n = 0;
-    for (int64_t i = 0; i < nquartet; ++i) {
-        int64_t sz = 1;
-        for (int k = 0; k < 4; ++k) sz *= nfun(shells[quartets[i].s[k]].l, solid);
-        n = std::max(n, quartets[i].out_offset + sz);
-    }
-    return n;
-}
-
-int64_t lx_eri_workspace_size(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
-                              int32_t flags) {
+// lx_eri_workspace_size (least = false) and lx_eri_workspace_min (least = true); extra is 0
+// or JK_DIGEST (not a caller flag: added after validation).
+int64_t workspace_need(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
+                       int32_t flags, int32_t extra, bool least) {
     const int v = validate(shells, nshell, nullptr, nullptr, 0, quartets, nquartet, flags, false);
     if (v != LX_OK) return v;
     const size_t head = head_bytes(nshell, (int32_t)prim_count(shells, nshell));
-    if (flags & LX_PATH_ROUTED) {
-        // either path may get every quartet; the predictions come first
-        const size_t a = chunk_estimate(shells, quartets, 0, nquartet, flags & LX_SOLID);
-        const size_t b = chunk_estimate(shells, quartets, 0, nquartet, (flags & LX_SOLID) | LX_PATH_SPLIT);
-        return (int64_t)std::max(head + std::max(a, b), routed_scratch_bytes(nquartet));
-    }
-    return (int64_t)(head + chunk_estimate(shells, quartets, 0, nquartet, flags & (LX_SOLID | LX_PATH_SPLIT)));
+    const int32_t solid = (flags & LX_SOLID) | extra;
+    // a routed quartet may take either path; the predictions come first
+    const bool routed = flags & LX_PATH_ROUTED;
+    auto est = [&](int64_t b, int64_t e) {
+        if (routed)
+            return std::max(chunk_estimate(shells, quartets, b, e, solid),
+                            chunk_estimate(shells, quartets, b, e, solid | LX_PATH_SPLIT));
+        return chunk_estimate(shells, quartets, b, e, solid | (flags & LX_PATH_SPLIT));
+    };
+    size_t need = CHUNK_SLACK;
+    if (!least)
+        need = est(0, nquartet);
+    else
+        for (int64_t i = 0; i < nquartet; ++i) need = std::max(need, est(i, i + 1));
+    const size_t total = head + need;
+    return (int64_t)(routed ? std::max(total, routed_scratch_bytes(nquartet)) : total);
 }
 
-int64_t lx_eri_workspace_min(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
-                             int32_t flags) {
-    const int v = validate(shells, nshell, nullptr, nullptr, 0, quartets, nquartet, flags, false);
-    if (v != LX_OK) return v;
-    size_t mx = CHUNK_SLACK;
-    // a routed quartet may take the split path, which needs more room
-    const int32_t f = (flags & LX_PATH_ROUTED) ? (flags & LX_SOLID) | LX_PATH_SPLIT : flags & (LX_SOLID | LX_PATH_SPLIT);
-    for (int64_t i = 0; i < nquartet; ++i) mx = std::max(mx, chunk_estimate(shells, quartets, i, i + 1, f));
-    const int64_t need = (int64_t)(head_bytes(nshell, (int32_t)prim_count(shells, nshell)) + mx);
-    return (flags & LX_PATH_ROUTED) ? std::max(need, (int64_t)routed_scratch_bytes(nquartet)) : need;
-}
-
-int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
-                 int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags, double* out,
-                 void* workspace, size_t workspace_bytes, void* cuda_stream) {
+// lx_eri_batch, and lx_eri_jk with jk set (flags then carry JK_DIGEST and out is unused).
+int eri_entry(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs, int32_t nprim_total,
+              const lx_quartet* quartets, int64_t nquartet, int32_t flags, double* out, void* workspace,
+              size_t workspace_bytes, void* cuda_stream, const JkArgs* jk) {
+    const int32_t internal = flags & JK_DIGEST;
+    flags &= ~JK_DIGEST;
     int v = validate(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, true);
     if (v != LX_OK) return v;
+    flags |= internal;
     if (nquartet == 0) return LX_OK;
-    if (!out) return LX_ERR_NULL;
+    if (!out && !jk) return LX_ERR_NULL;
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return LX_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -1013,7 +1025,7 @@ int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, con
     if ((v = ensure_device(&status)) != LX_OK) return v;
     if (!(flags & LX_PATH_ROUTED))
         return eri_batch_staged(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, out, workspace,
-                                workspace_bytes, st, status);
+                                workspace_bytes, st, status, jk);
     // routed: predictions into the (still unused) workspace, read back, then one staged batch
     // per path over the same output and workspace
     int dev = 0;
@@ -1050,13 +1062,49 @@ int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, con
     const int32_t base = flags & ~LX_PATH_ROUTED;
     if (!q64.empty() && (v = eri_batch_staged(shells, nshell, exps, coefs, nprim_total, q64.data(),
                                               (int64_t)q64.size(), base, out, workspace, workspace_bytes, st,
-                                              status)) != LX_OK)
+                                              status, jk)) != LX_OK)
         return v;
     if (!qsp.empty() && (v = eri_batch_staged(shells, nshell, exps, coefs, nprim_total, qsp.data(),
                                               (int64_t)qsp.size(), base | LX_PATH_SPLIT, out, workspace,
-                                              workspace_bytes, st, status)) != LX_OK)
+                                              workspace_bytes, st, status, jk)) != LX_OK)
         return v;
     return LX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t lx_eri_out_size(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
+                        int32_t flags) {
+    const int v = validate(shells, nshell, nullptr, nullptr, 0, quartets, nquartet, flags, false);
+    if (v != LX_OK) return v;
+    const bool solid = flags & LX_SOLID;
+    int64_t n = 0;
+    for (int64_t i = 0; i < nquartet; ++i) {
+        int64_t sz = 1;
+        for (int k = 0; k < 4; ++k) sz *= nfun(shells[quartets[i].s[k]].l, solid);
+        n = std::max(n, quartets[i].out_offset + sz);
+    }
+    return n;
+}
+
+int64_t lx_eri_workspace_size(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
+                              int32_t flags) {
+    return workspace_need(shells, nshell, quartets, nquartet, flags, 0, false);
+}
+
+int64_t lx_eri_workspace_min(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets, int64_t nquartet,
+                             int32_t flags) {
+    return workspace_need(shells, nshell, quartets, nquartet, flags, 0, true);
+}
+
+int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
+                 int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags, double* out,
+                 void* workspace, size_t workspace_bytes, void* cuda_stream) {
+    if (flags & JK_DIGEST) return LX_ERR_FLAGS;
+    return eri_entry(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags, out, workspace,
+                     workspace_bytes, cuda_stream, nullptr);
 }
 
 int lx_router_set(const void* params_f16, float tau) {
@@ -1159,7 +1207,7 @@ int lx_eri_graph_create(const lx_shell* shells, int32_t nshell, const double* ex
         cudaStreamDestroy(cs);
         return fail(cuda_fail(e));
     }
-    v = nquartet > 0 ? enqueue_batch(B, head_src, blobs, out, workspace, status, cs, false) : LX_OK;
+    v = nquartet > 0 ? enqueue_batch(B, head_src, blobs, out, workspace, status, cs, false, nullptr) : LX_OK;
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(cs, &g);
     cudaStreamDestroy(cs);
@@ -1242,7 +1290,8 @@ int lx_eri_autotune(const lx_shell* shells, int32_t nshell, const double* exps, 
             for (const auto& P : B.chunks) blobs.push_back(P.blob.data());
             double t1 = 1e300, t2 = 1e300;
             for (int rep = 0; rep < 3; ++rep) {  // first repetition warms up
-                if ((v = enqueue_batch(B, B.head_blob.data(), blobs, out, workspace, status, st, true)) != LX_OK)
+                if ((v = enqueue_batch(B, B.head_blob.data(), blobs, out, workspace, status, st, true, nullptr)) !=
+                    LX_OK)
                     return v;
                 double ms[LX_NSTAGE];
                 if ((v = collect_stage_ms(st, ms)) != LX_OK) return v;
@@ -1387,6 +1436,36 @@ int lx_eri_pairs(const lx_shell* shells, int32_t nshell, const double* exps, con
     if (v != LX_OK) return v;
     return lx_eri_batch(shells, nshell, exps, coefs, nprim_total, qs.data(), (int64_t)qs.size(), flags, out,
                         workspace, workspace_bytes, cuda_stream);
+}
+
+int64_t lx_nbf(const lx_shell* shells, int32_t nshell, int32_t flags) {
+    const int v = validate(shells, nshell, nullptr, nullptr, 0, nullptr, 0, flags, false);
+    if (v != LX_OK) return v;
+    int64_t n = 0;
+    for (int32_t s = 0; s < nshell; ++s) n += nfun(shells[s].l, flags & LX_SOLID);
+    return n;
+}
+
+int64_t lx_eri_jk_workspace_size(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets,
+                                 int64_t nquartet, int32_t flags) {
+    return workspace_need(shells, nshell, quartets, nquartet, flags, JK_DIGEST, false);
+}
+
+int64_t lx_eri_jk_workspace_min(const lx_shell* shells, int32_t nshell, const lx_quartet* quartets,
+                                int64_t nquartet, int32_t flags) {
+    return workspace_need(shells, nshell, quartets, nquartet, flags, JK_DIGEST, true);
+}
+
+int lx_eri_jk(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs, int32_t nprim_total,
+              const lx_quartet* quartets, int64_t nquartet, int32_t flags, const double* D, double* J, double* K,
+              void* workspace, size_t workspace_bytes, void* cuda_stream) {
+    const int64_t nbf = lx_nbf(shells, nshell, flags);
+    if (nbf < 0) return (int)nbf;
+    if (nbf > INT32_MAX) return LX_ERR_SIZE;
+    if (nquartet > 0 && (!D || (!J && !K))) return LX_ERR_NULL;
+    const JkArgs jk{D, J, K, nbf};
+    return eri_entry(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags | JK_DIGEST, nullptr,
+                     workspace, workspace_bytes, cuda_stream, &jk);
 }
 
 const char* lx_strerror(int code) {

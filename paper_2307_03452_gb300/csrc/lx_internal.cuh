@@ -35,7 +35,8 @@ __host__ __device__ inline int hidx(int t, int u, int v) {
 enum : unsigned { ST_BAD_INDEX = 1u, ST_BAD_INPUT = 2u, ST_TIMEOUT = 4u };
 
 struct DShell {  // 48 bytes
-    int l, K, prim_off, pad;
+    int l, K, prim_off;
+    int bf;  // first basis function of the shell (J/K digestion)
     double A[3];
     double pad2;
 };
@@ -60,7 +61,7 @@ struct DQuartet {
     int nr;              // pyr(L)
     int64_t rr_off;      // [kbra][kket][nr] doubles
     int64_t x_off;       // [nab][kket*nq] doubles
-    int64_t out_off;     // output block in the caller's buffer
+    int64_t out_off;     // output block in the caller's buffer (J/K digestion: in the workspace)
 };
 
 struct WorkItem {  // generic work descriptor: owner + two tile indices
@@ -81,6 +82,11 @@ cudaError_t launch_pair_h(const DPair* pairs, const WorkItem* items, int nitems,
                           const double* exps, const double* ncoef, double* ws, double* ws_info, bool solid,
                           int fold_lcap, int fold_qcap, int fold_wcap, unsigned* status,
                           cudaStream_t st);  // solid fold: largest l of the pairs, Q and W rows
+// J/K digestion of the blocks at ws + out_off, one CTA per quartet (lx_jk.cu).  J or K may
+// be null.
+cudaError_t launch_jk_digest(const DQuartet* qd, const DPair* pairs, const DShell* sh, int nquartet,
+                             const double* ws, bool solid, const double* D, int64_t nbf, double* J, double* K,
+                             cudaStream_t st);
 cudaError_t launch_boys_r(const DQuartet* qd, const DPair* pairs, const WorkItem* items, int nitems, int lmax,
                           double* ws, unsigned* status, cudaStream_t st);  // lmax: largest L of the items
 // items grouped by tile shape: counts[v] items of shape v, in shape order; counters[v] is the

@@ -36,7 +36,8 @@ EXPORTS = sorted(["lx_eri_out_size", "lx_eri_workspace_size", "lx_eri_workspace_
                   "lx_mlp_grad", "lx_mlp_adam", "lx_eri_graph_create", "lx_eri_graph_launch",
                   "lx_eri_graph_destroy", "lx_eri_autotune", "lx_tune_export", "lx_tune_import", "lx_tune_clear",
                   "lx_router_set", "lx_eri_pairs_out_size", "lx_eri_pairs_workspace_size",
-                  "lx_eri_pairs_workspace_min", "lx_eri_pairs"])
+                  "lx_eri_pairs_workspace_min", "lx_eri_pairs", "lx_nbf", "lx_eri_jk_workspace_size",
+                  "lx_eri_jk_workspace_min", "lx_eri_jk"])
 TILE_SHAPES = ["32x64", "64x32", "32x32", "64x64"]
 MLP_NIN = 20
 MLP_WIDTH = 64
@@ -45,7 +46,7 @@ LX_PATH_SPLIT = 0x2
 LX_PATH_ROUTED = 0x4
 LX_TIME_STAGES = 0x200
 PATH_FLAGS = {"fp64": 0, "split": LX_PATH_SPLIT, "routed": LX_PATH_ROUTED}
-STAGES = ["norm", "pair_h", "boys_r", "gemm1", "gemm2", "split"]
+STAGES = ["norm", "pair_h", "boys_r", "gemm1", "gemm2", "split", "digest"]
 
 
 class LxError(RuntimeError):
@@ -89,6 +90,14 @@ def load(build_if_missing: bool = True):
         lib.lx_eri_pairs.argtypes = [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_i64, c_vp, c_i64, c_i32, c_vp, c_vp, c_sz,
                                      c_vp]
         lib.lx_eri_pairs.restype = ctypes.c_int
+        lib.lx_nbf.argtypes = [c_vp, c_i32, c_i32]
+        lib.lx_nbf.restype = c_i64
+        for name in ("lx_eri_jk_workspace_size", "lx_eri_jk_workspace_min"):
+            getattr(lib, name).argtypes = [c_vp, c_i32, c_vp, c_i64, c_i32]
+            getattr(lib, name).restype = c_i64
+        lib.lx_eri_jk.argtypes = [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_i64, c_i32, c_vp, c_vp, c_vp, c_vp, c_sz,
+                                  c_vp]
+        lib.lx_eri_jk.restype = ctypes.c_int
         lib.lx_eri_batch_static.argtypes = [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_i64, c_i32, c_vp, c_vp]
         lib.lx_eri_batch_static.restype = ctypes.c_int
         lib.lx_eri_sync_status.argtypes = [c_vp]
@@ -315,6 +324,59 @@ def eri_pairs(basis: dict, bra_pairs, ket_pairs, solid: bool = True, device="cud
     b.run(out, ws, stream)
     sync_status(stream)
     return out[: b.out_size].view(b.shape)
+
+
+class JKBatch(Batch):
+    """A quartet list digested into Coulomb and exchange matrices (lx_eri_jk)."""
+
+    def __init__(self, basis: dict, quartets, solid: bool, path: str = "fp64"):
+        super().__init__(basis, quartets, solid, path=path)
+        n = load().lx_nbf(_ptr(self.shells), len(self.shells), self.flags)
+        if n < 0:
+            raise LxError(int(n), "lx_nbf")
+        self.nbf = int(n)
+
+    def _need(self, fn, where):
+        n = fn(_ptr(self.shells), len(self.shells), _ptr(self.quartets), len(self.quartets), self.flags)
+        if n < 0:
+            raise LxError(int(n), where)
+        return int(n)
+
+    def workspace_size(self) -> int:
+        return self._need(load().lx_eri_jk_workspace_size, "lx_eri_jk_workspace_size")
+
+    def workspace_min(self) -> int:
+        return self._need(load().lx_eri_jk_workspace_min, "lx_eri_jk_workspace_min")
+
+    def run_jk(self, D, J, K, workspace, stream=None, time_stages: bool = False):
+        """Enqueue lx_eri_jk: D, J, K float64 CUDA tensors (nbf x nbf; J or K may be None)."""
+        flags = self.flags | (LX_TIME_STAGES if time_stages else 0)
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr() if t is not None else None)  # noqa: E731
+        rc = load().lx_eri_jk(_ptr(self.shells), len(self.shells), _ptr(self.exps), _ptr(self.coefs),
+                              len(self.exps), _ptr(self.quartets), len(self.quartets), flags, ptr(D), ptr(J), ptr(K),
+                              ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size(),
+                              ctypes.c_void_p(_stream_ptr(stream)))
+        _check(rc, "lx_eri_jk")
+
+
+def eri_jk(basis: dict, quartets, D, solid: bool = True, want: str = "JK", device="cuda",
+           workspace_limit: int | None = None, stream=None, path: str = "fp64"):
+    """Coulomb and exchange contributions of the quartets to density D (nbf x nbf, any array
+    or tensor): returns (J, K) as float64 CUDA tensors (None for the one not in `want`)."""
+    import torch
+    b = JKBatch(basis, quartets, solid, path=path)
+    Dt = torch.as_tensor(np.asarray(D, dtype=np.float64) if not isinstance(D, torch.Tensor) else D,
+                         dtype=torch.float64, device=device).contiguous()
+    if Dt.shape != (b.nbf, b.nbf):
+        raise ValueError(f"D must be {b.nbf} x {b.nbf}")
+    J = torch.zeros_like(Dt) if "J" in want else None
+    K = torch.zeros_like(Dt) if "K" in want else None
+    need = b.workspace_size()
+    if workspace_limit is not None:
+        need = max(min(need, int(workspace_limit)), b.workspace_min())
+    b.run_jk(Dt, J, K, alloc_workspace(need, device), stream)
+    sync_status(stream)
+    return J, K
 
 
 def stage_times(stream=None) -> tuple[dict, dict]:

@@ -220,3 +220,31 @@ def test_pair_lists_sizes_and_errors():
                           b["coefs"].ctypes.data_as(ctypes.c_void_p), len(b["exps"]), None, 0, None, 0, 1, None,
                           None, 0, None)
     assert rc == 0
+
+
+def test_jk_entry_points_validate_on_the_host():
+    b = _pairs_basis()
+    lib = lx.load()
+    sh = lx.pack_shells(b)
+    c = ctypes.c_void_p
+    assert lib.lx_nbf(sh.ctypes.data_as(c), len(sh), lx.LX_SOLID) == 11 + 11 + 13 + 13 + 9
+    assert lib.lx_nbf(sh.ctypes.data_as(c), len(sh), lx.LX_CART) == 21 + 21 + 28 + 28 + 15
+    assert lib.lx_nbf(sh.ctypes.data_as(c), len(sh), 0x1000) == -5
+    jb = lx.JKBatch(b, [[0, 1, 2, 3], [4, 4, 0, 2]], True)
+    assert jb.nbf == 57
+    # the J/K workspace also holds each quartet's block
+    plain = lx.Batch(b, [[0, 1, 2, 3], [4, 4, 0, 2]], True)
+    assert jb.workspace_size() >= plain.workspace_size() + 8 * (121 * 169 + 81 * 143)
+    assert plain.workspace_min() < jb.workspace_min() <= jb.workspace_size()
+    q = jb.quartets
+    ex, co = np.ascontiguousarray(b["exps"]), np.ascontiguousarray(b["coefs"])
+
+    def call(D, J, K, flags=lx.LX_SOLID, nq=len(q)):
+        return lib.lx_eri_jk(sh.ctypes.data_as(c), len(sh), ex.ctypes.data_as(c), co.ctypes.data_as(c), len(ex),
+                             q.ctypes.data_as(c), nq, flags, c(D), c(J), c(K), c(1 << 20), 1 << 20, None)
+    assert call(None, 8, 8) == -1            # no density
+    assert call(8, None, None) == -1         # neither output
+    assert call(8, 8, 8, flags=0x40000000) == -5   # the planner's internal bit is not a caller flag
+    assert call(8, 8, 8, nq=0) == 0          # empty list: nothing to do
+    # lx_eri_batch refuses the internal bit as well
+    assert _call_batch(b, [[0, 1, 2, 3]], flags=lx.LX_SOLID | 0x40000000) == -5
