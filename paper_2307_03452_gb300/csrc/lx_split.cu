@@ -149,43 +149,47 @@ __device__ inline double scale2(double x, int s) {
     return __longlong_as_double((bits & ~(0x7FFll << 52)) | ((long long)ne << 52));
 }
 
-// q = round(x * 2^(W - e)) for |x| < 2^e, from the bit pattern (no FP64 arithmetic).
-__device__ inline long long fixed_of(double x, int e) {
+// Biased exponent field of x 2^s: 0 if x is zero or subnormal or x 2^s underflows the normal
+// range (the value scale2 would give), capped at 2047.
+__device__ inline int exp_field_scaled(double x, int s) {
+    const int ex = exp_field(x);
+    return ex > 0 ? min(max(ex + s, 0), 2047) : 0;
+}
+
+// q = round(x 2^s 2^(W - e)) for |x 2^s| < 2^e, from the bit pattern (no FP64 arithmetic);
+// equal to the rounding of scale2(x, s), so a scaled value that underflows gives 0.
+__device__ inline long long fixed_of(double x, int s, int e) {
     const long long bits = __double_as_longlong(x);
     const int ex = (int)((bits >> 52) & 0x7FF);
-    if (ex == 0) return 0;  // zero or subnormal: below any row scale that matters
+    const int ne = ex + s;
+    if (ex == 0 || ne <= 0) return 0;  // zero or subnormal: below any row scale that matters
     const long long mant = (bits & 0xFFFFFFFFFFFFFll) | (1ll << 52);
-    const int rs = 1075 - ex - SPLIT_W + e;  // right shift, >= 53 - W > 0
+    const int rs = 1075 - ne - SPLIT_W + e;  // right shift, >= 53 - W > 0
     long long q = 0;
     if (rs < 63) q = (mant + (1ll << (rs - 1))) >> rs;
     return bits < 0 ? -q : q;
 }
 
 // The digits of q (|q| <= 2^48), most significant first, balanced: |d_0| <= 2^BETA and
-// |d_s| <= 2^(BETA-1) for s > 0.  They are taken from the bottom, three from each 24-bit
-// half of q in 32-bit integers (d = ((x + 128) mod 256) - 128, then x = (x - d) / 256), and
-// returned as FP32 bit patterns: 0x4B400000 + d is the FP32 number 1.5 * 2^23 + d for
-// |d| < 2^22, so subtracting 1.5 * 2^23 leaves d exactly.  A digit has at most 8 significant
-// bits, so its BF16 pattern is the upper half of its FP32 pattern.
+// -2^(BETA-1) <= d_s < 2^(BETA-1) for s > 0.  Adding B = 2^(BETA-1) (1 + 256 + ... + 256^4)
+// makes the five low digits plain bytes: byte j of y = q + B is d_(5-j) + 128, with every
+// carry done by the one 64-bit add, and d_0 = floor(y / 2^40).  Each byte becomes an FP32 bit
+// pattern with one byte permute: [byte, 0, 0x40, 0x4B] is the FP32 number 1.5 2^23 + byte,
+// so subtracting 1.5 2^23 + 128 leaves d exactly.  A digit has at most 8 significant bits,
+// so its BF16 pattern is the upper half of its FP32 pattern.
 static_assert(SPLIT_NSLICE == 6 && SPLIT_BETA == 8, "digit extraction assumes 6 digits of 8 bits");
 __device__ inline void digits_of(long long q, uint32_t (&f)[SPLIT_NSLICE]) {
-    int lo = (int)(q & 0xFFFFFF);  // q = hi 2^24 + lo, 0 <= lo < 2^24
-    int hi = (int)(q >> 24);
-    int d[SPLIT_NSLICE];
-#pragma unroll
-    for (int s = SPLIT_NSLICE - 1; s >= 3; --s) {
-        d[s] = ((lo + 128) & 255) - 128;
-        lo = (lo - d[s]) >> 8;
-    }
-    hi += lo;  // carry out of the low half (0 or 1)
-#pragma unroll
-    for (int s = 2; s >= 1; --s) {
-        d[s] = ((hi + 128) & 255) - 128;
-        hi = (hi - d[s]) >> 8;
-    }
-    d[0] = hi;
-#pragma unroll
-    for (int s = 0; s < SPLIT_NSLICE; ++s) f[s] = __float_as_uint(__int_as_float(0x4B400000 + d[s]) - 12582912.0f);
+    const long long y = q + 0x8080808080ll;
+    const uint32_t lo = (uint32_t)y;
+    const int hi = (int)(y >> 32);
+    constexpr uint32_t MAGIC = 0x4B400000u;  // 1.5 2^23
+    constexpr float BIAS = 12582912.0f + 128.0f;
+    f[5] = __float_as_uint(__uint_as_float(__byte_perm(lo, MAGIC, 0x7650)) - BIAS);
+    f[4] = __float_as_uint(__uint_as_float(__byte_perm(lo, MAGIC, 0x7651)) - BIAS);
+    f[3] = __float_as_uint(__uint_as_float(__byte_perm(lo, MAGIC, 0x7652)) - BIAS);
+    f[2] = __float_as_uint(__uint_as_float(__byte_perm(lo, MAGIC, 0x7653)) - BIAS);
+    f[1] = __float_as_uint(__uint_as_float(__byte_perm((uint32_t)hi, MAGIC, 0x7650)) - BIAS);
+    f[0] = __float_as_uint(__int_as_float((int)MAGIC + (hi >> 8)) - 12582912.0f);
 }
 
 // Digits of 8 consecutive values (k0 .. k0+7, k0 a multiple of 8) of one row, written as one
@@ -231,7 +235,8 @@ __device__ inline int row_max16(int mx) {
     return mx;
 }
 
-// Split 8 rows (4 pairs) through value(row, k0, v[8]) (zeros outside the matrix): digit planes
+// Split 8 rows (4 pairs) through value(row, k0, v[8], sh[8]) (values and the powers of two
+// they are scaled by; zeros outside the matrix): digit planes
 // of row tile T with nkb K blocks, one int exponent per row.  fixed: every value lies in
 // (-1, 1) and every row takes e = 0, so the exponent pass is skipped.
 template <typename Value>
@@ -244,19 +249,21 @@ __device__ __forceinline__ void split_8rows(int r0, int nkb, int T, bool fixed, 
         if (!fixed) {
             for (int k0 = c8; k0 < nkb * SPLIT_KB; k0 += 128) {
                 double v[8];
-                value(row, k0, v);
+                int sh[8];
+                value(row, k0, v, sh);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) mx = max(mx, exp_field(v[i]));
+                for (int i = 0; i < 8; ++i) mx = max(mx, exp_field_scaled(v[i], sh[i]));
             }
             mx = row_max16(mx);
         }
         const int e = mx > 0 ? mx - 1022 : 0;  // |x| < 2^e over the row
         for (int k0 = c8; k0 < nkb * SPLIT_KB; k0 += 128) {
             double v[8];
-            value(row, k0, v);
+            int sh[8];
+            value(row, k0, v, sh);
             long long q[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) q[i] = mx > 0 ? fixed_of(v[i], e) : 0ll;
+            for (int i = 0; i < 8; ++i) q[i] = mx > 0 ? fixed_of(v[i], sh[i], e) : 0ll;
             store_digit_group(dig, row, k0, T, nkb, q);
         }
         if ((lane & 15) == 0) exps[row] = e;
@@ -270,15 +277,15 @@ __device__ __forceinline__ void split_rows_item(const SplitRowsDesc* __restrict_
     const double* src = src_base + d.src_off;
     const int* shift = d.shift_off >= 0 ? reinterpret_cast<const int*>(ws + d.shift_off) : nullptr;
     split_8rows(it.a, d.nkb, d.T, d.fixed != 0, reinterpret_cast<__nv_bfloat16*>(ws + d.dig_off),
-                reinterpret_cast<int*>(ws + d.exp_off), [&](int row, int k0, double (&v)[8]) {
+                reinterpret_cast<int*>(ws + d.exp_off), [&](int row, int k0, double (&v)[8], int (&sh)[8]) {
                     const bool live = row < d.rows;
                     const double* sr = src + (int64_t)row * d.ld;
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int k = k0 + i;
-                        double x = 0.0;
-                        if (live && k < d.K) x = shift ? scale2(sr[k], d.shift_sign * shift[k]) : sr[k];
-                        v[i] = x;
+                        const bool in = live && k < d.K;
+                        v[i] = in ? sr[k] : 0.0;
+                        sh[i] = in && shift ? d.shift_sign * shift[k] : 0;
                     }
                 });
 }
@@ -354,10 +361,7 @@ __device__ __forceinline__ void split_r_item(const DQuartet* __restrict__ qd, co
         int sh[8];
         group(SPLIT_KB * kb + c8, v, sh);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int ef = exp_field(v[i]);
-            mx = max(mx, ef > 0 ? min(max(ef + sh[i], 0), 2047) : 0);
-        }
+        for (int i = 0; i < 8; ++i) mx = max(mx, exp_field_scaled(v[i], sh[i]));
     }
     mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
     mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
@@ -369,7 +373,7 @@ __device__ __forceinline__ void split_r_item(const DQuartet* __restrict__ qd, co
         group(SPLIT_KB * kb + c8, v, sh);
         long long qv[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) qv[i] = mx > 0 ? fixed_of(scale2(v[i], sh[i]), e) : 0ll;
+        for (int i = 0; i < 8; ++i) qv[i] = mx > 0 ? fixed_of(v[i], sh[i], e) : 0ll;
         store_digit_group(dig, row, SPLIT_KB * kb + c8, SPLIT_TA, s.nkb1, qv);
     }
     if ((lane & 3) == 0) reinterpret_cast<int*>(ws + s.a1_exp)[row] = e;
