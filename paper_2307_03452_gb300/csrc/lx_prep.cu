@@ -220,7 +220,7 @@ __device__ __forceinline__ void fold_stage(int grp0, int nrow, const int* __rest
 }
 
 // One CTA per primitive pair, solid-harmonic rows:
-//   H[m_a m_b][p] = pref * sign(p) * sum_a C_a[m_a][a] sum_b C_b[m_b][b] E_ab^p
+//   H[m_a m_b][p] = sign(p) * sum_a (pref C_a[m_a][a]) sum_b C_b[m_b][b] E_ab^p
 // by the factorised fold (one Cartesian index at a time, structural zeros skipped; the row
 // groups are built on the host).  Per m_b: the Q stage, a barrier, the W stage, a barrier,
 // then the H stage of m_b together with the Q stage of m_b + 1 (which touch disjoint
@@ -250,11 +250,14 @@ __global__ void __launch_bounds__(PAIR_SOLID_THREADS, 2) pair_h_solid_kernel(
         Q[c_fold.pair[la][lb].maxq] = 0.0;
     }
     pair_setup(pr, kp, sh, exps, ncoef, ws_info, E, etab, &s_pref);
+    // the prefactor rides on C_a (one multiply per coefficient instead of one per H entry);
+    // each thread scales the entries it loaded, and the first read is two barriers away
+    const double pref = s_pref;
+    for (int i = threadIdx.x; i < (2 * la + 1) * nca; i += blockDim.x) Csa[i] *= pref;
 
     const int np = pr.np;
     const int64_t ldh = (int64_t)pr.Kab * np;
     double* H = ws + pr.h_off + (int64_t)kp * np;
-    const double pref = s_pref;
     const double* Ex = E;
     const double* Ey = E + etab;
     const double* Ez = E + 2 * etab;
@@ -280,7 +283,9 @@ __global__ void __launch_bounds__(PAIR_SOLID_THREADS, 2) pair_h_solid_kernel(
                        const int ma = o & 15, p = o >> 4;
                        const int tuv = g_tuv_prep[p];
                        const bool neg = sign && (((tuv & 255) + ((tuv >> 8) & 255) + (tuv >> 16)) & 1);
-                       H[(int64_t)(ma * nsb + mb) * ldh + p] = (neg ? -pref : pref) * v;
+                       // the sign as a bit flip, off the FP64 pipe
+                       H[(int64_t)(ma * nsb + mb) * ldh + p] =
+                           __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
                    });
         if (mb + 1 < nsb) fold_stage(sg[1].q_grp0, sg[1].q_nrow, c_fold.q_gptr, c_fold.q_ent, q_term, q_store);
         __syncthreads();
