@@ -49,6 +49,7 @@ def parse_args(argv=None):
                    help="skip the (hh|hh)+(ii|ii) K=1..3 split-path workload")
     p.add_argument("--no-routed", action="store_true", help="skip the routed-workload sample")
     p.add_argument("--no-pairs", action="store_true", help="skip the bra-list x ket-list (engine form) workload")
+    p.add_argument("--pairs", type=int, default=64, help="bra pairs = ket pairs of the engine-form and J/K workloads")
     p.add_argument("--routed-quartets", type=int, default=4000)
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
     p.add_argument("--sweep", action="store_true",
@@ -568,7 +569,7 @@ def main(argv=None):
     # built once and shared by its 64 quartets
     pairs = None
     if not args.no_pairs:
-        pbas, pbra, pket = inputs.iiii_pairs()
+        pbas, pbra, pket = inputs.iiii_pairs(args.pairs, args.pairs)
         pq = [(a, b, c, d) for (a, b) in pbra for (c, d) in pket]
         pg1, pg2, _ = gemm_flops(pbas, pq, True)
         pairs = {"workload": f"{len(pbra)} (ii) bra pairs x {len(pket)} (ii) ket pairs = {len(pq)} quartets, K = 1, "
@@ -595,7 +596,7 @@ def main(argv=None):
     # digested from the workspace into J and K instead of being returned
     jk = None
     if not args.no_pairs:
-        pbas, pbra, pket = inputs.iiii_pairs()
+        pbas, pbra, pket = inputs.iiii_pairs(args.pairs, args.pairs)
         pq = np.array([(a, b, c, d) for (a, b) in pbra for (c, d) in pket], np.int32)
         jb_ = {p_: lx.JKBatch(pbas, pq, True, path=p_) for p_ in ("fp64", "split")}
         nbf = jb_["fp64"].nbf
