@@ -14,8 +14,9 @@
 // of it: the splitting works on the bit patterns of the FP64 inputs.
 //
 // Kernels:
-//   split_rows_kernel  FP64 row-major matrix rows -> digit planes + row exponents
-//   split_r_kernel     rows q of the [p|q] operand gathered from [r]^(0) -> digit planes
+//   split_operands_kernel  rows q of the [p|q] operand gathered from [r]^(0), and the H
+//                      rows, -> digit planes + row exponents (GEMM1 operands, H_ket)
+//   split_rows_kernel  FP64 row-major matrix rows ([ab|q]) -> digit planes + row exponents
 //   colmax_kernel      column scales of the H matrices (powers of two along K)
 //   split_gemm_kernel  D = A B^T on tcgen05 (M tile 128, N tile <= 32, K blocks of 32),
 //                      persistent, operand blocks streamed by bulk TMA copies into a
@@ -379,18 +380,6 @@ __device__ __forceinline__ void split_r_item(const DQuartet* __restrict__ qd, co
     if ((lane & 3) == 0) reinterpret_cast<int*>(ws + s.a1_exp)[row] = e;
 }
 
-__global__ void __launch_bounds__(256) split_r_kernel(const DQuartet* __restrict__ qd,
-                                                      const SplitQuartet* __restrict__ sq,
-                                                      const WorkItem* __restrict__ items, int nitems,
-                                                      const double* __restrict__ wsd, char* __restrict__ ws) {
-    __shared__ int tab_n[NTAB], tab_i[NTAB];
-    hermite_tables(tab_n, tab_i);
-    __syncthreads();
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (warp >= nitems) return;
-    split_r_item(qd, sq, items[warp], wsd, ws, tab_n, tab_i);
-}
-
 // The operands of GEMM1 and the H operand of GEMM2 in one launch: split_r items ([p|q]^T rows,
 // issue-bound gathers) and split_rows items (H rows, load-latency bound) in alternating blocks,
 // so that the two kinds share the SMs.  8 warps (items) per block.
@@ -681,15 +670,6 @@ cudaError_t launch_split_rows(const SplitRowsDesc* descs, const WorkItem* items,
     const int warps_per_block = 8;
     split_rows_kernel<<<(nitems + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
         descs, items, nitems, src_base, ws);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_split_r(const DQuartet* qd, const SplitQuartet* sq, const WorkItem* items, int nitems,
-                           const double* wsd, char* ws, cudaStream_t st) {
-    if (nitems <= 0) return cudaSuccess;
-    const int warps_per_block = 8;
-    split_r_kernel<<<(nitems + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
-        qd, sq, items, nitems, wsd, ws);
     return cudaGetLastError();
 }
 

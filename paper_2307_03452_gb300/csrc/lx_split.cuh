@@ -75,8 +75,6 @@ __host__ __device__ inline int64_t split_dig_bytes(int rows, int K, int T) {
 cudaError_t init_split_kernels(const int* host_tuv);
 cudaError_t launch_split_rows(const SplitRowsDesc* descs, const WorkItem* items, int nitems, const double* src_base,
                               char* ws, cudaStream_t st);
-cudaError_t launch_split_r(const DQuartet* qd, const SplitQuartet* sq, const WorkItem* items, int nitems,
-                           const double* wsd, char* ws, cudaStream_t st);
 // split_r items and split_rows items in one launch (8 items per block, kinds alternating)
 cudaError_t launch_split_operands(const DQuartet* qd, const SplitQuartet* sq, const WorkItem* items_r, int n_r,
                                   const SplitRowsDesc* descs, const WorkItem* items_w, int n_w, const double* wsd,
