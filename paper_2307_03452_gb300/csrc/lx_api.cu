@@ -440,6 +440,8 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             SplitQuartet q{};
             q.nkb1 = split_nkb(k1);
             q.nkb2 = split_nkb(k2);
+            const DPair &pb = P.pairs[d.pb], &pk = P.pairs[d.pk];
+            q.gidx_off = gidx_offset(sh[pb.sa].l + sh[pb.sb].l, sh[pk.sa].l + sh[pk.sb].l);
             P.sq.push_back(q);
             const int tb1 = split_tb(d.nab), tb2 = split_tb(d.ncd);
             P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k2, d.nab, k2, SPLIT_TA, q.nkb2, +1, 0, 0});  // A2: X

@@ -23,6 +23,7 @@
 //                      3-stage mbarrier ring, one thread issuing the MMAs, two TMEM
 //                      accumulator sets drained by eight warps.
 #include <cstdint>
+#include <mutex>
 #include <vector>
 
 #include "lx_internal.cuh"
@@ -304,47 +305,49 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const SplitRowsDesc* __
 // the 8 rows are processed at once: lane (rr, c) = (lane / 4, lane % 4) handles row r0 + rr
 // and columns 8c .. 8c+7 of every K block, so the gathers of neighbouring rows (neighbouring
 // Hermite indices) fall close together; the rows are gathered twice, once for the exponent.
-// Hermite triplets are carried as n | i << 8 | v << 16 (n = t+u+v, i = u+v), which add
-// componentwise, and hidx(t, u, v) = n(n+1)(n+2)/6 + i(i+1)/2 + v comes from two small tables.
-__device__ int g_niv_split[NHERM_TOT];
-constexpr int NTAB = 2 * LTOT + 2;
-__device__ __forceinline__ void hermite_tables(int* tab_n, int* tab_i) {
-    for (int j = threadIdx.x; j < NTAB; j += blockDim.x) {
-        tab_n[j] = j * (j + 1) * (j + 2) / 6;
-        tab_i[j] = j * (j + 1) / 2;
-    }
-}
+// The position of [p+q]^(0) in [r]^(0) comes from the class's index table (gidx_offset): 8
+// consecutive p of one primitive pair are one 16-byte load when they start on a multiple of 8
+// within the pair's block, which every group does when K_bra = 1.
+__device__ const uint16_t* g_gidx;
 
-// One split_r item (item.q = quartet, item.a = r0), by one warp; tab_n, tab_i from hermite_tables.
+// One split_r item (item.q = quartet, item.a = r0), by one warp.
 __device__ __forceinline__ void split_r_item(const DQuartet* __restrict__ qd, const SplitQuartet* __restrict__ sq,
                                              const WorkItem& it, const double* __restrict__ wsd,
-                                             char* __restrict__ ws, const int* tab_n, const int* tab_i) {
-    const int* niv = g_niv_split;
+                                             char* __restrict__ ws) {
     const int lane = threadIdx.x & 31;
     const DQuartet q = qd[it.q];
     const SplitQuartet s = sq[it.q];
     const int row = it.a + (lane >> 2), c8 = 8 * (lane & 3);
     const int nrow = q.kket * q.nq, K = q.kbra * q.np;
     const bool live = row < nrow;
-    int kq = 0, nq_ = 0;
-    if (live) {
-        kq = row / q.nq;
-        nq_ = niv[row - kq * q.nq];
-    }
+    const int kq = live ? row / q.nq : 0;
     const double* Rr = wsd + q.rr_off + (int64_t)kq * q.nr;
     const int64_t kp_stride = (int64_t)q.kket * q.nr;
     const int* c1 = reinterpret_cast<const int*>(ws + s.c1_off);
+    // this row's positions hidx(p + q) for p < Np
+    const uint16_t* G = g_gidx + s.gidx_off + (int64_t)(row - kq * q.nq) * ((q.np + 7) / 8 * 8);
     // [p+q]^(0) of columns k0 .. k0+7 (unscaled) and their shifts, walking (kp, p)
     auto group = [&](int k0, double (&v)[8], int (&sh)[8]) {
+        int kp = k0 / q.np, p = k0 - kp * q.np;
+        if (live && (p & 7) == 0 && p + 8 <= q.np && k0 + 8 <= K) {
+            // one primitive pair, 16-byte aligned: vector loads of positions and shifts
+            const uint4 g = *reinterpret_cast<const uint4*>(G + p);
+            const int4 ca = *reinterpret_cast<const int4*>(c1 + k0);
+            const int4 cb = *reinterpret_cast<const int4*>(c1 + k0 + 4);
+            const double* Rk = Rr + kp * kp_stride;
+            v[0] = Rk[g.x & 0xFFFF], v[1] = Rk[g.x >> 16], v[2] = Rk[g.y & 0xFFFF], v[3] = Rk[g.y >> 16];
+            v[4] = Rk[g.z & 0xFFFF], v[5] = Rk[g.z >> 16], v[6] = Rk[g.w & 0xFFFF], v[7] = Rk[g.w >> 16];
+            sh[0] = ca.x, sh[1] = ca.y, sh[2] = ca.z, sh[3] = ca.w;
+            sh[4] = cb.x, sh[5] = cb.y, sh[6] = cb.z, sh[7] = cb.w;
+            return;
+        }
         int k = k0;
-        int kp = k / q.np, p = k - kp * q.np;
 #pragma unroll
         for (int i = 0; i < 8; ++i, ++k) {
             double x = 0.0;
             int h = 0;
             if (live && k < K) {
-                const int w = niv[p] + nq_;
-                x = Rr[kp * kp_stride + tab_n[w & 255] + tab_i[(w >> 8) & 255] + (w >> 16)];
+                x = Rr[kp * kp_stride + G[p]];
                 h = c1[k];
             }
             v[i] = x;
@@ -389,9 +392,6 @@ __global__ void __launch_bounds__(256) split_operands_kernel(const DQuartet* __r
                                                              const SplitRowsDesc* __restrict__ descs,
                                                              const WorkItem* __restrict__ items_w, int n_w,
                                                              const double* __restrict__ wsd, char* __restrict__ ws) {
-    __shared__ int tab_n[NTAB], tab_i[NTAB];
-    hermite_tables(tab_n, tab_i);
-    __syncthreads();
     const int nb_r = (n_r + 7) / 8, nb_w = (n_w + 7) / 8, m = min(nb_r, nb_w);
     const int b = blockIdx.x;
     int kind, idx;  // kind 0: split_r, 1: split_rows
@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(256) split_operands_kernel(const DQuartet* __r
     }
     const int w = idx * 8 + (threadIdx.x >> 5);
     if (kind == 0) {
-        if (w < n_r) split_r_item(qd, sq, items_r[w], wsd, ws, tab_n, tab_i);
+        if (w < n_r) split_r_item(qd, sq, items_r[w], wsd, ws);
     } else {
         if (w < n_w) split_rows_item(descs, items_w[w], wsd, ws);
     }
@@ -691,12 +691,34 @@ cudaError_t launch_colmax(const ColMaxDesc* descs, const WorkItem* items, int ni
 
 cudaError_t init_split_kernels(const int* host_tuv) {
     cudaError_t e = cudaSuccess;
-    std::vector<int> niv(NHERM_TOT);
-    for (int k = 0; k < NHERM_TOT; ++k) {
-        const int t = host_tuv[k] & 255, u = (host_tuv[k] >> 8) & 255, v = host_tuv[k] >> 16;
-        niv[k] = (t + u + v) | ((u + v) << 8) | (v << 16);
+    // the [p+q] index table (built once per process; a device copy per device, kept for the
+    // life of the process)
+    static std::vector<uint16_t> table;
+    static std::mutex table_mutex;
+    {
+        std::lock_guard<std::mutex> lock(table_mutex);
+        if (table.empty()) {
+            table.assign((size_t)gidx_offset(GIDX_L, 0), 0);
+            for (int lb = 0; lb < GIDX_L; ++lb)
+                for (int lk = 0; lk < GIDX_L; ++lk) {
+                    uint16_t* blk = table.data() + gidx_offset(lb, lk);
+                    for (int q = 0; q < pyr(lk); ++q)
+                        for (int p = 0; p < pyr(lb); ++p) {
+                            const int a = host_tuv[p], b = host_tuv[q];
+                            const int t = (a & 255) + (b & 255), u = ((a >> 8) & 255) + ((b >> 8) & 255),
+                                      v = (a >> 16) + (b >> 16);
+                            blk[(size_t)q * gidx_ld(lb) + p] = (uint16_t)hidx(t, u, v);
+                        }
+                }
+        }
     }
-    if ((e = cudaMemcpyToSymbol(g_niv_split, niv.data(), sizeof(int) * NHERM_TOT)) != cudaSuccess) return e;
+    void* dev_table = nullptr;
+    if ((e = cudaMalloc(&dev_table, sizeof(uint16_t) * table.size())) != cudaSuccess) return e;
+    if ((e = cudaMemcpy(dev_table, table.data(), sizeof(uint16_t) * table.size(), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return e;
+    const uint16_t* p = static_cast<const uint16_t*>(dev_table);
+    if ((e = cudaMemcpyToSymbol(g_gidx, &p, sizeof(p))) != cudaSuccess) return e;
     return cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
 }
 

@@ -45,8 +45,26 @@ struct SplitQuartet {
     int64_t a2_dig, a2_exp;  // [ab|q] rows (nab), K = Kket Nq, columns scaled by 2^c2
     int64_t b2_dig, b2_exp;  // H_ket rows (ncd), columns scaled by 2^-c2
     int64_t c1_off, c2_off;  // int[Kbra Np], int[Kket Nq]
+    int64_t gidx_off;        // this class's block of the [p+q] index table (gidx_offset)
     int nkb1, nkb2;
 };
+
+// Index table of the [p|q] gathers: for l_bra, l_ket <= 2 LMAX, entry gidx_offset(l_bra,
+// l_ket) + q gidx_ld(l_bra) + p holds hidx(p + q) (the position of [p+q]^(0) in the [r]^(0)
+// vector of the quartet) as a 16-bit integer, for q < pyr(l_ket), p < pyr(l_bra); rows are
+// padded to a multiple of 8 entries so that 8 consecutive entries are one 16-byte load.
+constexpr int GIDX_L = 2 * LMAX + 1;  // l_bra (and l_ket) = 0 .. 2 LMAX
+__host__ __device__ inline int gidx_ld(int lbra) { return (pyr(lbra) + 7) / 8 * 8; }
+__host__ __device__ inline int64_t gidx_offset(int lbra, int lket) {
+    int64_t off = 0;
+    for (int b = 0; b < GIDX_L; ++b)
+        for (int k = 0; k < GIDX_L; ++k) {
+            if (b == lbra && k == lket) return off;
+            off += (int64_t)pyr(k) * gidx_ld(b);
+        }
+    return off;  // total size
+}
+static_assert(NHERM_TOT < 65536, "[r]^(0) positions fit 16 bits");
 
 // D = A B^T: A digits (row tiles of SPLIT_TA), B digits (row tiles of tb = split_tb(N)), both
 // with nkb K blocks; D written to (double*)C + c_off with row stride ldc (transpose: D[m][n] ->
