@@ -119,6 +119,7 @@ __device__ void gemm_tile(const DQuartet& q, const DPair* __restrict__ pairs, in
         __syncthreads();
 #pragma unroll
         for (int ks = 0; ks < BK; ks += 4) {
+            if (k0 + ks >= K) break;  // k steps wholly past K (zeros) are skipped
             double af[WM], bf[WN];
 #pragma unroll
             for (int i = 0; i < WM; ++i) af[i] = sm.As[wm + 8 * i + (lane >> 2)][ks + (lane & 3)];
