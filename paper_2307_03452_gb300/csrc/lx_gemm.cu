@@ -83,11 +83,29 @@ __device__ void gemm_tile(const DQuartet& q, const DPair* __restrict__ pairs, in
     for (int i = 0; i < WM; ++i)
 #pragma unroll
         for (int j = 0; j < WN; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
-    bool rowok[WM], colok[WN];
+    // 8-row (8-column) blocks past the edge are skipped; a block holding exactly one row
+    // (column) at the edge -- solid outputs have N_ab = (2l_a+1)(2l_b+1) = 1 mod 8 -- is done
+    // with scalar FMAs over the 32 lanes (lane = column x k step) at 1/8 of the MMA's work,
+    // in a loop of its own so that the MMA sequence stays as it is
+    bool rowok[WM], colok[WN], row1[WM], col1[WN], mma_ok[WM][WN];
+    bool edge = false;
 #pragma unroll
-    for (int i = 0; i < WM; ++i) rowok[i] = m0 + wm + 8 * i < M;
+    for (int i = 0; i < WM; ++i) {
+        rowok[i] = m0 + wm + 8 * i < M;
+        row1[i] = m0 + wm + 8 * i == M - 1;
+    }
 #pragma unroll
-    for (int j = 0; j < WN; ++j) colok[j] = n0 + wn + 8 * j < N;
+    for (int j = 0; j < WN; ++j) {
+        colok[j] = n0 + wn + 8 * j < N;
+        col1[j] = n0 + wn + 8 * j == N - 1;
+    }
+#pragma unroll
+    for (int i = 0; i < WM; ++i)
+#pragma unroll
+        for (int j = 0; j < WN; ++j) {
+            mma_ok[i][j] = rowok[i] && colok[j] && !row1[i] && !col1[j];
+            edge |= rowok[i] && colok[j] && (row1[i] || col1[j]);
+        }
 
     for (int k0 = 0; k0 < K; k0 += BK) {
         for (int e = tid; e < BM * BK; e += 128) {
@@ -129,21 +147,47 @@ __device__ void gemm_tile(const DQuartet& q, const DPair* __restrict__ pairs, in
             for (int i = 0; i < WM; ++i)
 #pragma unroll
                 for (int j = 0; j < WN; ++j)
-                    if (rowok[i] && colok[j]) dmma(acc[i][j][0], acc[i][j][1], af[i], bf[j]);
+                    if (mma_ok[i][j]) dmma(acc[i][j][0], acc[i][j][1], af[i], bf[j]);
+        }
+        if (edge) {
+            // the one-row / one-column blocks: A[row][k lane%4] B[k lane%4][column lane/4]
+            // (or A[row lane/4][k lane%4] B[k lane%4][column]) summed per lane over k
+            for (int ks = 0; ks < BK && k0 + ks < K; ks += 4) {
+#pragma unroll
+                for (int i = 0; i < WM; ++i)
+#pragma unroll
+                    for (int j = 0; j < WN; ++j) {
+                        if (!(rowok[i] && colok[j]) || !(row1[i] || col1[j])) continue;
+                        const double a = sm.As[wm + 8 * i + (row1[i] ? 0 : lane >> 2)][ks + (lane & 3)];
+                        const double b = sm.Bs[ks + (lane & 3)][wn + 8 * j + (row1[i] ? lane >> 2 : 0)];
+                        acc[i][j][0] = fma(a, b, acc[i][j][0]);
+                    }
+            }
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < WM; ++i) {
-        const int row = m0 + wm + 8 * i + (lane >> 2);
-        if (row >= M) continue;
+    for (int i = 0; i < WM; ++i)
 #pragma unroll
         for (int j = 0; j < WN; ++j) {
+            if (!(rowok[i] && colok[j])) continue;
+            if (row1[i] || col1[j]) {
+                // sum the four k partials (lanes 4c .. 4c+3); lane 4c then holds entry c
+                double v = acc[i][j][0];
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                if ((lane & 3) != 0) continue;
+                const int row = m0 + wm + 8 * i + (row1[i] ? 0 : lane >> 2);
+                const int col = n0 + wn + 8 * j + (row1[i] ? lane >> 2 : 0);
+                if (row < M && col < N) C[(int64_t)row * ldc + col] = v;
+                continue;
+            }
+            const int row = m0 + wm + 8 * i + (lane >> 2);
+            if (row >= M) continue;
             const int col = n0 + wn + 8 * j + 2 * (lane & 3);
             if (col < N) C[(int64_t)row * ldc + col] = acc[i][j][0];
             if (col + 1 < N) C[(int64_t)row * ldc + col + 1] = acc[i][j][1];
         }
-    }
 }
 
 // Persistent, one instantiation per tile shape (each keeps its own register budget): every
