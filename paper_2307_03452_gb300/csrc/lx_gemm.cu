@@ -195,7 +195,7 @@ __device__ void gemm_tile(const DQuartet& q, const DPair* __restrict__ pairs, in
 // left (item.q = quartet, item.a = M tile, item.b = N tile).  The planner groups items by
 // shape and orders each group by decreasing cost.
 template <int MODE, int WM, int WN>
-__global__ void __launch_bounds__(128) gemm_kernel(const DQuartet* __restrict__ qd, const DPair* __restrict__ pairs,
+__global__ void __launch_bounds__(128, WM * WN > 8 ? 4 : 8) gemm_kernel(const DQuartet* __restrict__ qd, const DPair* __restrict__ pairs,
                                                    const WorkItem* __restrict__ items, int nitems,
                                                    const double* __restrict__ ws, double* __restrict__ cout,
                                                    int* __restrict__ counter) {
