@@ -376,7 +376,9 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             for (int k = 0; k < d.kbra * d.kket; ++k) P.items_br.push_back({i, k, 0, 0});
             P.br_lmax = std::max(P.br_lmax, d.L);
             if (split) continue;
-            int v1 = GEMM_V32x64, v2 = GEMM_V32x64;
+            // untuned: 64-row tiles once the bra has 128 rows or more (measured on (ii|ii)),
+            // 32-row tiles for smaller classes
+            int v1 = d.nab >= 128 ? GEMM_V64x32 : GEMM_V32x64, v2 = v1;
             auto f = g_tune.find(tune_key(sh, qs[ch.q_begin + i], solid));
             if (f != g_tune.end()) {
                 v1 = f->second.v1;
