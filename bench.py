@@ -71,7 +71,7 @@ def nfun(l, solid):
 # DRAM bytes per quartet of one launch, from single ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum) of these kernels on 256 solid (ii|ii) K = 1 quartets; a launch's
 # traffic grows with its quartet count.  Valid for that workload and these kernel builds.
-NCU_BYTES_PER_QUARTET = {"gemm1": 311.649024e6 / 256, "split_gemm1": 1186.914816e6 / 256}
+NCU_BYTES_PER_QUARTET = {"gemm1": 311.383296e6 / 256, "split_gemm1": 1186.914816e6 / 256}
 
 
 def gemm_flops(basis, quartets, solid):
