@@ -105,6 +105,7 @@ int ensure_device(unsigned** status) {
         if ((e = init_prep_tables(solid.data(), tuv.data(), &g_fold)) != cudaSuccess) return cuda_fail(e);
         if ((e = init_tuv_table(tuv.data())) != cudaSuccess) return cuda_fail(e);
         if ((e = init_split_kernels(tuv.data())) != cudaSuccess) return cuda_fail(e);
+        if ((e = init_jk_kernels()) != cudaSuccess) return cuda_fail(e);
         if ((e = init_router_kernels()) != cudaSuccess) return cuda_fail(e);
         void* p = nullptr;
         if ((e = cudaGetSymbolAddress(&p, g_status_word)) != cudaSuccess) return cuda_fail(e);
@@ -205,7 +206,9 @@ size_t quartet_bytes(const lx_shell* sh, const lx_quartet& q, int flags) {
     int64_t items = kbra * kket;
     // + 256 bytes per data block: each block starts on a 256-byte boundary
     size_t bytes = sizeof(DQuartet) + 8 * (size_t)(kbra * kket * pyr(L) + nab * n1) + 512;
-    if (flags & JK_DIGEST) bytes += 8 * (size_t)(nab * ncd) + 256;  // the block, digested in place
+    // J/K: the split path digests each block from the workspace; the FP64 path contracts
+    // [ab|q] directly and stores no block
+    if ((flags & JK_DIGEST) && split) bytes += 8 * (size_t)(nab * ncd) + 256;
     if (!split) {
         // bound: the 32 x 32 tile gives the most work items
         items += ((nab + 31) / 32) * ((n1 + 31) / 32);
@@ -289,6 +292,8 @@ struct ChunkPlan {
     std::vector<WorkItem> items_h, items_br, items_g1, items_g2;
     int br_lmax = 0;  // largest L of the chunk's quartets
     int fold_lcap = 0, fold_qcap = 0, fold_wcap = 0;  // solid fold: largest l, Q and W rows of the chunk's pairs
+    int jkd_qc = 0;          // J/K on the FP64 path: chunk width of jk_direct_kernel
+    size_t jkd_smem = 0;     // and its shared memory
     size_t off_pairs = 0, off_quartets = 0, off_h = 0, off_br = 0, off_g1 = 0, off_g2 = 0, off_data = 0;
     int g1_counts[GEMM_NVARIANT] = {0, 0, 0, 0}, g2_counts[GEMM_NVARIANT] = {0, 0, 0, 0};
     size_t off_counters = 0;  // 2 x GEMM_NVARIANT work counters, uploaded as zeros with the blob
@@ -314,6 +319,8 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     P.items_br.clear();
     P.br_lmax = 0;
     P.fold_lcap = P.fold_qcap = P.fold_wcap = 0;
+    P.jkd_qc = 0;
+    P.jkd_smem = 0;
     P.items_g1.clear();
     P.items_g2.clear();
     P.srd.clear();
@@ -394,12 +401,33 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
                     P.items_g1.push_back({i, m, n, v1});
                     cost1.push_back((int64_t)gemm_bm(v1) * gemm_bn(v1) * k1);
                 }
+            if (jk) continue;  // J/K straight from [ab|q]: no second transform
             for (int m = 0; m < mt2; ++m)
                 for (int n = 0; n < nt2; ++n) {
                     P.items_g2.push_back({i, m, n, v2});
                     cost2.push_back((int64_t)gemm_bm(v2) * gemm_bn(v2) * n1);
                 }
         }
+    }
+    if (jk && !split) {
+        // chunk width of jk_direct_kernel: the widest whose shared memory lets 2 CTAs share an
+        // SM, else the widest that fits at all
+        P.jkd_qc = 0;
+        for (int pass = 0; pass < 2 && P.jkd_qc == 0; ++pass)
+            for (int qc = 16; qc >= 1; qc /= 2) {
+                size_t need = 0;
+                for (int i = 0; i < (int)P.quartets.size(); ++i) {
+                    const lx_quartet& qq = qs[ch.q_begin + i];
+                    const int nb_ = nfun(sh[qq.s[1]].l, solid), nc_ = nfun(sh[qq.s[2]].l, solid),
+                              nd_ = nfun(sh[qq.s[3]].l, solid);
+                    need = std::max(need, jk_direct_smem(P.quartets[i].nab, P.quartets[i].ncd, nb_, nc_, nd_, qc));
+                }
+                if (need <= (pass == 0 ? (size_t)110 * 1024 : JKD_SMEM_MAX)) {
+                    P.jkd_qc = qc;
+                    P.jkd_smem = need;
+                    break;
+                }
+            }
     }
     // grouped by tile shape (one persistent launch each), largest tiles first within a shape:
     // the persistent launches hand items out round-robin
@@ -503,7 +531,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     for (auto& d : P.quartets) {
         d.rr_off = take((int64_t)d.kbra * d.kket * d.nr);
         d.x_off = take((int64_t)d.nab * d.kket * d.nq);
-        if (jk) d.out_off = take((int64_t)d.nab * d.ncd);  // doubles from the workspace base
+        if (jk && split) d.out_off = take((int64_t)d.nab * d.ncd);  // doubles from the workspace base
     }
     if (split) {
         auto take_bytes = [&](int64_t bytes) { return 8 * take((bytes + 7) / 8); };
@@ -752,6 +780,15 @@ int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector
             if ((e = launch_gemm1(d_q, d_pairs, d_ig1, P.g1_counts, ws, d_counters, status, st)) != cudaSuccess)
                 return cuda_fail(e);
             if ((e = tm.end(LX_STAGE_GEMM1, 1)) != cudaSuccess) return cuda_fail(e);
+            if (jk) {
+                // J and K straight from [ab|q]: no second transform, no stored block
+                if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
+                if ((e = launch_jk_direct(d_q, d_pairs, d_sh, (int)P.quartets.size(), P.jkd_qc, P.jkd_smem, ws,
+                                          solid, jk->D, jk->nbf, jk->J, jk->K, st)) != cudaSuccess)
+                    return cuda_fail(e);
+                if ((e = tm.end(LX_STAGE_DIGEST, 1)) != cudaSuccess) return cuda_fail(e);
+                continue;
+            }
             if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
             if ((e = launch_gemm2(d_q, d_pairs, d_ig2, P.g2_counts, ws, out, d_counters + GEMM_NVARIANT, status,
                                   st)) != cudaSuccess)

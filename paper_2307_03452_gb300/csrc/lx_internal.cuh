@@ -87,6 +87,14 @@ cudaError_t launch_pair_h(const DPair* pairs, const WorkItem* items, int nitems,
 cudaError_t launch_jk_digest(const DQuartet* qd, const DPair* pairs, const DShell* sh, int nquartet,
                              const double* ws, bool solid, const double* D, int64_t nbf, double* J, double* K,
                              cudaStream_t st);
+// J/K straight from X = [ab|q] and the ket H, one CTA per quartet walking K_ket N_q in
+// chunks of qc columns (lx_jk.cu); smem = jk_direct_smem(...) over the chunk's quartets.
+constexpr size_t JKD_SMEM_MAX = 200 * 1024;
+size_t jk_direct_smem(int nab, int ncd, int nb, int nc, int nd, int qc);
+cudaError_t launch_jk_direct(const DQuartet* qd, const DPair* pairs, const DShell* sh, int nquartet, int qc,
+                             size_t smem, const double* ws, bool solid, const double* D, int64_t nbf, double* J,
+                             double* K, cudaStream_t st);
+cudaError_t init_jk_kernels();
 cudaError_t launch_boys_r(const DQuartet* qd, const DPair* pairs, const WorkItem* items, int nitems, int lmax,
                           double* ws, unsigned* status, cudaStream_t st);  // lmax: largest L of the items
 // items grouped by tile shape: counts[v] items of shape v, in shape order; counters[v] is the

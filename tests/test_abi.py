@@ -232,10 +232,15 @@ def test_jk_entry_points_validate_on_the_host():
     assert lib.lx_nbf(sh.ctypes.data_as(c), len(sh), 0x1000) == -5
     jb = lx.JKBatch(b, [[0, 1, 2, 3], [4, 4, 0, 2]], True)
     assert jb.nbf == 57
-    # the J/K workspace also holds each quartet's block
+    # FP64 path: J and K straight from [ab|q], so no block is stored; split path: each
+    # quartet's block is kept in the workspace for the digestion kernel
     plain = lx.Batch(b, [[0, 1, 2, 3], [4, 4, 0, 2]], True)
-    assert jb.workspace_size() >= plain.workspace_size() + 8 * (121 * 169 + 81 * 143)
-    assert plain.workspace_min() < jb.workspace_min() <= jb.workspace_size()
+    assert jb.workspace_size() <= plain.workspace_size()
+    assert 0 < jb.workspace_min() <= jb.workspace_size()
+    js = lx.JKBatch(b, [[0, 1, 2, 3], [4, 4, 0, 2]], True, path="split")
+    ps = lx.Batch(b, [[0, 1, 2, 3], [4, 4, 0, 2]], True, path="split")
+    assert js.workspace_size() >= ps.workspace_size() + 8 * (121 * 169 + 81 * 143)
+    assert ps.workspace_min() < js.workspace_min() <= js.workspace_size()
     q = jb.quartets
     ex, co = np.ascontiguousarray(b["exps"]), np.ascontiguousarray(b["coefs"])
 
