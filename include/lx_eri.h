@@ -182,9 +182,11 @@ int lx_eri_pairs(const lx_shell* shells, int32_t nshell, const double* exps, con
  *     (atomically: the summation order, and so the last bits, vary from run to run); either
  *     may be NULL to skip it, not both.
  *   quartets[].out_offset is not used (it must still be >= 0).
- *   workspace: as lx_eri_batch, sized by lx_eri_jk_workspace_size / _min: each quartet's
- *     block is written there by the second transform and streamed once by the digestion
- *     kernel; nothing is written to a caller output.
+ *   workspace: as lx_eri_batch, sized by lx_eri_jk_workspace_size / _min.  On the FP64
+ *     path J and K are contracted straight from [ab|q] (no second transform, no block
+ *     stored); on the split path each quartet's block is written to the workspace by the
+ *     second transform and streamed once by the digestion kernel.  Nothing is written to a
+ *     caller output.
  * Flags, paths (LX_PATH_SPLIT, LX_PATH_ROUTED), staging and stream semantics as
  * lx_eri_batch; LX_TIME_STAGES times the digestion as LX_STAGE_DIGEST.  nbf <= 2^31 - 1.
  */
