@@ -153,19 +153,21 @@ __global__ void __launch_bounds__(JKD_THREADS) jk_direct_kernel(const DQuartet* 
             Hs[r * ld + c] = c < kc ? Hc[(int64_t)r * K2 + k0 + c] : 0.0;
         }
         __syncthreads();
-        for (int c = tid; c < qc; c += JKD_THREADS) {
-            double w = 0.0;
-            for (int i = 0; i < ncd; ++i) w = fma(Hs[i * ld + c], Dcd[i], w);
-            wv[c] = w;
-        }
-        for (int e = tid; e < nbc * qc; e += JKD_THREADS) {
-            const int nl = e / qc, c = e - nl * qc, n = nl / nc, l = nl - n * nc;
-            const double* dn = Dbd + n * nd;
-            const double* hl = Hs + (l * nd) * ld + c;
-            double g = 0.0;
-            for (int s = 0; s < nd; ++s) g = fma(dn[s], hl[s * ld], g);
-            Gs[nl * ld + c] = g;
-        }
+        if (J)
+            for (int c = tid; c < qc; c += JKD_THREADS) {
+                double w = 0.0;
+                for (int i = 0; i < ncd; ++i) w = fma(Hs[i * ld + c], Dcd[i], w);
+                wv[c] = w;
+            }
+        if (K)  // G only for K (J alone costs 4 n_ab K_ket N_q FLOPs per quartet)
+            for (int e = tid; e < nbc * qc; e += JKD_THREADS) {
+                const int nl = e / qc, c = e - nl * qc, n = nl / nc, l = nl - n * nc;
+                const double* dn = Dbd + n * nd;
+                const double* hl = Hs + (l * nd) * ld + c;
+                double g = 0.0;
+                for (int s = 0; s < nd; ++s) g = fma(dn[s], hl[s * ld], g);
+                Gs[nl * ld + c] = g;
+            }
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < JKD_OWN; ++i) {
