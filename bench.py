@@ -53,7 +53,7 @@ def parse_args(argv=None):
     p.add_argument("--routed-quartets", type=int, default=4000)
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
     p.add_argument("--sweep", action="store_true",
-                   help="instead of the benchmark line: one JSON line per integral class (dd|dd)..(ii|ii) "
+                   help="instead of the benchmark line: one JSON line per integral class (dd|dd)..(kk|kk) "
                         "and total contraction degree 1, 5, 25, both paths, with per-stage shares")
     return p.parse_args(argv)
 
@@ -294,7 +294,7 @@ def run_reference(args):
     return 0
 
 
-SWEEP_CLASSES = [(2, 2, 2, 2), (3, 3, 3, 3), (4, 4, 4, 4), (5, 5, 5, 5), (6, 6, 6, 6)]
+SWEEP_CLASSES = [(2, 2, 2, 2), (3, 3, 3, 3), (4, 4, 4, 4), (5, 5, 5, 5), (6, 6, 6, 6), (7, 7, 7, 7)]
 # total contraction degree K_bra K_ket -> per-shell degrees (a, b, c, d)
 SWEEP_K = {1: (1, 1, 1, 1), 5: (5, 1, 1, 1), 25: (5, 1, 5, 1)}
 
@@ -308,7 +308,7 @@ def run_sweep(args):
     torch.cuda.set_device(0)
     lx.load(build_if_missing=True)
     flush_buf = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    names = "spdfghi"
+    names = "spdfghik"
     for cls in SWEEP_CLASSES:
         for ktot, ks in SWEEP_K.items():
             la, lb, lc, ld = cls
