@@ -258,6 +258,12 @@ def cpu_baseline(basis, quartets, solid, seconds):
                       f"{dt:.1f} s of CPU work (plain McMurchie-Davidson in C, FP64, OpenMP)"}
 
 
+def workload_name(nq):
+    """The headline workload, as both arms name it in their config."""
+    return (f"(ii|ii) K=1 x{nq} quartets, 20-bohr cube, exponents log-uniform [0.05, 20], "
+            "real solid-harmonic output (13^4 per quartet); Cartesian (28^4) beside")
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle on the same workload and metric (bounded samples)."""
     import numpy as np
@@ -285,8 +291,10 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"(ii|ii) K=1, {args.nquartet} quartets, solid harmonics; each step a sample of "
-                                   f"{per_step} quartets of it", "parallelism": "host threads"},
+            "config": {"workload": workload_name(args.nquartet),
+                       "path": "CPU oracle (plain FP64 McMurchie-Davidson in C, OpenMP); each step a sample of "
+                               f"{per_step} quartets of the workload, solid output",
+                       "parallelism": f"{cores} host threads"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} quartets per step, {args.steps} timed steps"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -652,8 +660,7 @@ def main(argv=None):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"(ii|ii) K=1 x{nq} quartets, 20-bohr cube, exponents log-uniform [0.05, 20], "
-                                   "real solid-harmonic output (13^4 per quartet); Cartesian (28^4) beside",
+            "config": {"workload": workload_name(nq),
                        "path": "plain FP64", "l2": "512 MB buffer written between timed steps",
                        "parallelism": f"replicas x{world}"},
             "fp64_equiv_tflops": fp64_tf, "integrals_per_s": world * nint * args.steps / (total_ms * 1e-3),
