@@ -206,9 +206,13 @@ int lx_eri_jk(const lx_shell* shells, int32_t nshell, const double* exps, const 
  * paper; it exists only for such callers.
  *   Same inputs, output and stream semantics as lx_eri_batch.  The scratch is a fixed array
  *   of LX_STATIC_SCRATCH_BYTES inside the library's device image: every GPU that loads the
- *   library holds it until the process exits.  The call allocates no device memory.
- *   The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- *   with that device current); make that first call before any stream capture.
+ *   library holds it until the process exits.  The call allocates no device memory of its
+ *   own; the first call of any entry point on a device (this one included) uploads the
+ *   library's constant tables there once (the solid-fold row lists and the split path's
+ *   [p+q] index table, about 45 MB, held until exit), so a caller that must not allocate
+ *   makes that first call where allocation is still allowed.  The first call on a device
+ *   also looks up the array's device address (cudaGetSymbolAddress, with that device
+ *   current); make that first call before any stream capture.
  *   A batch whose smallest workspace (lx_eri_workspace_min) exceeds LX_STATIC_SCRATCH_BYTES
  *   is rejected with LX_ERR_STATIC_SCRATCH; larger batches that fit one quartet at a time are
  *   processed in chunks.
