@@ -253,3 +253,15 @@ def test_jk_entry_points_validate_on_the_host():
     assert call(8, 8, 8, nq=0) == 0          # empty list: nothing to do
     # lx_eri_batch refuses the internal bit as well
     assert _call_batch(b, [[0, 1, 2, 3]], flags=lx.LX_SOLID | 0x40000000) == -5
+
+
+def test_jk_workspace_for_routed_covers_both_paths():
+    # a routed J/K call may send every quartet to either path, and needs the predictions'
+    # room besides
+    b = _pairs_basis()
+    q = [[0, 1, 2, 3], [4, 4, 0, 2], [1, 1, 3, 3]]
+    sizes = {p: lx.JKBatch(b, q, True, path=p).workspace_size() for p in ("fp64", "split", "routed")}
+    mins = {p: lx.JKBatch(b, q, True, path=p).workspace_min() for p in ("fp64", "split", "routed")}
+    assert sizes["routed"] >= max(sizes["fp64"], sizes["split"])
+    assert mins["routed"] >= max(mins["fp64"], mins["split"])
+    assert sizes["split"] > sizes["fp64"]  # the split path keeps each block for the digestion
