@@ -151,3 +151,21 @@ def test_routed_jk_within_the_split_bound():
     per_int = np.abs(ints.cpu().numpy() - ref).max() + 1e-14 * np.abs(ref).max()
     assert np.all(np.abs(J.cpu().numpy() - Jr) <= per_int * WJ)
     assert np.all(np.abs(K.cpu().numpy() - Kr) <= per_int * WK)
+
+
+@pytest.mark.parametrize("path", ["fp64", "split"])
+def test_jk_largest_blocks(path):
+    # (kk|kk) Cartesian: 36^4 blocks; on the FP64 path the direct kernel stages one column of
+    # X and H_cd at a time (its widest chunk that leaves room for two CTAs per SM)
+    basis = jk_basis(ls=(7, 7, 7, 7), seed=51)
+    q = np.array([[0, 1, 2, 3], [2, 3, 0, 1]], np.int32)
+    _, nbf = oracle.function_offsets(basis, False)
+    D = density(nbf, 52)
+    Jr, Kr = oracle.jk(basis, q, D, False)
+    J, K = lx.eri_jk(basis, q, D, solid=False, path=path)
+    WJ, WK = weights(basis, q, D, False)
+    ref, _ = oracle.eri(basis, q, solid=False)
+    ints, _ = lx.eri(basis, q, solid=False, path=path)
+    per_int = np.abs(ints.cpu().numpy() - ref).max() + 1e-14 * np.abs(ref).max()
+    assert np.all(np.abs(J.cpu().numpy() - Jr) <= per_int * WJ)
+    assert np.all(np.abs(K.cpu().numpy() - Kr) <= per_int * WK)
