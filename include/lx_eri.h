@@ -276,6 +276,16 @@ int lx_eri_sync_status(void* cuda_stream);
  */
 int lx_eri_stage_times(double* ms, int64_t* launches, int32_t nstage, void* cuda_stream);
 
+/*
+ * Failure-detection self-test: enqueue on cuda_stream one wait of `tries` attempts
+ * (tries <= 2^24, the limit of the library's own waits) on a barrier that nothing
+ * arrives on -- the path every bounded wait of the library takes when its partner never
+ * comes.  The kernel sets the device status word's timeout bit and returns; the next
+ * lx_eri_sync_status reports LX_ERR_DEVICE_STATUS (and clears the word), and the device
+ * stays usable.  Returns LX_OK once enqueued.
+ */
+int lx_selftest_timeout(uint64_t tries, void* cuda_stream);
+
 /* Human-readable text of an error code (static storage). */
 const char* lx_strerror(int code);
 

@@ -16,6 +16,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lx_internal.cuh"
 #include "lx_split.cuh"
 
@@ -701,6 +703,12 @@ struct JkArgs {
     int64_t nbf;
 };
 
+// NVTX range over a scope (host side: marks when the work is enqueued; no-op without a tool)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 // Enqueue a planned batch on stream st: the head upload, normalisation, then per chunk the
 // descriptor upload and the kernels of the chosen path.  head_src / blob_src are the host
 // bytes to upload (pageable, or pinned for graph capture).
@@ -708,6 +716,8 @@ int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector
                   void* workspace, unsigned* status, cudaStream_t st, bool time_stages, const JkArgs* jk) {
     const bool split = B.flags & LX_PATH_SPLIT, solid = B.flags & LX_SOLID;
     if ((B.flags & JK_DIGEST) && !jk) return LX_ERR_NULL;
+    const NvtxRange range(split ? (jk ? "lx_eri split path, J/K" : "lx_eri split path")
+                                : (jk ? "lx_eri FP64 path, J/K" : "lx_eri FP64 path"));
     if (jk) out = static_cast<double*>(workspace);  // blocks at workspace offsets, digested below
     const int nshell = B.nshell;
     char* wsb = static_cast<char*>(workspace);
@@ -723,6 +733,7 @@ int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector
     if ((e = launch_norm(d_sh, nshell, d_exps, d_coefs, d_ncoef, status, st)) != cudaSuccess) return cuda_fail(e);
     if ((e = tm.end(LX_STAGE_NORM, 1)) != cudaSuccess) return cuda_fail(e);
     for (size_t c = 0; c < B.chunks.size(); ++c) {
+        const NvtxRange chunk_range("lx_eri chunk");
         const ChunkPlan& P = B.chunks[c];
         char* base = wsb + B.head;
         e = cudaMemcpyAsync(base, blob_src[c], P.off_data, cudaMemcpyHostToDevice, st);
@@ -1507,6 +1518,15 @@ int lx_eri_jk(const lx_shell* shells, int32_t nshell, const double* exps, const 
     const JkArgs jk{D, J, K, nbf};
     return eri_entry(shells, nshell, exps, coefs, nprim_total, quartets, nquartet, flags | JK_DIGEST, nullptr,
                      workspace, workspace_bytes, cuda_stream, &jk);
+}
+
+int lx_selftest_timeout(uint64_t tries, void* cuda_stream) {
+    if (tries > (1ull << 24)) return LX_ERR_SIZE;
+    unsigned* status = nullptr;
+    const int v = ensure_device(&status);
+    if (v != LX_OK) return v;
+    const cudaError_t e = launch_wait_selftest(status, tries, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? LX_OK : cuda_fail(e);
 }
 
 const char* lx_strerror(int code) {

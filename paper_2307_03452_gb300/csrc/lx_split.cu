@@ -61,12 +61,24 @@ __device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
     return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase; false (and the status bit) when the limit is reached.
-__device__ inline bool mbar_wait(uint64_t* bar, uint32_t phase, unsigned* status) {
-    for (unsigned long long i = 0; i < WAIT_LIMIT; ++i)
+// Bounded wait on an mbarrier phase; false (and the status bit) when `limit` tries are spent.
+__device__ inline bool mbar_wait(uint64_t* bar, uint32_t phase, unsigned* status,
+                                 unsigned long long limit = WAIT_LIMIT) {
+    for (unsigned long long i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, phase)) return true;
     set_status(status, ST_TIMEOUT);
     return false;
+}
+
+// The timeout path of the bounded waits, on purpose: one thread waits, with `limit` tries,
+// on an mbarrier that nothing arrives on (no copy is in flight, no TMEM is held), sets the
+// status bit and returns.
+__global__ void wait_selftest_kernel(unsigned* status, unsigned long long limit) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_wait(&bar, 0, status, limit);
 }
 
 // Bulk (non-tensor) TMA copy global -> shared; completes `bytes` of transaction on `bar`.
@@ -720,6 +732,12 @@ cudaError_t init_split_kernels(const int* host_tuv) {
     const uint16_t* p = static_cast<const uint16_t*>(dev_table);
     if ((e = cudaMemcpyToSymbol(g_gidx, &p, sizeof(p))) != cudaSuccess) return e;
     return cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+}
+
+cudaError_t launch_wait_selftest(unsigned* status, unsigned long long limit, cudaStream_t st) {
+    if (limit > WAIT_LIMIT) return cudaErrorInvalidValue;
+    wait_selftest_kernel<<<1, 32, 0, st>>>(status, limit);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_split_gemm(const SplitGemmDesc* probs, const WorkItem* items, int nitems, const char* ws,

@@ -100,6 +100,9 @@ cudaError_t launch_split_operands(const DQuartet* qd, const SplitQuartet* sq, co
 // item = (desc, chunk of 128 columns)
 cudaError_t launch_colmax(const ColMaxDesc* descs, const WorkItem* items, int nitems, const double* src_base,
                           char* ws, cudaStream_t st);
+// The bounded-wait timeout path on purpose (a wait of `limit` tries, <= the kernels' own
+// limit, on an mbarrier nothing arrives on): sets the status word's timeout bit.
+cudaError_t launch_wait_selftest(unsigned* status, unsigned long long limit, cudaStream_t st);
 cudaError_t launch_split_gemm(const SplitGemmDesc* probs, const WorkItem* items, int nitems, const char* ws,
                               double* cbase, unsigned* status, cudaStream_t st);
 

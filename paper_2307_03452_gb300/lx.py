@@ -37,7 +37,7 @@ EXPORTS = sorted(["lx_eri_out_size", "lx_eri_workspace_size", "lx_eri_workspace_
                   "lx_eri_graph_destroy", "lx_eri_autotune", "lx_tune_export", "lx_tune_import", "lx_tune_clear",
                   "lx_router_set", "lx_eri_pairs_out_size", "lx_eri_pairs_workspace_size",
                   "lx_eri_pairs_workspace_min", "lx_eri_pairs", "lx_nbf", "lx_eri_jk_workspace_size",
-                  "lx_eri_jk_workspace_min", "lx_eri_jk"])
+                  "lx_eri_jk_workspace_min", "lx_eri_jk", "lx_selftest_timeout"])
 TILE_SHAPES = ["32x64", "64x32", "32x32", "64x64"]
 MLP_NIN = 20
 MLP_WIDTH = 64
@@ -90,6 +90,8 @@ def load(build_if_missing: bool = True):
         lib.lx_eri_pairs.argtypes = [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_i64, c_vp, c_i64, c_i32, c_vp, c_vp, c_sz,
                                      c_vp]
         lib.lx_eri_pairs.restype = ctypes.c_int
+        lib.lx_selftest_timeout.argtypes = [ctypes.c_uint64, c_vp]
+        lib.lx_selftest_timeout.restype = ctypes.c_int
         lib.lx_nbf.argtypes = [c_vp, c_i32, c_i32]
         lib.lx_nbf.restype = c_i64
         for name in ("lx_eri_jk_workspace_size", "lx_eri_jk_workspace_min"):
@@ -377,6 +379,12 @@ def eri_jk(basis: dict, quartets, D, solid: bool = True, want: str = "JK", devic
     b.run_jk(Dt, J, K, alloc_workspace(need, device), stream)
     sync_status(stream)
     return J, K
+
+
+def selftest_timeout(tries: int = 1000, stream=None):
+    """Enqueue the library's bounded-wait timeout path on purpose (lx_selftest_timeout); the
+    next sync_status raises LxError(LX_ERR_DEVICE_STATUS)."""
+    _check(load().lx_selftest_timeout(int(tries), ctypes.c_void_p(_stream_ptr(stream))), "lx_selftest_timeout")
 
 
 def stage_times(stream=None) -> tuple[dict, dict]:

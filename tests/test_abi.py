@@ -265,3 +265,8 @@ def test_jk_workspace_for_routed_covers_both_paths():
     assert sizes["routed"] >= max(sizes["fp64"], sizes["split"])
     assert mins["routed"] >= max(mins["fp64"], mins["split"])
     assert sizes["split"] > sizes["fp64"]  # the split path keeps each block for the digestion
+
+
+def test_selftest_timeout_bounds_its_tries():
+    # more tries than the library's own wait limit is refused on the host
+    assert lx.load().lx_selftest_timeout((1 << 24) + 1, None) == -10
