@@ -66,10 +66,10 @@ def run_and_check(basis, quartets, solid, **kw):
 
 # ---------------------------------------------------------------- stage: Boys
 
-def test_boys_stage_matches_oracle():
+@pytest.mark.parametrize("mmax", [24, 28])  # L of (ii|ii) and of (kk|kk)
+def test_boys_stage_matches_oracle(mmax):
     T = np.concatenate([[0.0, 1e-14, 1e-9], np.logspace(-6, 4.7, 400), np.arange(0, 36.05, 0.1),
                         np.arange(0.05, 36, 0.1), np.linspace(35.9, 36.1, 41), [36.0, 80.0, 80.5, 1e5]])
-    mmax = 24
     F = lx.boys(mmax, torch.tensor(T, dtype=torch.float64, device="cuda")).cpu().numpy()
     ref = np.stack([oracle.boys(mmax, t) for t in T])
     rel = np.abs(F - ref) / np.abs(ref)
