@@ -213,6 +213,10 @@ int lx_eri_jk(const lx_shell* shells, int32_t nshell, const double* exps, const 
  *   makes that first call where allocation is still allowed.  The first call on a device
  *   also looks up the array's device address (cudaGetSymbolAddress, with that device
  *   current); make that first call before any stream capture.
+ *   A stream in capture mode is refused (LX_ERR_CUDA): the call uploads its descriptors from
+ *   host memory that it releases on return.  LX_PATH_ROUTED and LX_TIME_STAGES are refused
+ *   (LX_ERR_FLAGS): routing needs scratch beyond the array, and stage timing creates CUDA
+ *   events.
  *   A batch whose smallest workspace (lx_eri_workspace_min) exceeds LX_STATIC_SCRATCH_BYTES
  *   is rejected with LX_ERR_STATIC_SCRATCH; larger batches that fit one quartet at a time are
  *   processed in chunks.

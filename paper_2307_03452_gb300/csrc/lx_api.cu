@@ -920,6 +920,20 @@ namespace lx {
 
 const FoldHost* fold_tables() { return g_fold_ready ? &g_fold : nullptr; }
 
+int report_cuda_error(cudaError_t e) { return cuda_fail(e); }
+
+int entry_prepare(void* cuda_stream, const char* who, unsigned** status) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(static_cast<cudaStream_t>(cuda_stream), &cap);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (cap != cudaStreamCaptureStatusNone) {
+        std::snprintf(t_cuda_msg, sizeof(t_cuda_msg), "%s on a capturing stream: its uploads read host memory "
+                      "released when the call returns", who);
+        return LX_ERR_CUDA;
+    }
+    return ensure_device(status);
+}
+
 // lx_eri_batch without the pinned staging: the descriptors are uploaded straight from the
 // planner's host vectors (the copies then wait for the stream).  Allocates nothing.
 int eri_batch_unstaged(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,

@@ -163,6 +163,12 @@ int eri_batch_unstaged(const lx_shell* shells, int32_t nshell, const double* exp
                        int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags, double* out,
                        void* workspace, size_t workspace_bytes, void* cuda_stream);
 
+// Entry-point preamble (lx_api.cu): refuses a capturing stream (LX_ERR_CUDA, with `who` in
+// lx_last_cuda_error), then sets up the current device (architecture check, tables).
+int entry_prepare(void* cuda_stream, const char* who, unsigned** status);
+// LX_ERR_CUDA, with the error's text kept for lx_last_cuda_error.
+int report_cuda_error(cudaError_t e);
+
 // Host-side table generators (lx_tables.cpp).
 void make_boys_table(double* table);        // BOYS_NROW * BOYS_NPT
 void make_solid_coefs(double* coefs);       // packed: l = 0..LMAX, (2l+1) x ncart(l) each

@@ -28,20 +28,28 @@ void* g_scratch_ptr[MAX_DEVICES];
 extern "C" int lx_eri_batch_static(const lx_shell* shells, int32_t nshell, const double* exps, const double* coefs,
                                    int32_t nprim_total, const lx_quartet* quartets, int64_t nquartet, int32_t flags,
                                    double* out, void* cuda_stream) {
-    if (flags & LX_PATH_ROUTED) return LX_ERR_FLAGS;  // routing needs scratch this entry does not have
+    // Routing needs scratch this entry does not have; stage timing would create CUDA events.
+    if (flags & (LX_PATH_ROUTED | LX_TIME_STAGES)) return LX_ERR_FLAGS;
     // The smallest workspace this batch can run in (it is processed in chunks that fit).
     const int64_t need = lx_eri_workspace_min(shells, nshell, quartets, nquartet, flags);
     if (need < 0) return (int)need;
     if (need > (int64_t)LX_STATIC_SCRATCH_BYTES) return LX_ERR_STATIC_SCRATCH;
+    // A capturing stream is refused (the descriptor uploads below read host vectors that are
+    // released when the call returns); then the device is set up and its architecture checked.
+    unsigned* status = nullptr;
+    int v = lx::entry_prepare(cuda_stream, "lx_eri_batch_static", &status);
+    if (v != LX_OK) return v;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return LX_ERR_CUDA;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return lx::report_cuda_error(e);
     if (dev < 0 || dev >= MAX_DEVICES) return LX_ERR_ARCH;
     void* ptr = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mutex);
         if (!g_scratch_ptr[dev]) {
             void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, lx_static_scratch) != cudaSuccess || !p) return LX_ERR_CUDA;
+            if ((e = cudaGetSymbolAddress(&p, lx_static_scratch)) != cudaSuccess) return lx::report_cuda_error(e);
+            if (!p) return LX_ERR_CUDA;
             g_scratch_ptr[dev] = p;
         }
         ptr = g_scratch_ptr[dev];

@@ -400,12 +400,14 @@ def stage_times(stream=None) -> tuple[dict, dict]:
 STATIC_SCRATCH_BYTES = 64 << 20
 
 
-def run_static(batch: "Batch", out, stream=None):
+def run_static(batch: "Batch", out, stream=None, time_stages: bool = False):
     """lx_eri_batch_static: the same evaluation with the library's fixed device scratch
-    array instead of a caller workspace (for callers that cannot allocate device memory)."""
+    array instead of a caller workspace (for callers that cannot allocate device memory).
+    time_stages passes LX_TIME_STAGES, which this entry refuses."""
     b = batch
+    flags = b.flags | (LX_TIME_STAGES if time_stages else 0)
     rc = load().lx_eri_batch_static(_ptr(b.shells), len(b.shells), _ptr(b.exps), _ptr(b.coefs), len(b.exps),
-                                    _ptr(b.quartets), len(b.quartets), b.flags, ctypes.c_void_p(out.data_ptr()),
+                                    _ptr(b.quartets), len(b.quartets), flags, ctypes.c_void_p(out.data_ptr()),
                                     ctypes.c_void_p(_stream_ptr(stream)))
     _check(rc, "lx_eri_batch_static")
 

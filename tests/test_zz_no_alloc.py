@@ -54,3 +54,38 @@ def test_static_scratch_rejects_oversized_batch():
     with pytest.raises(lx.LxError) as e:
         lx.run_static(b, out)
     assert e.value.code == -11
+
+
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")
+def test_static_scratch_refuses_capture_and_stage_timing():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    torch.cuda.set_device(0)
+    basis, quartets = inputs.uniform_class((2, 1, 2, 0), 3, 132, cube=3.0, exps=(0.2, 5.0))
+    b = lx.Batch(basis, quartets, solid=True)
+    out = torch.empty(b.out_size, dtype=torch.float64, device="cuda")
+    lx.run_static(b, out)  # device set-up and the symbol lookup happen outside any capture
+    lx.sync_status()
+    ref = out.clone()
+    # the descriptors are uploaded from host memory released on return: a capturing stream
+    # is refused before anything is enqueued, and the capture ends cleanly (empty graph)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    code = None
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        try:
+            lx.run_static(b, out, stream=s)
+        except lx.LxError as exc:
+            code = exc.code
+        finally:
+            g.capture_end()
+    torch.cuda.synchronize()
+    assert code == -7
+    # stage timing would create CUDA events: refused with LX_ERR_FLAGS
+    with pytest.raises(lx.LxError) as e:
+        lx.run_static(b, out, time_stages=True)
+    assert e.value.code == -5
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)  # neither refused call wrote anything
