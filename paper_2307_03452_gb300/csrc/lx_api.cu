@@ -216,7 +216,7 @@ size_t quartet_bytes(const lx_shell* sh, const lx_quartet& q, int flags) {
         items += ((nab + 31) / 32) * ((n1 + 31) / 32);
         items += ((nab + 31) / 32) * ((ncd + 31) / 32);
     } else {
-        // [p|q]^T and X digit planes; H's go with the pair (pair_bytes)
+        // [p|q]^T and X digit planes with their segment exponents; H's go with the pair (pair_bytes)
         const int k1 = (int)(kbra * np), k2 = (int)n1;
         const int ra1 = split_rowpad(k2, SPLIT_TA), ra2 = split_rowpad((int)nab, SPLIT_TA);
         items += (ra1 + ra2) / 8;
@@ -224,7 +224,7 @@ size_t quartet_bytes(const lx_shell* sh, const lx_quartet& q, int flags) {
         items += (ra2 / SPLIT_TA) * ((ncd + SPLIT_TB - 1) / SPLIT_TB);
         bytes += sizeof(SplitQuartet) + 2 * sizeof(SplitGemmDesc) + sizeof(SplitRowsDesc);
         bytes += (size_t)split_dig_bytes(k2, k1, SPLIT_TA) + (size_t)split_dig_bytes((int)nab, k2, SPLIT_TA);
-        bytes += 4 * (size_t)(ra1 + ra2) + 4 * 256;
+        bytes += 4 * ((size_t)ra1 + (size_t)ra2 * split_nseg(split_nkb(k2))) + 4 * 256;
     }
     return bytes + items * sizeof(WorkItem);
 }
@@ -476,11 +476,11 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             q.gidx_off = gidx_offset(sh[pb.sa].l + sh[pb.sb].l, sh[pk.sa].l + sh[pk.sb].l);
             P.sq.push_back(q);
             const int tb1 = split_tb(d.nab), tb2 = split_tb(d.ncd);
-            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k2, d.nab, k2, SPLIT_TA, q.nkb2, +1, 0, 0});  // A2: X
-            for (int row = 0; row < split_rowpad(k2, SPLIT_TA); row += 8) P.items_sr.push_back({i, row, 0, 0});
+            // A2: X, one exponent per row and segment (the rows up to nab rounded to 8 are used)
+            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k2, d.nab, k2, SPLIT_TA, q.nkb2, +1, 2, split_nseg(q.nkb2)});
+            for (int row = 0; row < split_rowpad(k2, 8); row += 8) P.items_sr.push_back({i, row, 0, 0});
             // X's digit planes only after GEMM1
-            for (int row = 0; row < split_rowpad(d.nab, SPLIT_TA); row += 8)
-                P.items_sD.push_back({npair + i, row, 0, 0});
+            for (int row = 0; row < split_rowpad(d.nab, 8); row += 8) P.items_sD.push_back({npair + i, row, 0, 0});
             const int mt1 = split_rowpad(k2, SPLIT_TA) / SPLIT_TA, nt1 = (d.nab + tb1 - 1) / tb1;
             const int mt2 = split_rowpad(d.nab, SPLIT_TA) / SPLIT_TA, nt2 = (d.ncd + tb2 - 1) / tb2;
             for (int m = 0; m < mt1; ++m)
@@ -516,7 +516,6 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     region(P.off_isr, sizeof(WorkItem) * P.items_sr.size());
     region(P.off_isB, sizeof(WorkItem) * P.items_sB.size());
     region(P.off_isg1, sizeof(WorkItem) * P.items_sg1.size());
-
     region(P.off_isD, sizeof(WorkItem) * P.items_sD.size());
     region(P.off_isg2, sizeof(WorkItem) * P.items_sg2.size());
     P.off_data = o;
@@ -559,7 +558,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             q.b1_dig = hb.dig_off;
             q.b1_exp = hb.exp_off;
             q.a2_dig = take_bytes(split_dig_bytes(d.nab, k2, SPLIT_TA));
-            q.a2_exp = take_bytes(4 * (int64_t)split_rowpad(d.nab, SPLIT_TA));
+            q.a2_exp = take_bytes(4 * (int64_t)split_rowpad(d.nab, SPLIT_TA) * split_nseg(q.nkb2));
             q.b2_dig = hk.dig_off;
             q.b2_exp = hk.exp_off;
             q.c1_off = hb.shift_off;
@@ -581,6 +580,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             g1.ldc = k2;
             g1.transpose = 1;
             g1.tb = split_tb(d.nab);
+            g1.a_nseg = 1;
             P.sg1.push_back(g1);
             SplitGemmDesc g2{};
             g2.a_dig = q.a2_dig;
@@ -594,6 +594,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             g2.ldc = d.ncd;
             g2.transpose = 0;
             g2.tb = split_tb(d.ncd);
+            g2.a_nseg = split_nseg(q.nkb2);  // X: one exponent per row and segment
             P.sg2.push_back(g2);
         }
     }
@@ -617,7 +618,6 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     put(P.off_isr, P.items_sr.data(), sizeof(WorkItem) * P.items_sr.size());
     put(P.off_isB, P.items_sB.data(), sizeof(WorkItem) * P.items_sB.size());
     put(P.off_isg1, P.items_sg1.data(), sizeof(WorkItem) * P.items_sg1.size());
-
     put(P.off_isD, P.items_sD.data(), sizeof(WorkItem) * P.items_sD.size());
     put(P.off_isg2, P.items_sg2.data(), sizeof(WorkItem) * P.items_sg2.size());
 }
@@ -771,18 +771,18 @@ int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector
                 return cuda_fail(e);
             if ((e = tm.end(LX_STAGE_SPLIT, 2)) != cudaSuccess) return cuda_fail(e);
             if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
-            if ((e = launch_split_gemm(d_sg1, items(P.off_isg1), (int)P.items_sg1.size(), wsb, ws, status, st)) !=
-                cudaSuccess)
+            if ((e = launch_split_gemm(d_sg1, items(P.off_isg1), (int)P.items_sg1.size(), wsb, ws, status, st,
+                                       false)) != cudaSuccess)
                 return cuda_fail(e);
             if ((e = tm.end(LX_STAGE_GEMM1, 1)) != cudaSuccess) return cuda_fail(e);
-            // the other operand of GEMM2: digit planes of [ab|q]
+            // the other operand of GEMM2: digit planes of [ab|q], one exponent per row and segment
             if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
             if ((e = launch_split_rows(d_srd, items(P.off_isD), (int)P.items_sD.size(), ws, wsb, st)) != cudaSuccess)
                 return cuda_fail(e);
             if ((e = tm.end(LX_STAGE_SPLIT, 1)) != cudaSuccess) return cuda_fail(e);
             if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
-            if ((e = launch_split_gemm(d_sg2, items(P.off_isg2), (int)P.items_sg2.size(), wsb, out, status, st)) !=
-                cudaSuccess)
+            if ((e = launch_split_gemm(d_sg2, items(P.off_isg2), (int)P.items_sg2.size(), wsb, out, status, st,
+                                       true)) != cudaSuccess)
                 return cuda_fail(e);
             if ((e = tm.end(LX_STAGE_GEMM2, 1)) != cudaSuccess) return cuda_fail(e);
         } else {
@@ -1705,7 +1705,17 @@ int lx_split_gemm(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda,
     rd[0].exp_off = (int64_t)region(4 * (size_t)ra);
     rd[1].dig_off = (int64_t)region((size_t)split_dig_bytes(N, K, tb));
     rd[1].exp_off = (int64_t)region(4 * (size_t)rb);
-    SplitGemmDesc g{rd[0].dig_off, rd[0].exp_off, rd[1].dig_off, rd[1].exp_off, 0, M, N, nkb, ldc, 0, tb};
+    SplitGemmDesc g{};
+    g.a_dig = rd[0].dig_off;
+    g.a_exp = rd[0].exp_off;
+    g.b_dig = rd[1].dig_off;
+    g.b_exp = rd[1].exp_off;
+    g.M = M;
+    g.N = N;
+    g.nkb = nkb;
+    g.ldc = ldc;
+    g.tb = tb;
+    g.a_nseg = 1;
     std::vector<char> blob(blob_bytes, 0);
     std::memcpy(blob.data() + o_rd, rd.data(), sizeof(SplitRowsDesc) * 2);
     std::memcpy(blob.data() + o_g, &g, sizeof(g));
@@ -1726,7 +1736,7 @@ int lx_split_gemm(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda,
         return cuda_fail(e);
     if ((e = launch_split_gemm(reinterpret_cast<const SplitGemmDesc*>(scratch + o_g),
                                reinterpret_cast<const WorkItem*>(scratch + o_ig), (int)ig.size(), scratch, C, status,
-                               st)) != cudaSuccess)
+                               st, false)) != cudaSuccess)
         return cuda_fail(e);
     if ((e = cudaFreeAsync(scratch, st)) != cudaSuccess) return cuda_fail(e);
     return LX_OK;

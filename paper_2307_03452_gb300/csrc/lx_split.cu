@@ -145,6 +145,12 @@ __device__ inline void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr)
         : "memory");
 }
+__device__ inline void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+}
 __device__ inline void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // ------------------------------------------------------------------ splitting
@@ -250,17 +256,41 @@ __device__ inline int row_max16(int mx) {
 }
 
 // Split 8 rows (4 pairs) through value(row, k0, v[8], sh[8]) (values and the powers of two
-// they are scaled by; zeros outside the matrix): digit planes
-// of row tile T with nkb K blocks, one int exponent per row.  fixed: every value lies in
-// (-1, 1) and every row takes e = 0, so the exponent pass is skipped.
-template <typename Value>
-__device__ __forceinline__ void split_8rows(int r0, int nkb, int T, bool fixed, __nv_bfloat16* __restrict__ dig,
-                                            int* __restrict__ exps, Value value) {
+// they are scaled by; zeros outside the matrix): digit planes of row tile T with nkb K blocks
+// and one int exponent per row (the modes of SplitRowsDesc::fixed).
+template <bool SEGMENTS, typename Value>
+__device__ __forceinline__ void split_8rows(int r0, int nkb, int T, int fixed, int nseg,
+                                            __nv_bfloat16* __restrict__ dig, int* __restrict__ exps, Value value) {
     const int lane = threadIdx.x & 31, c8 = 8 * (lane & 15);
+    static_assert(SPLIT_SEG_KB * SPLIT_KB == 128, "one pass of a row pair covers one segment");
     for (int pr = 0; pr < 4; ++pr) {
         const int row = r0 + 2 * pr + (lane >> 4);
-        int mx = fixed ? 1022 : 0;  // 1022: the exponent field bound of values in (-1, 1)
-        if (!fixed) {
+        if (SEGMENTS && fixed == 2) {
+            // one exponent per segment of 128 columns: one pass of the row's 16 lanes covers a
+            // segment (every lane takes every pass, for the shuffles; columns past the K blocks
+            // read as zeros and are not stored)
+            for (int sg = 0; sg < nseg; ++sg) {
+                const int k0 = 128 * sg + c8;
+                double v[8];
+                int sh[8];
+                value(row, k0, v, sh);
+                int mx = 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) mx = max(mx, exp_field_scaled(v[i], sh[i]));
+                mx = row_max16(mx);
+                const int e = mx > 0 ? mx - 1022 : SPLIT_EXP_NONE;
+                if (k0 < nkb * SPLIT_KB) {
+                    long long q[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) q[i] = mx > 0 ? fixed_of(v[i], sh[i], e) : 0ll;
+                    store_digit_group(dig, row, k0, T, nkb, q);
+                }
+                if ((lane & 15) == 0) exps[(int64_t)row * nseg + sg] = e;
+            }
+            continue;
+        }
+        int mx = fixed == 1 ? 1022 : 0;  // 1022: the exponent field bound of values in (-1, 1)
+        if (fixed == 0) {
             for (int k0 = c8; k0 < nkb * SPLIT_KB; k0 += 128) {
                 double v[8];
                 int sh[8];
@@ -284,13 +314,15 @@ __device__ __forceinline__ void split_8rows(int r0, int nkb, int T, bool fixed, 
     }
 }
 
-// One split_rows item (item.q = descriptor, item.a = r0), by one warp.
+// One split_rows item (item.q = descriptor, item.a = r0), by one warp (SEGMENTS: fixed = 2 may
+// occur).
+template <bool SEGMENTS>
 __device__ __forceinline__ void split_rows_item(const SplitRowsDesc* __restrict__ descs, const WorkItem& it,
                                                 const double* __restrict__ src_base, char* __restrict__ ws) {
     const SplitRowsDesc d = descs[it.q];
     const double* src = src_base + d.src_off;
     const int* shift = d.shift_off >= 0 ? reinterpret_cast<const int*>(ws + d.shift_off) : nullptr;
-    split_8rows(it.a, d.nkb, d.T, d.fixed != 0, reinterpret_cast<__nv_bfloat16*>(ws + d.dig_off),
+    split_8rows<SEGMENTS>(it.a, d.nkb, d.T, d.fixed, d.nseg, reinterpret_cast<__nv_bfloat16*>(ws + d.dig_off),
                 reinterpret_cast<int*>(ws + d.exp_off), [&](int row, int k0, double (&v)[8], int (&sh)[8]) {
                     const bool live = row < d.rows;
                     const double* sr = src + (int64_t)row * d.ld;
@@ -309,7 +341,7 @@ __global__ void __launch_bounds__(256) split_rows_kernel(const SplitRowsDesc* __
                                                          const double* __restrict__ src_base, char* __restrict__ ws) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (warp >= nitems) return;
-    split_rows_item(descs, items[warp], src_base, ws);
+    split_rows_item<true>(descs, items[warp], src_base, ws);
 }
 
 // Rows q of the GEMM1 A operand: A[q][k] = [p+q]^(0) of primitive quartet (kp, kq) with
@@ -418,7 +450,7 @@ __global__ void __launch_bounds__(256) split_operands_kernel(const DQuartet* __r
     if (kind == 0) {
         if (w < n_r) split_r_item(qd, sq, items_r[w], wsd, ws);
     } else {
-        if (w < n_w) split_rows_item(descs, items_w[w], wsd, ws);
+        if (w < n_w) split_rows_item<false>(descs, items_w[w], wsd, ws);  // H rows: fixed = 1
     }
 }
 
@@ -451,11 +483,19 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
 // warp 0 TMA, warp 1 MMA issue + TMEM, warps 2..9 drain / epilogue: two warps per TMEM lane
 // quarter, each owning 16 of the tile's (at most 32) columns
 constexpr int DRAIN_WARPS = 8;
+constexpr int DCOLS = 16;  // columns per drain warp
 constexpr int GEMM_THREADS = 32 * (2 + DRAIN_WARPS);
-static_assert(SPLIT_TB == 16 * (DRAIN_WARPS / 4), "each drain warp owns 16 columns");
+static_assert(SPLIT_TB == DCOLS * (DRAIN_WARPS / 4), "the drain warps cover the widest column tile");
 
 __device__ inline void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// x / 2^s rounded to nearest (ties up), for s >= 0; 0 once the shift passes every bit.
+__device__ inline long long shr_round(long long x, int s) {
+    if (s <= 0) return x;
+    if (s >= 62) return 0;
+    return (x + (1ll << (s - 1))) >> s;
 }
 
 // Persistent: CTA b takes work items b, b + gridDim.x, ... (item.q = problem, item.a = M tile,
@@ -475,6 +515,7 @@ __device__ inline void mbar_arrive(uint64_t* bar) {
 // once: slice t lies tb rows after slice t-1 in shared memory and diagonal s + t lies tb TMEM
 // columns after s + t - 1, so A_s [B_0; B_1; ...] lands every product on its diagonal in one
 // MMA of N = (NSLICE - s) tb <= 192.
+template <bool SEGS>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     split_gemm_kernel(const SplitGemmDesc* __restrict__ probs, const WorkItem* __restrict__ items, int nitems,
                       const char* __restrict__ ws, double* __restrict__ cbase, unsigned* status) {
@@ -519,6 +560,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 const int b_block = SPLIT_NSLICE * P.tb * SPLIT_KB * 2;
                 const char* a_src = ws + P.a_dig + (int64_t)it.a * P.nkb * A_BLOCK;
                 const char* b_src = ws + P.b_dig + (int64_t)it.b * P.nkb * b_block;
+                // rows of this A tile that exist (up to M rounded up to 8): a partial last tile
+                // is copied slice by slice, its first vr rows only; the rows past them hold
+                // whatever the stage held before and only reach output rows >= M, which the
+                // drain discards
+                const int vr = min(SPLIT_TA, ((P.M + 7) & ~7) - it.a * SPLIT_TA);
+                const int a_bytes = vr == SPLIT_TA ? A_BLOCK : SPLIT_NSLICE * vr * SPLIT_KB * 2;
                 for (int kb = 0; kb < P.nkb; ++kb, ++g) {
                     const int st = g % STAGES, use = g / STAGES;
                     if ((use > 0 && !mbar_wait(&empty_bar[st], (use - 1) & 1, status)) || *(volatile int*)&abort_sh) {
@@ -527,8 +574,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                         break;
                     }
                     unsigned char* sa = smem + st * STAGE_BYTES;
-                    mbar_expect_tx(&full_bar[st], A_BLOCK + b_block);
-                    bulk_g2s(sa, a_src + (int64_t)kb * A_BLOCK, A_BLOCK, &full_bar[st]);
+                    mbar_expect_tx(&full_bar[st], a_bytes + b_block);
+                    if (vr == SPLIT_TA) {
+                        bulk_g2s(sa, a_src + (int64_t)kb * A_BLOCK, A_BLOCK, &full_bar[st]);
+                    } else {
+                        for (int sl = 0; sl < SPLIT_NSLICE; ++sl)
+                            bulk_g2s(sa + sl * A_SLICE, a_src + (int64_t)kb * A_BLOCK + sl * A_SLICE,
+                                     vr * SPLIT_KB * 2, &full_bar[st]);
+                    }
                     bulk_g2s(sa + A_BLOCK, b_src + (int64_t)kb * b_block, b_block, &full_bar[st]);
                 }
             }
@@ -599,8 +652,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         }
     } else {
         // drain / epilogue: warp w reads TMEM lanes (rows) 32 (w % 4) .. 32 (w % 4) + 31 and the
-        // 16 columns c0 .. c0 + 15 of each diagonal
-        const int quarter = warp & 3, c0 = 16 * ((warp - 2) >> 2);
+        // DCOLS columns c0 .. c0 + DCOLS - 1 of each diagonal
+        const int quarter = warp & 3, c0 = DCOLS * ((warp - 2) >> 2);
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + c0;
         int sgc = 0;
         bool ok = true;
@@ -612,34 +665,68 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             const int nt = min(tb, P.N - n0);
             const bool mine = c0 < nt;  // warp-uniform
             const int xs = max(0, 32 - __clz(nkb * SPLIT_KB - 1) - 14);  // ceil(log2 K) - 14, if positive
-            long long acc[16];
+            const int row = m0 + quarter * 32 + lane;
+            const bool rlive = row < P.M;  // rows past M may come from stale shared memory: dropped
+            // SEGS (A exponents per segment): acc 2^E is the row's sum so far, E the largest
+            // exponent of its segments so far; each segment's exponent is read one segment ahead.
+            // Otherwise one exponent per row, read at the end.
+            constexpr bool segs = SEGS;
+            const int* a_exp = reinterpret_cast<const int*>(ws + P.a_exp) + (int64_t)row * P.a_nseg;
+            int E = SPLIT_EXP_NONE, es_next = segs && rlive ? a_exp[0] : SPLIT_EXP_NONE;
+            long long acc[DCOLS];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[j] = 0;
-            for (int kb0 = 0; kb0 < nkb; kb0 += SPLIT_SEG_KB, ++sgc) {
+            for (int j = 0; j < DCOLS; ++j) acc[j] = 0;
+            for (int kb0 = 0, sg = 0; kb0 < nkb; kb0 += SPLIT_SEG_KB, ++sg, ++sgc) {
                 const int buf = sgc & 1;
+                int sa = 0, sv = 0;  // right shifts of the running sum and of this segment
+                if (segs) {
+                    const int es = es_next;
+                    if (kb0 + SPLIT_SEG_KB < nkb) es_next = rlive ? a_exp[sg + 1] : SPLIT_EXP_NONE;
+                    if (es > E) {
+                        sa = E == SPLIT_EXP_NONE ? 62 : es - E;
+                        E = es;
+                    } else {
+                        sv = E - es;  // a zero segment (es = SPLIT_EXP_NONE) contributes nothing
+                    }
+                }
                 const bool got = mbar_wait(&seg_full[buf], (sgc >> 1) & 1, status);
                 ok = __all_sync(0xffffffffu, got) && !*(volatile int*)&abort_sh;
                 if (!ok) break;
                 tc_fence_after();
                 if (mine) {
-                    // all six diagonals in flight before one wait
-                    uint32_t r[SPLIT_NSLICE][16];
+                    // all six diagonals of HC columns in flight before one wait (the aligned sum
+                    // takes its 16 columns in two halves, to stay within the registers)
+                    constexpr int HC = SEGS ? 8 : DCOLS;
 #pragma unroll
-                    for (int dg = 0; dg < SPLIT_NSLICE; ++dg) tmem_ld16(lane_base + buf * BUF_COLS + dg * tb, r[dg]);
-                    tmem_ld_wait();
-                    // acc += sum_d G_d 2^(BETA (NSLICE-2-d)) (>> xs); the last diagonal is rounded down BETA bits
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        long long v = 0;
+                    for (int h = 0; h < DCOLS / HC; ++h) {
+                        uint32_t r[SPLIT_NSLICE][HC];
 #pragma unroll
                         for (int dg = 0; dg < SPLIT_NSLICE; ++dg) {
-                            const long long gv = (long long)__float2int_rn(__uint_as_float(r[dg][j]));
-                            if (dg < SPLIT_NSLICE - 1)
-                                v += gv << (SPLIT_BETA * (SPLIT_NSLICE - 2 - dg));
+                            if constexpr (HC == 16)
+                                tmem_ld16(lane_base + buf * BUF_COLS + dg * tb, r[dg]);
                             else
-                                v += (gv + (1ll << (SPLIT_BETA - 1))) >> SPLIT_BETA;
+                                tmem_ld8(lane_base + buf * BUF_COLS + dg * tb + HC * h, r[dg]);
                         }
-                        acc[j] += xs ? (v + (1ll << (xs - 1))) >> xs : v;
+                        tmem_ld_wait();
+                        // v = sum_d G_d 2^(BETA (NSLICE-2-d)) (>> xs); the last diagonal is rounded down BETA bits
+#pragma unroll
+                        for (int jj = 0; jj < HC; ++jj) {
+                            long long v = 0;
+#pragma unroll
+                            for (int dg = 0; dg < SPLIT_NSLICE; ++dg) {
+                                const long long gv = (long long)__float2int_rn(__uint_as_float(r[dg][jj]));
+                                if (dg < SPLIT_NSLICE - 1)
+                                    v += gv << (SPLIT_BETA * (SPLIT_NSLICE - 2 - dg));
+                                else
+                                    v += (gv + (1ll << (SPLIT_BETA - 1))) >> SPLIT_BETA;
+                            }
+                            if (xs) v = (v + (1ll << (xs - 1))) >> xs;
+                            const int j = HC * h + jj;
+                            if (segs)
+                                acc[j] = shr_round(acc[j], sa) + shr_round(v, sv);
+                            else
+                                acc[j] += v;
+                        }
                     }
                 }
                 tc_fence_before();
@@ -647,17 +734,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 if (lane == 0) mbar_arrive(&seg_empty[buf]);
             }
             if (!ok) break;
-            const int row = m0 + quarter * 32 + lane;
-            if (mine && row < P.M) {
-                const int ea = reinterpret_cast<const int*>(ws + P.a_exp)[row];
+            if (mine && rlive) {
+                const int ea = segs ? E : reinterpret_cast<const int*>(ws + P.a_exp)[row];
                 const int* eb_tab = reinterpret_cast<const int*>(ws + P.b_exp);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
+                for (int j = 0; j < DCOLS; ++j) {
                     const int col = n0 + c0 + j;
                     if (c0 + j < nt) {
-                        // D = 2^(eA + eB - 2W + BETA NSLICE + xs) * acc: one rounding (int64 -> FP64,
-                        // to nearest even), then an exact power-of-two scaling
-                        const int scale = ea + eb_tab[col] - 2 * SPLIT_W + SPLIT_BETA * SPLIT_NSLICE + xs;
+                        // D = 2^(eA + eB - BETA NSLICE + xs) * acc: one rounding (int64 -> FP64, to
+                        // nearest even), then an exact power-of-two scaling (acc = 0 gives 0)
+                        const int scale = ea + eb_tab[col] - SPLIT_BETA * SPLIT_NSLICE + xs;
                         const double v = scale2(__ll2double_rn(acc[j]), scale);
                         if (P.transpose)
                             cbase[P.c_off + (int64_t)col * P.ldc + row] = v;
@@ -731,7 +817,10 @@ cudaError_t init_split_kernels(const int* host_tuv) {
         return e;
     const uint16_t* p = static_cast<const uint16_t*>(dev_table);
     if ((e = cudaMemcpyToSymbol(g_gidx, &p, sizeof(p))) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(split_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if ((e = cudaFuncSetAttribute(split_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  SMEM_BYTES)) != cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(split_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
 }
 
 cudaError_t launch_wait_selftest(unsigned* status, unsigned long long limit, cudaStream_t st) {
@@ -741,7 +830,7 @@ cudaError_t launch_wait_selftest(unsigned* status, unsigned long long limit, cud
 }
 
 cudaError_t launch_split_gemm(const SplitGemmDesc* probs, const WorkItem* items, int nitems, const char* ws,
-                              double* cbase, unsigned* status, cudaStream_t st) {
+                              double* cbase, unsigned* status, cudaStream_t st, bool segments) {
     if (nitems <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -749,7 +838,10 @@ cudaError_t launch_split_gemm(const SplitGemmDesc* probs, const WorkItem* items,
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     // one CTA per SM (the TMEM allocation and the operand ring take the whole SM)
     const int grid = nitems < sms ? nitems : sms;
-    split_gemm_kernel<<<grid, GEMM_THREADS, SMEM_BYTES, st>>>(probs, items, nitems, ws, cbase, status);
+    if (segments)
+        split_gemm_kernel<true><<<grid, GEMM_THREADS, SMEM_BYTES, st>>>(probs, items, nitems, ws, cbase, status);
+    else
+        split_gemm_kernel<false><<<grid, GEMM_THREADS, SMEM_BYTES, st>>>(probs, items, nitems, ws, cbase, status);
     return cudaGetLastError();
 }
 

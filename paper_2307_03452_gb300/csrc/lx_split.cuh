@@ -18,15 +18,24 @@ constexpr int SPLIT_SEG_KB = 4;                      // K blocks accumulated in 
 
 // One matrix whose rows are split: src at (double*)base + src_off, row stride ld.  Before
 // splitting, column k is multiplied by 2^(shift_sign * shift[k]) (exact; shift_off < 0: none).
-// fixed = 0: each row gets its own power of two (|x| < 2^e over the row); fixed = 1: the
-// scaled values are known to lie in (-1, 1) and every row takes e = 0 (one pass, no maximum).
+// Exponent of an all-zero row segment (below any real exponent; its digits are zero).
+constexpr int SPLIT_EXP_NONE = -(1 << 29);
+
+// One matrix whose rows are split: src at (double*)base + src_off, row stride ld.  Before
+// splitting, column k is multiplied by 2^(shift_sign * shift[k]) (exact; shift_off < 0: none).
+// fixed = 0: each row gets its own power of two (|x| < 2^e over the row: an exponent pass, then
+// a digit pass); fixed = 1: the scaled values are known to lie in (-1, 1) and every row takes
+// e = 0 (one pass, no maximum); fixed = 2: each row and segment of SPLIT_SEG_KB K blocks (128
+// columns) gets its own power of two, int[row][nseg] (SPLIT_EXP_NONE for a zero segment), so
+// every value is read once.
 struct SplitRowsDesc {
     int64_t src_off;    // doubles
     int64_t dig_off;    // bytes from the workspace base
-    int64_t exp_off;    // bytes from the workspace base (int per padded row)
+    int64_t exp_off;    // bytes from the workspace base (int per padded row, times nseg if fixed = 2)
     int64_t shift_off;  // bytes from the workspace base (int per column), or -1
-    int ld, rows, K, T, nkb, shift_sign, fixed, pad;
+    int ld, rows, K, T, nkb, shift_sign, fixed, nseg;
 };
+__host__ __device__ inline int split_nseg(int nkb) { return (nkb + SPLIT_SEG_KB - 1) / SPLIT_SEG_KB; }
 
 // out[k] = c_k with |x| < 2^c_k over column k of a row-major matrix (0 for a zero column):
 // the column scale of an H matrix.
@@ -38,7 +47,7 @@ struct ColMaxDesc {
 
 // Per-quartet split operands of the two GEMMs.  Column k of H_bra is scaled by 2^-c1[k] into
 // (-1, 1) and column k of [p|q]^T by 2^c1[k] (the product is unchanged); likewise H_ket and
-// [ab|q] with c2.
+// [ab|q] with c2.  Every operand carries one exponent per row.
 struct SplitQuartet {
     int64_t a1_dig, a1_exp;  // [p|q]^T rows (Kket Nq), K = Kbra Np, columns scaled by 2^c1
     int64_t b1_dig, b1_exp;  // H_bra rows (nab), columns scaled by 2^-c1
@@ -68,11 +77,14 @@ static_assert(NHERM_TOT < 65536, "[r]^(0) positions fit 16 bits");
 
 // D = A B^T: A digits (row tiles of SPLIT_TA), B digits (row tiles of tb = split_tb(N)), both
 // with nkb K blocks; D written to (double*)C + c_off with row stride ldc (transpose: D[m][n] ->
-// C[n][m]).
+// C[n][m]).  B carries one exponent per row; A one per row (a_nseg = 1) or one per row and
+// segment of SPLIT_SEG_KB K blocks (a_nseg = split_nseg(nkb), int[row][a_nseg]).  The A operand
+// is read only up to M rows rounded to 8 (the last row tile is loaded that far).
 struct SplitGemmDesc {
     int64_t a_dig, a_exp, b_dig, b_exp;
     int64_t c_off;
     int M, N, nkb, ldc, transpose, tb;
+    int a_nseg, pad;
 };
 
 // B row tile for an operand of N rows: as few tiles as SPLIT_TB rows allow, each a multiple
@@ -103,7 +115,9 @@ cudaError_t launch_colmax(const ColMaxDesc* descs, const WorkItem* items, int ni
 // The bounded-wait timeout path on purpose (a wait of `limit` tries, <= the kernels' own
 // limit, on an mbarrier nothing arrives on): sets the status word's timeout bit.
 cudaError_t launch_wait_selftest(unsigned* status, unsigned long long limit, cudaStream_t st);
+// segments: some A operands carry one exponent per segment (a_nseg may exceed 1); otherwise
+// every problem has a_nseg = 1
 cudaError_t launch_split_gemm(const SplitGemmDesc* probs, const WorkItem* items, int nitems, const char* ws,
-                              double* cbase, unsigned* status, cudaStream_t st);
+                              double* cbase, unsigned* status, cudaStream_t st, bool segments);
 
 }  // namespace lx
