@@ -64,16 +64,23 @@ typedef struct {
 #define LX_PATH_FP64 0x0   /* every step in FP64 */
 #define LX_PATH_SPLIT 0x2  /* the two Hermite transforms as Ozaki-style BF16 slice products on the
                               tensor cores (FP32 accumulation, integer recombination); Boys,
-                              [r]^(m), E and H stay FP64.  Operands carry 48 bits; the absolute
-                              error grows with the magnitude of a quartet's intermediates */
-#define LX_PATH_ROUTED 0x4 /* per quartet: the routing network set by lx_router_set predicts log10
-                              of the largest |integral|; quartets predicted at or above its
-                              threshold take LX_PATH_FP64, and so do quartets whose two
-                              transforms need fewer than LX_ROUTE_SPLIT_MIN_FLOP FLOPs (too
-                              small for the split path to be faster); the rest take
-                              LX_PATH_SPLIT.  lx_eri_batch then waits for the stream once, to
-                              read the predictions back.  Not with LX_PATH_SPLIT; not for
-                              lx_eri_graph_create, lx_eri_autotune or lx_eri_batch_static */
+                              [r]^(m), E and H stay FP64.  Operands carry 8 bits per digit kept
+                              (48 with the default 6 digits); the absolute error grows with the
+                              magnitude of a quartet's intermediates */
+#define LX_SPLIT_DIGITS(n) (((n) & 7) << 4) /* with LX_PATH_SPLIT: BF16 digits kept per operand
+                              value, n = 4, 5 or 6 (the default, also given by 0); the transforms
+                              keep the n(n+1)/2 digit products with s + t < n, and each digit
+                              fewer multiplies the error by about 2^8 */
+#define LX_SPLIT_DIGITS_MASK 0x70
+#define LX_PATH_ROUTED 0x4 /* per quartet: the routing network set by lx_router_set predicts
+                              log10 of the split path's error on the quartet (its output 1); the
+                              quartet takes the split path with the fewest digits (4, 5, 6) whose
+                              threshold lies above that prediction, else LX_PATH_FP64.  Quartets
+                              whose two transforms need fewer than LX_ROUTE_SPLIT_MIN_FLOP FLOPs
+                              (too small for the split path to be faster) take LX_PATH_FP64.
+                              lx_eri_batch then waits for the stream once, to read the predictions
+                              back.  Not with LX_PATH_SPLIT; not for lx_eri_graph_create,
+                              lx_eri_autotune or lx_eri_batch_static */
 #define LX_ROUTE_SPLIT_MIN_FLOP 1.0e6 /* 2 N_ab (K_bra N_p)(K_ket N_q) + 2 N_ab (K_ket N_q) N_cd */
 #define LX_TIME_STAGES 0x200 /* record CUDA events around each stage (see lx_eri_stage_times) */
 
@@ -334,23 +341,29 @@ int lx_hermite_H(const lx_shell* shells, int32_t nshell, const double* exps, con
  * C = A B^T through the split path's kernels (the same splitting and tensor-core GEMM that
  * LX_PATH_SPLIT uses for Eq. make-abq / Eq. make-abcd): A is M x K, B is N x K, both FP64
  * row-major in DEVICE memory with row strides lda, ldb; C is M x N FP64 row-major, stride ldc.
- * Each row of A and of B is scaled by its own power of two and split into 6 BF16 digits of
- * 8 bits; the 21 digit products with s + t <= 5 are summed.  Scratch for the digit
- * planes is taken from the stream-ordered allocator.  M, N, K >= 1, K <= 1 << 20.
+ * Each row of A and of B is scaled by its own power of two and split into BF16 digits of
+ * 8 bits, of which `digits` (4, 5 or 6) are kept; the digit products with s + t < digits
+ * are summed.  Scratch for the digit planes is taken from the stream-ordered allocator.
+ * M, N, K >= 1, K <= 1 << 20.
  */
 int lx_split_gemm(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda, const double* B, int32_t ldb,
-                  double* C, int32_t ldc, void* cuda_stream);
+                  double* C, int32_t ldc, int32_t digits, void* cuda_stream);
 
 /* ---------------------------------------------------------------- learned router
- * A small MLP predicts, per quartet, log10 of its largest |integral| from shell descriptors;
- * the caller routes quartets predicted large to LX_PATH_FP64 and the rest to LX_PATH_SPLIT,
- * whose absolute error grows with the integrals' magnitude.  The paper has no such part.
- * Network: LX_MLP_NIN inputs -> 64 -> 64 -> 1, ReLU, parameters packed as W1[64][20], b1[64],
- * W2[64][64], b2[64], W3[64], b3; the forward pass uses FP16 weights. */
+ * A small MLP predicts, per quartet from shell descriptors, log10 of its largest |integral|
+ * (output 0) and log10 of the split path's absolute error on it with 6 digits (output 1),
+ * which follows the magnitude of the quartet's intermediates rather than of its result when
+ * the Hermite sums cancel.  LX_PATH_ROUTED sends each quartet to the split path with as few
+ * digits as that prediction allows, or to LX_PATH_FP64.  The paper has no such part.
+ * Network: LX_MLP_NIN inputs -> 64 -> 64 -> LX_MLP_NOUT, ReLU, parameters packed as
+ * W1[64][20], b1[64], W2[64][64], b2[64], W3[2][64], b3[2]; the forward pass uses FP16
+ * weights. */
 #define LX_MLP_NIN 20
 #define LX_MLP_WIDTH 64
+#define LX_MLP_NOUT 2
 #define LX_MLP_NPARAM (LX_MLP_WIDTH * LX_MLP_NIN + LX_MLP_WIDTH + LX_MLP_WIDTH * LX_MLP_WIDTH + LX_MLP_WIDTH + \
-                       LX_MLP_WIDTH + 1)
+                       LX_MLP_NOUT * LX_MLP_WIDTH + LX_MLP_NOUT)
+#define LX_ROUTE_NTIER 3 /* split tiers of LX_PATH_ROUTED: 4, 5 and 6 digits */
 
 /*
  * Router features of each quartet: feat[q * LX_MLP_NIN + k] (DEVICE, float).  Descriptors are
@@ -365,19 +378,22 @@ int lx_route_features(const lx_shell* shells, int32_t nshell, const double* exps
 
 /*
  * The routing network of LX_PATH_ROUTED on the current device: params_f16 holds the
- * LX_MLP_NPARAM FP16 parameters (HOST memory, layout as above), tau the threshold on the
- * predicted log10 max |integral| at or above which a quartet takes the FP64 path.  The
- * parameters are copied (synchronously); a later call replaces them.
+ * LX_MLP_NPARAM FP16 parameters (HOST memory, layout as above); tau[LX_ROUTE_NTIER] (HOST)
+ * the thresholds on output 1 for the split tiers of 4, 5 and 6 digits: a quartet takes the
+ * first tier, in that order, whose threshold lies above its prediction, and the FP64 path if
+ * none does (a tier is disabled by a threshold of -1e30).  The parameters are copied
+ * (synchronously); a later call replaces them.  Thresholds must be finite.
  */
-int lx_router_set(const void* params_f16, float tau);
+int lx_router_set(const void* params_f16, const float* tau);
 
-/* Inference: out[i] = MLP(feat[i]) with FP16 parameters params_f16 (DEVICE, LX_MLP_NPARAM halves). */
+/* Inference: out[i * LX_MLP_NOUT + o] = output o of MLP(feat[i]) with FP16 parameters
+ * params_f16 (DEVICE, LX_MLP_NPARAM halves). */
 int lx_mlp_forward(const void* params_f16, const float* feat, int64_t n, float* out, void* cuda_stream);
 
 /*
- * Training gradient: loss[0] = mean over i < n of (MLP(feat[i]) - target[i])^2, evaluated with
- * the FP16-rounded params, and grad = its gradient with respect to params (straight through
- * the rounding).  All DEVICE float arrays; grad and loss are overwritten.
+ * Training gradient: loss[0] = mean over i < n of sum_o (MLP(feat[i])_o - target[i*LX_MLP_NOUT+o])^2,
+ * evaluated with the FP16-rounded params, and grad = its gradient with respect to params
+ * (straight through the rounding).  All DEVICE float arrays; grad and loss are overwritten.
  */
 int lx_mlp_grad(const float* params, const float* feat, const float* target, int64_t n, float* grad, float* loss,
                 void* cuda_stream);

@@ -131,8 +131,12 @@ int validate(const lx_shell* shells, int32_t nshell, const double* exps, const d
     if (nshell < 0 || nquartet < 0 || nprim_total < 0) return LX_ERR_SIZE;
     if ((nshell > 0 && !shells) || (nquartet > 0 && !quartets)) return LX_ERR_NULL;
     if (need_prims && nprim_total > 0 && (!exps || !coefs)) return LX_ERR_NULL;
-    if (flags & ~(LX_SOLID | LX_PATH_SPLIT | LX_PATH_ROUTED | LX_TIME_STAGES)) return LX_ERR_FLAGS;
+    if (flags & ~(LX_SOLID | LX_PATH_SPLIT | LX_PATH_ROUTED | LX_TIME_STAGES | LX_SPLIT_DIGITS_MASK)) return LX_ERR_FLAGS;
     if ((flags & LX_PATH_ROUTED) && (flags & LX_PATH_SPLIT)) return LX_ERR_FLAGS;
+    if (flags & LX_SPLIT_DIGITS_MASK) {  // a digit count: 4, 5 or 6, with the split path only
+        const int nd = (flags & LX_SPLIT_DIGITS_MASK) >> 4;
+        if (!(flags & LX_PATH_SPLIT) || nd < SPLIT_MIN_DIGITS || nd > SPLIT_NSLICE) return LX_ERR_FLAGS;
+    }
     for (int32_t s = 0; s < nshell; ++s) {
         const lx_shell& d = shells[s];
         if (d.l < 0 || d.l > LX_LMAX || d.nprim < 1 || d.nprim > LX_KMAX || d.reserved != 0) return LX_ERR_SHELL;
@@ -293,6 +297,7 @@ struct ChunkPlan {
     std::vector<DQuartet> quartets;
     std::vector<WorkItem> items_h, items_br, items_g1, items_g2;
     int br_lmax = 0;  // largest L of the chunk's quartets
+    int digits = 6;   // split path: BF16 digits kept per value (one count per batch)
     int fold_lcap = 0, fold_qcap = 0, fold_wcap = 0;  // solid fold: largest l, Q and W rows of the chunk's pairs
     int jkd_qc = 0;          // J/K on the FP64 path: chunk width of jk_direct_kernel
     size_t jkd_smem = 0;     // and its shared memory
@@ -315,6 +320,8 @@ struct ChunkPlan {
 void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int flags, size_t chunk_base,
                  ChunkPlan& P, const Overrides& ov = Overrides()) {
     const bool solid = flags & LX_SOLID, split = flags & LX_PATH_SPLIT, jk = flags & JK_DIGEST;
+    const int nd_flag = (flags & LX_SPLIT_DIGITS_MASK) >> 4, nd = nd_flag ? nd_flag : SPLIT_NSLICE;
+    P.digits = nd;
     P.pairs.clear();
     P.quartets.clear();
     P.items_h.clear();
@@ -581,6 +588,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             g1.transpose = 1;
             g1.tb = split_tb(d.nab);
             g1.a_nseg = 1;
+            g1.nd = nd;
             P.sg1.push_back(g1);
             SplitGemmDesc g2{};
             g2.a_dig = q.a2_dig;
@@ -595,6 +603,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             g2.transpose = 0;
             g2.tb = split_tb(d.ncd);
             g2.a_nseg = split_nseg(q.nkb2);  // X: one exponent per row and segment
+            g2.nd = nd;
             P.sg2.push_back(g2);
         }
     }
@@ -665,7 +674,7 @@ int plan_batch(const lx_shell* shells, int32_t nshell, const double* exps, const
     B.nprim = nprim_total;
     B.head = head_bytes(nshell, nprim_total);
     if (workspace_bytes < B.head + CHUNK_SLACK) return LX_ERR_WORKSPACE;
-    const int pflags = flags & (LX_SOLID | LX_PATH_SPLIT | JK_DIGEST);
+    const int pflags = flags & (LX_SOLID | LX_PATH_SPLIT | JK_DIGEST | LX_SPLIT_DIGITS_MASK);
     std::vector<Chunk> chunks;
     int v = plan_chunks(shells, quartets, nquartet, pflags, workspace_bytes - B.head, chunks);
     if (v != LX_OK) return v;
@@ -772,7 +781,7 @@ int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector
             if ((e = tm.end(LX_STAGE_SPLIT, 2)) != cudaSuccess) return cuda_fail(e);
             if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
             if ((e = launch_split_gemm(d_sg1, items(P.off_isg1), (int)P.items_sg1.size(), wsb, ws, status, st,
-                                       false)) != cudaSuccess)
+                                       false, P.digits)) != cudaSuccess)
                 return cuda_fail(e);
             if ((e = tm.end(LX_STAGE_GEMM1, 1)) != cudaSuccess) return cuda_fail(e);
             // the other operand of GEMM2: digit planes of [ab|q], one exponent per row and segment
@@ -782,7 +791,7 @@ int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector
             if ((e = tm.end(LX_STAGE_SPLIT, 1)) != cudaSuccess) return cuda_fail(e);
             if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
             if ((e = launch_split_gemm(d_sg2, items(P.off_isg2), (int)P.items_sg2.size(), wsb, out, status, st,
-                                       true)) != cudaSuccess)
+                                       true, P.digits)) != cudaSuccess)
                 return cuda_fail(e);
             if ((e = tm.end(LX_STAGE_GEMM2, 1)) != cudaSuccess) return cuda_fail(e);
         } else {
@@ -960,14 +969,15 @@ int eri_batch_unstaged(const lx_shell* shells, int32_t nshell, const double* exp
 
 namespace {
 
-// Routing network of LX_PATH_ROUTED per device (FP16 parameters on the device, threshold).
+// Routing network of LX_PATH_ROUTED per device (FP16 parameters on the device, thresholds of
+// the 4-, 5- and 6-digit split tiers on the predicted log10 split error).
 std::mutex g_router_mutex;
 void* g_router_params[MAX_DEVICES];
-float g_router_tau[MAX_DEVICES];
+float g_router_tau[MAX_DEVICES][LX_ROUTE_NTIER];
 
 // Workspace the routed call needs before the batches run: features and predictions.
 size_t routed_scratch_bytes(int64_t n) {
-    return align256(sizeof(float) * LX_MLP_NIN * (size_t)n) + align256(sizeof(float) * (size_t)n);
+    return align256(sizeof(float) * LX_MLP_NIN * (size_t)n) + align256(sizeof(float) * LX_MLP_NOUT * (size_t)n);
 }
 
 // Plan one batch, stage its descriptors in pinned memory and enqueue it (inputs validated,
@@ -1097,11 +1107,11 @@ int eri_entry(const lx_shell* shells, int32_t nshell, const double* exps, const 
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e);
     const void* params = nullptr;
-    float tau = 0.f;
+    float tau[LX_ROUTE_NTIER];
     {
         std::lock_guard<std::mutex> lock(g_router_mutex);
         params = g_router_params[dev];
-        tau = g_router_tau[dev];
+        for (int t = 0; t < LX_ROUTE_NTIER; ++t) tau[t] = g_router_tau[dev][t];
     }
     if (!params) return LX_ERR_NO_ROUTER;
     if (workspace_bytes < routed_scratch_bytes(nquartet)) return LX_ERR_WORKSPACE;
@@ -1111,11 +1121,13 @@ int eri_entry(const lx_shell* shells, int32_t nshell, const double* exps, const 
     if ((v = lx_route_features(shells, nshell, exps, nprim_total, quartets, nquartet, feat, cuda_stream)) != LX_OK)
         return v;
     if ((e = launch_mlp_forward(params, feat, nquartet, pred, st)) != cudaSuccess) return cuda_fail(e);
-    std::vector<float> hp(nquartet);
-    if ((e = cudaMemcpyAsync(hp.data(), pred, sizeof(float) * nquartet, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    std::vector<float> hp((size_t)LX_MLP_NOUT * nquartet);
+    if ((e = cudaMemcpyAsync(hp.data(), pred, sizeof(float) * LX_MLP_NOUT * nquartet, cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
         return cuda_fail(e);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e);
-    std::vector<lx_quartet> q64, qsp;
+    // sub-batches: FP64, then the split tiers of 4, 5 and 6 digits
+    std::vector<lx_quartet> sub[1 + LX_ROUTE_NTIER];
     const bool solid = flags & LX_SOLID;
     for (int64_t i = 0; i < nquartet; ++i) {
         const lx_quartet& q = quartets[i];
@@ -1123,17 +1135,24 @@ int eri_entry(const lx_shell* shells, int32_t nshell, const double* exps, const 
         const double nab = (double)nfun(a.l, solid) * nfun(b.l, solid), ncd = (double)nfun(c.l, solid) * nfun(d.l, solid);
         const double kp = (double)a.nprim * b.nprim * pyr(a.l + b.l), kq = (double)c.nprim * d.nprim * pyr(c.l + d.l);
         const double flop = 2.0 * nab * kp * kq + 2.0 * nab * kq * ncd;
-        (hp[i] >= tau || flop < LX_ROUTE_SPLIT_MIN_FLOP ? q64 : qsp).push_back(q);
+        const float err = hp[(size_t)LX_MLP_NOUT * i + 1];  // predicted log10 split error (6 digits)
+        int dst = 0;
+        if (flop >= LX_ROUTE_SPLIT_MIN_FLOP)
+            for (int t = 0; t < LX_ROUTE_NTIER; ++t)
+                if (err < tau[t]) {
+                    dst = 1 + t;
+                    break;
+                }
+        sub[dst].push_back(q);
     }
     const int32_t base = flags & ~LX_PATH_ROUTED;
-    if (!q64.empty() && (v = eri_batch_staged(shells, nshell, exps, coefs, nprim_total, q64.data(),
-                                              (int64_t)q64.size(), base, out, workspace, workspace_bytes, st,
-                                              status, jk)) != LX_OK)
-        return v;
-    if (!qsp.empty() && (v = eri_batch_staged(shells, nshell, exps, coefs, nprim_total, qsp.data(),
-                                              (int64_t)qsp.size(), base | LX_PATH_SPLIT, out, workspace,
-                                              workspace_bytes, st, status, jk)) != LX_OK)
-        return v;
+    for (int k = 0; k <= LX_ROUTE_NTIER; ++k) {
+        if (sub[k].empty()) continue;
+        const int32_t f = k == 0 ? base : base | LX_PATH_SPLIT | LX_SPLIT_DIGITS(SPLIT_MIN_DIGITS + k - 1);
+        if ((v = eri_batch_staged(shells, nshell, exps, coefs, nprim_total, sub[k].data(), (int64_t)sub[k].size(), f,
+                                  out, workspace, workspace_bytes, st, status, jk)) != LX_OK)
+            return v;
+    }
     return LX_OK;
 }
 
@@ -1173,9 +1192,10 @@ int lx_eri_batch(const lx_shell* shells, int32_t nshell, const double* exps, con
                      workspace_bytes, cuda_stream, nullptr);
 }
 
-int lx_router_set(const void* params_f16, float tau) {
-    if (!params_f16) return LX_ERR_NULL;
-    if (!std::isfinite(tau)) return LX_ERR_SIZE;
+int lx_router_set(const void* params_f16, const float* tau) {
+    if (!params_f16 || !tau) return LX_ERR_NULL;
+    for (int t = 0; t < LX_ROUTE_NTIER; ++t)
+        if (!std::isfinite(tau[t])) return LX_ERR_SIZE;
     unsigned* status = nullptr;
     int v = ensure_device(&status);
     if (v != LX_OK) return v;
@@ -1193,7 +1213,7 @@ int lx_router_set(const void* params_f16, float tau) {
     if ((e = cudaMemcpy(g_router_params[dev], params_f16, 2 * (size_t)LX_MLP_NPARAM, cudaMemcpyHostToDevice)) !=
         cudaSuccess)
         return cuda_fail(e);
-    g_router_tau[dev] = tau;
+    for (int t = 0; t < LX_ROUTE_NTIER; ++t) g_router_tau[dev][t] = tau[t];
     return LX_OK;
 }
 
@@ -1673,8 +1693,9 @@ int lx_hermite_H(const lx_shell* shells, int32_t nshell, const double* exps, con
 }
 
 int lx_split_gemm(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda, const double* B, int32_t ldb,
-                  double* C, int32_t ldc, void* cuda_stream) {
+                  double* C, int32_t ldc, int32_t digits, void* cuda_stream) {
     if (M < 1 || N < 1 || K < 1 || K > (1 << 20) || lda < K || ldb < K || ldc < N) return LX_ERR_SIZE;
+    if (digits < SPLIT_MIN_DIGITS || digits > SPLIT_NSLICE) return LX_ERR_SIZE;
     if (!A || !B || !C) return LX_ERR_NULL;
     unsigned* status = nullptr;
     int v = ensure_device(&status);
@@ -1716,6 +1737,7 @@ int lx_split_gemm(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda,
     g.ldc = ldc;
     g.tb = tb;
     g.a_nseg = 1;
+    g.nd = digits;
     std::vector<char> blob(blob_bytes, 0);
     std::memcpy(blob.data() + o_rd, rd.data(), sizeof(SplitRowsDesc) * 2);
     std::memcpy(blob.data() + o_g, &g, sizeof(g));
@@ -1736,7 +1758,7 @@ int lx_split_gemm(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda,
         return cuda_fail(e);
     if ((e = launch_split_gemm(reinterpret_cast<const SplitGemmDesc*>(scratch + o_g),
                                reinterpret_cast<const WorkItem*>(scratch + o_ig), (int)ig.size(), scratch, C, status,
-                               st, false)) != cudaSuccess)
+                               st, false, digits)) != cudaSuccess)
         return cuda_fail(e);
     if ((e = cudaFreeAsync(scratch, st)) != cudaSuccess) return cuda_fail(e);
     return LX_OK;

@@ -1,9 +1,10 @@
-// Learned router: per-quartet features, a 3-layer MLP (20 -> 64 -> 64 -> 1, FP16 weights)
-// predicting log10 of the quartet's largest |integral|, and its training kernels
-// (forward, backward with the gradient of the mean squared error, Adam).
+// Learned router: per-quartet features, a 3-layer MLP (20 -> 64 -> 64 -> 2, FP16 weights)
+// predicting log10 of the quartet's largest |integral| (output 0) and log10 of the split
+// path's error on it (output 1), and its training kernels (forward, backward with the
+// gradient of the mean over samples of the summed squared errors, Adam).
 //
 // Parameter layout (LX_MLP_NPARAM floats): W1[64][20], b1[64], W2[64][64], b2[64],
-// W3[64], b3[1].  Activations are ReLU.  The forward pass always uses the FP16-rounded
+// W3[2][64], b3[2].  Activations are ReLU.  The forward pass always uses the FP16-rounded
 // weights; training keeps FP32 master weights and takes the gradient of the FP16 forward
 // (straight through the rounding).
 #include <cmath>
@@ -15,9 +16,9 @@ namespace lx {
 
 namespace {
 
-constexpr int NIN = LX_MLP_NIN, NW = LX_MLP_WIDTH;
+constexpr int NIN = LX_MLP_NIN, NW = LX_MLP_WIDTH, NOUT = LX_MLP_NOUT;
 constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NW * NIN, OFF_W2 = OFF_B1 + NW, OFF_B2 = OFF_W2 + NW * NW,
-              OFF_W3 = OFF_B2 + NW, OFF_B3 = OFF_W3 + NW, NPARAM = OFF_B3 + 1;
+              OFF_W3 = OFF_B2 + NW, OFF_B3 = OFF_W3 + NOUT * NW, NPARAM = OFF_B3 + NOUT;
 static_assert(NPARAM == LX_MLP_NPARAM, "parameter layout");
 
 constexpr float PI_F = 3.14159265358979f;
@@ -98,20 +99,23 @@ __global__ void mlp_forward_kernel(const __half* __restrict__ p16, const float* 
         for (int k = 0; k < NIN; ++k) a += P[OFF_W1 + j * NIN + k] * x[k];
         h1[j] = relu(a);
     }
-    float y = P[OFF_B3];
+    float y[NOUT];
+    for (int o = 0; o < NOUT; ++o) y[o] = P[OFF_B3 + o];
     for (int j = 0; j < NW; ++j) {
         float a = P[OFF_B2 + j];
         for (int k = 0; k < NW; ++k) a += P[OFF_W2 + j * NW + k] * h1[k];
-        y += P[OFF_W3 + j] * relu(a);
+        const float h2 = relu(a);
+        for (int o = 0; o < NOUT; ++o) y[o] += P[OFF_W3 + o * NW + j] * h2;
     }
-    out[i] = y;
+    for (int o = 0; o < NOUT; ++o) out[i * NOUT + o] = y[o];
 }
 
 constexpr int TB = 128;  // samples per training block
 
-// Loss and gradient of mean((y - t)^2) over n samples, forward with FP16-rounded weights.
-// grad (NPARAM floats) and loss (1 float) must be zero on entry; blocks add into them.
-constexpr size_t GRAD_SMEM = sizeof(float) * (NPARAM + TB * (NIN + 1) + 3 * TB * (NW + 1) + TB);
+// Loss and gradient of (1/n) sum_i sum_o (y_io - t_io)^2 over n samples (targets t[n][NOUT]),
+// forward with FP16-rounded weights.  grad (NPARAM floats) and loss (1 float) must be zero on
+// entry; blocks add into them.
+constexpr size_t GRAD_SMEM = sizeof(float) * (NPARAM + TB * (NIN + 1) + 3 * TB * (NW + 1) + TB * NOUT);
 
 __global__ void __launch_bounds__(TB) mlp_grad_kernel(const float* __restrict__ params,
                                                        const float* __restrict__ feat,
@@ -123,7 +127,7 @@ __global__ void __launch_bounds__(TB) mlp_grad_kernel(const float* __restrict__ 
     float (*H1)[NW + 1] = reinterpret_cast<float (*)[NW + 1]>(&X[TB][0]);
     float (*D2)[NW + 1] = H1 + TB;  // dL/d(pre-activation 2), then reused for layer 1
     float (*H2)[NW + 1] = D2 + TB;
-    float* DY = &H2[TB][0];
+    float (*DY)[NOUT] = reinterpret_cast<float (*)[NOUT]>(&H2[TB][0]);
     for (int j = threadIdx.x; j < NPARAM; j += TB) P[j] = __half2float(__float2half_rn(params[j]));
     const int t = threadIdx.x;
     const int64_t i = blockIdx.x * (int64_t)TB + t;
@@ -136,34 +140,43 @@ __global__ void __launch_bounds__(TB) mlp_grad_kernel(const float* __restrict__ 
         for (int k = 0; k < NIN; ++k) a += P[OFF_W1 + j * NIN + k] * X[t][k];
         H1[t][j] = relu(a);
     }
-    float y = P[OFF_B3];
+    float y[NOUT];
+    for (int o = 0; o < NOUT; ++o) y[o] = P[OFF_B3 + o];
     for (int j = 0; j < NW; ++j) {
         float a = P[OFF_B2 + j];
         for (int k = 0; k < NW; ++k) a += P[OFF_W2 + j * NW + k] * H1[t][k];
         H2[t][j] = relu(a);
-        y += P[OFF_W3 + j] * H2[t][j];
+        for (int o = 0; o < NOUT; ++o) y[o] += P[OFF_W3 + o * NW + j] * H2[t][j];
     }
-    const float r = live ? y - target[i] : 0.f;
-    const float dy = live ? 2.f * r / (float)n : 0.f;
-    DY[t] = dy;
-    if (live) atomicAdd(loss, r * r / (float)n);
-    // dL/d(pre2)_j = dy W3_j [pre2_j > 0]
-    for (int j = 0; j < NW; ++j) D2[t][j] = H2[t][j] > 0.f ? dy * P[OFF_W3 + j] : 0.f;
+    float l2 = 0.f;
+    for (int o = 0; o < NOUT; ++o) {
+        const float r = live ? y[o] - target[i * NOUT + o] : 0.f;
+        DY[t][o] = live ? 2.f * r / (float)n : 0.f;
+        l2 += r * r;
+    }
+    if (live) atomicAdd(loss, l2 / (float)n);
+    // dL/d(pre2)_j = sum_o dy_o W3[o][j] [pre2_j > 0]
+    for (int j = 0; j < NW; ++j) {
+        float a = 0.f;
+        for (int o = 0; o < NOUT; ++o) a += DY[t][o] * P[OFF_W3 + o * NW + j];
+        D2[t][j] = H2[t][j] > 0.f ? a : 0.f;
+    }
     __syncthreads();
     // layer-3 and layer-2 gradients, reduced over the block's samples
     for (int j = t; j < NW; j += TB) {
-        float gw3 = 0.f, gb2 = 0.f;
+        float gw3[NOUT], gb2 = 0.f;
+        for (int o = 0; o < NOUT; ++o) gw3[o] = 0.f;
         for (int s = 0; s < TB; ++s) {
-            gw3 += DY[s] * H2[s][j];
+            for (int o = 0; o < NOUT; ++o) gw3[o] += DY[s][o] * H2[s][j];
             gb2 += D2[s][j];
         }
-        atomicAdd(&grad[OFF_W3 + j], gw3);
+        for (int o = 0; o < NOUT; ++o) atomicAdd(&grad[OFF_W3 + o * NW + j], gw3[o]);
         atomicAdd(&grad[OFF_B2 + j], gb2);
     }
-    if (t == 0) {
+    if (t < NOUT) {
         float gb3 = 0.f;
-        for (int s = 0; s < TB; ++s) gb3 += DY[s];
-        atomicAdd(&grad[OFF_B3], gb3);
+        for (int s = 0; s < TB; ++s) gb3 += DY[s][t];
+        atomicAdd(&grad[OFF_B3 + t], gb3);
     }
     for (int e = t; e < NW * NW; e += TB) {
         const int j = e / NW, k = e - j * NW;

@@ -511,11 +511,12 @@ __device__ inline long long shr_round(long long x, int s) {
 // the next segment accumulates in the other TMEM set.  Per k the combined value is at most
 // 2^(2W - 48) = 2^48, so the 64-bit sum is shifted down by xs bits when K exceeds 2^14.
 //
-// The MMAs of one A slice s and one K step are issued against the B slices 0..NSLICE-1-s at
-// once: slice t lies tb rows after slice t-1 in shared memory and diagonal s + t lies tb TMEM
+// The MMAs of one A slice s and one K step are issued against the B slices 0..nd-1-s at once:
+// slice t lies tb rows after slice t-1 in shared memory and diagonal s + t lies tb TMEM
 // columns after s + t - 1, so A_s [B_0; B_1; ...] lands every product on its diagonal in one
-// MMA of N = (NSLICE - s) tb <= 192.
-template <bool SEGS>
+// MMA of N = (nd - s) tb <= 192.  With nd < NSLICE digits only the first nd slices of each
+// operand block are loaded, nd MMAs are issued per K step and nd diagonals drained.
+template <bool SEGS, int ND>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     split_gemm_kernel(const SplitGemmDesc* __restrict__ probs, const WorkItem* __restrict__ items, int nitems,
                       const char* __restrict__ ws, double* __restrict__ cbase, unsigned* status) {
@@ -565,7 +566,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 // whatever the stage held before and only reach output rows >= M, which the
                 // drain discards
                 const int vr = min(SPLIT_TA, ((P.M + 7) & ~7) - it.a * SPLIT_TA);
-                const int a_bytes = vr == SPLIT_TA ? A_BLOCK : SPLIT_NSLICE * vr * SPLIT_KB * 2;
+                // the first nd digit slices of each block (slices are the outer index of a block)
+                constexpr int nd = ND;  // P.nd equals ND (the launch is chosen by it)
+                const int a_bytes = nd * vr * SPLIT_KB * 2, b_bytes = nd * P.tb * SPLIT_KB * 2;
                 for (int kb = 0; kb < P.nkb; ++kb, ++g) {
                     const int st = g % STAGES, use = g / STAGES;
                     if ((use > 0 && !mbar_wait(&empty_bar[st], (use - 1) & 1, status)) || *(volatile int*)&abort_sh) {
@@ -574,15 +577,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                         break;
                     }
                     unsigned char* sa = smem + st * STAGE_BYTES;
-                    mbar_expect_tx(&full_bar[st], a_bytes + b_block);
+                    mbar_expect_tx(&full_bar[st], a_bytes + b_bytes);
                     if (vr == SPLIT_TA) {
-                        bulk_g2s(sa, a_src + (int64_t)kb * A_BLOCK, A_BLOCK, &full_bar[st]);
+                        bulk_g2s(sa, a_src + (int64_t)kb * A_BLOCK, a_bytes, &full_bar[st]);
                     } else {
-                        for (int sl = 0; sl < SPLIT_NSLICE; ++sl)
+                        for (int sl = 0; sl < nd; ++sl)
                             bulk_g2s(sa + sl * A_SLICE, a_src + (int64_t)kb * A_BLOCK + sl * A_SLICE,
                                      vr * SPLIT_KB * 2, &full_bar[st]);
                     }
-                    bulk_g2s(sa + A_BLOCK, b_src + (int64_t)kb * b_block, b_block, &full_bar[st]);
+                    bulk_g2s(sa + A_BLOCK, b_src + (int64_t)kb * b_block, b_bytes, &full_bar[st]);
                 }
             }
             // no copy may still be landing in shared memory when the CTA exits
@@ -605,9 +608,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 const WorkItem it = items[w];
                 const SplitGemmDesc P = probs[it.q];
                 const int tb = P.tb, nkb = P.nkb;
-                uint32_t idesc[SPLIT_NSLICE];
+                constexpr int nd = ND;
+                uint32_t idesc[ND];
 #pragma unroll
-                for (int s = 0; s < SPLIT_NSLICE; ++s) idesc[s] = idesc_bf16(SPLIT_TA, (SPLIT_NSLICE - s) * tb);
+                for (int s = 0; s < ND; ++s) idesc[s] = idesc_bf16(SPLIT_TA, (ND - s) * tb);
                 for (int kb0 = 0; kb0 < nkb && ok; kb0 += SPLIT_SEG_KB, ++sgc) {
                     const int buf = sgc & 1, ub = sgc >> 1;
                     if (ub > 0) {
@@ -632,7 +636,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 #pragma unroll
                         for (int ks = 0; ks < SPLIT_KB / 16; ++ks) {
 #pragma unroll
-                            for (int s = 0; s < SPLIT_NSLICE; ++s) {
+                            for (int s = 0; s < ND; ++s) {
                                 // the slice-0 MMA of a segment's first K step covers every diagonal
                                 const uint32_t acc = (ks == 0 && s == 0 && kb == kb0) ? 0u : 1u;
                                 umma_bf16(dcol + s * tb, ad0 + ((s * A_SLICE + ks * 256) >> 4), bd0 + ((ks * 256) >> 4),
@@ -661,6 +665,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             const WorkItem it = items[w];
             const SplitGemmDesc P = probs[it.q];
             const int tb = P.tb, nkb = P.nkb;
+            constexpr int nd = ND;
             const int m0 = it.a * SPLIT_TA, n0 = it.b * tb;
             const int nt = min(tb, P.N - n0);
             const bool mine = c0 < nt;  // warp-uniform
@@ -694,29 +699,29 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 if (!ok) break;
                 tc_fence_after();
                 if (mine) {
-                    // all six diagonals of HC columns in flight before one wait (the aligned sum
+                    // the nd diagonals of HC columns in flight before one wait (the aligned sum
                     // takes its 16 columns in two halves, to stay within the registers)
                     constexpr int HC = SEGS ? 8 : DCOLS;
 #pragma unroll
                     for (int h = 0; h < DCOLS / HC; ++h) {
-                        uint32_t r[SPLIT_NSLICE][HC];
+                        uint32_t r[ND][HC];
 #pragma unroll
-                        for (int dg = 0; dg < SPLIT_NSLICE; ++dg) {
+                        for (int dg = 0; dg < ND; ++dg) {
                             if constexpr (HC == 16)
                                 tmem_ld16(lane_base + buf * BUF_COLS + dg * tb, r[dg]);
                             else
                                 tmem_ld8(lane_base + buf * BUF_COLS + dg * tb + HC * h, r[dg]);
                         }
                         tmem_ld_wait();
-                        // v = sum_d G_d 2^(BETA (NSLICE-2-d)) (>> xs); the last diagonal is rounded down BETA bits
+                        // v = sum_d G_d 2^(BETA (nd-2-d)) (>> xs); the last diagonal is rounded down BETA bits
 #pragma unroll
                         for (int jj = 0; jj < HC; ++jj) {
                             long long v = 0;
 #pragma unroll
-                            for (int dg = 0; dg < SPLIT_NSLICE; ++dg) {
+                            for (int dg = 0; dg < ND; ++dg) {
                                 const long long gv = (long long)__float2int_rn(__uint_as_float(r[dg][jj]));
-                                if (dg < SPLIT_NSLICE - 1)
-                                    v += gv << (SPLIT_BETA * (SPLIT_NSLICE - 2 - dg));
+                                if (dg < nd - 1)
+                                    v += gv << (SPLIT_BETA * (nd - 2 - dg));
                                 else
                                     v += (gv + (1ll << (SPLIT_BETA - 1))) >> SPLIT_BETA;
                             }
@@ -741,9 +746,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 for (int j = 0; j < DCOLS; ++j) {
                     const int col = n0 + c0 + j;
                     if (c0 + j < nt) {
-                        // D = 2^(eA + eB - BETA NSLICE + xs) * acc: one rounding (int64 -> FP64, to
+                        // D = 2^(eA + eB - BETA nd + xs) * acc: one rounding (int64 -> FP64, to
                         // nearest even), then an exact power-of-two scaling (acc = 0 gives 0)
-                        const int scale = ea + eb_tab[col] - SPLIT_BETA * SPLIT_NSLICE + xs;
+                        const int scale = ea + eb_tab[col] - SPLIT_BETA * nd + xs;
                         const double v = scale2(__ll2double_rn(acc[j]), scale);
                         if (P.transpose)
                             cbase[P.c_off + (int64_t)col * P.ldc + row] = v;
@@ -817,10 +822,13 @@ cudaError_t init_split_kernels(const int* host_tuv) {
         return e;
     const uint16_t* p = static_cast<const uint16_t*>(dev_table);
     if ((e = cudaMemcpyToSymbol(g_gidx, &p, sizeof(p))) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(split_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  SMEM_BYTES)) != cudaSuccess)
-        return e;
-    return cudaFuncSetAttribute(split_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    const void* kernels[] = {(const void*)split_gemm_kernel<false, 4>, (const void*)split_gemm_kernel<false, 5>,
+                             (const void*)split_gemm_kernel<false, 6>, (const void*)split_gemm_kernel<true, 4>,
+                             (const void*)split_gemm_kernel<true, 5>,  (const void*)split_gemm_kernel<true, 6>};
+    for (const void* k : kernels)
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)) != cudaSuccess)
+            return e;
+    return cudaSuccess;
 }
 
 cudaError_t launch_wait_selftest(unsigned* status, unsigned long long limit, cudaStream_t st) {
@@ -830,7 +838,7 @@ cudaError_t launch_wait_selftest(unsigned* status, unsigned long long limit, cud
 }
 
 cudaError_t launch_split_gemm(const SplitGemmDesc* probs, const WorkItem* items, int nitems, const char* ws,
-                              double* cbase, unsigned* status, cudaStream_t st, bool segments) {
+                              double* cbase, unsigned* status, cudaStream_t st, bool segments, int digits) {
     if (nitems <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -838,10 +846,17 @@ cudaError_t launch_split_gemm(const SplitGemmDesc* probs, const WorkItem* items,
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     // one CTA per SM (the TMEM allocation and the operand ring take the whole SM)
     const int grid = nitems < sms ? nitems : sms;
-    if (segments)
-        split_gemm_kernel<true><<<grid, GEMM_THREADS, SMEM_BYTES, st>>>(probs, items, nitems, ws, cbase, status);
-    else
-        split_gemm_kernel<false><<<grid, GEMM_THREADS, SMEM_BYTES, st>>>(probs, items, nitems, ws, cbase, status);
+#define LX_SPLIT_GEMM(S, D) split_gemm_kernel<S, D><<<grid, GEMM_THREADS, SMEM_BYTES, st>>>(probs, items, nitems, ws, cbase, status)
+    switch ((segments ? 8 : 0) + digits) {
+        case 4: LX_SPLIT_GEMM(false, 4); break;
+        case 5: LX_SPLIT_GEMM(false, 5); break;
+        case 6: LX_SPLIT_GEMM(false, 6); break;
+        case 12: LX_SPLIT_GEMM(true, 4); break;
+        case 13: LX_SPLIT_GEMM(true, 5); break;
+        case 14: LX_SPLIT_GEMM(true, 6); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef LX_SPLIT_GEMM
     return cudaGetLastError();
 }
 

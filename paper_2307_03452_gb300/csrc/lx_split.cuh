@@ -79,13 +79,15 @@ static_assert(NHERM_TOT < 65536, "[r]^(0) positions fit 16 bits");
 // with nkb K blocks; D written to (double*)C + c_off with row stride ldc (transpose: D[m][n] ->
 // C[n][m]).  B carries one exponent per row; A one per row (a_nseg = 1) or one per row and
 // segment of SPLIT_SEG_KB K blocks (a_nseg = split_nseg(nkb), int[row][a_nseg]).  The A operand
-// is read only up to M rows rounded to 8 (the last row tile is loaded that far).
+// is read only up to M rows rounded to 8 (the last row tile is loaded that far).  Only the
+// first nd (4..6) digit slices of each operand are used: the products with s + t < nd.
 struct SplitGemmDesc {
     int64_t a_dig, a_exp, b_dig, b_exp;
     int64_t c_off;
     int M, N, nkb, ldc, transpose, tb;
-    int a_nseg, pad;
+    int a_nseg, nd;
 };
+constexpr int SPLIT_MIN_DIGITS = 4;
 
 // B row tile for an operand of N rows: as few tiles as SPLIT_TB rows allow, each a multiple
 // of 16 rows (169 rows -> 6 tiles of 32, 81 -> 3 of 32, 13 -> 1 of 16).
@@ -116,8 +118,8 @@ cudaError_t launch_colmax(const ColMaxDesc* descs, const WorkItem* items, int ni
 // limit, on an mbarrier nothing arrives on): sets the status word's timeout bit.
 cudaError_t launch_wait_selftest(unsigned* status, unsigned long long limit, cudaStream_t st);
 // segments: some A operands carry one exponent per segment (a_nseg may exceed 1); otherwise
-// every problem has a_nseg = 1
+// every problem has a_nseg = 1.  digits: the nd (4..6) of every problem of the launch.
 cudaError_t launch_split_gemm(const SplitGemmDesc* probs, const WorkItem* items, int nitems, const char* ws,
-                              double* cbase, unsigned* status, cudaStream_t st, bool segments);
+                              double* cbase, unsigned* status, cudaStream_t st, bool segments, int digits);
 
 }  // namespace lx

@@ -41,11 +41,16 @@ EXPORTS = sorted(["lx_eri_out_size", "lx_eri_workspace_size", "lx_eri_workspace_
 TILE_SHAPES = ["32x64", "64x32", "32x32", "64x64"]
 MLP_NIN = 20
 MLP_WIDTH = 64
-MLP_NPARAM = MLP_WIDTH * MLP_NIN + MLP_WIDTH + MLP_WIDTH * MLP_WIDTH + MLP_WIDTH + MLP_WIDTH + 1
+MLP_NOUT = 2  # log10 max |integral|, log10 of the split path's error (6 digits)
+MLP_NPARAM = MLP_WIDTH * MLP_NIN + MLP_WIDTH + MLP_WIDTH * MLP_WIDTH + MLP_WIDTH + MLP_NOUT * MLP_WIDTH + MLP_NOUT
+ROUTE_TIERS = (4, 5, 6)  # digits of the split tiers of path "routed"
+SPLIT_DIGITS_MASK = 0x70
 LX_PATH_SPLIT = 0x2
 LX_PATH_ROUTED = 0x4
 LX_TIME_STAGES = 0x200
-PATH_FLAGS = {"fp64": 0, "split": LX_PATH_SPLIT, "routed": LX_PATH_ROUTED}
+# "split4" / "split5": the split path keeping 4 / 5 digits per value ("split": 6)
+PATH_FLAGS = {"fp64": 0, "split": LX_PATH_SPLIT, "split4": LX_PATH_SPLIT | (4 << 4), "split5": LX_PATH_SPLIT | (5 << 4),
+              "split6": LX_PATH_SPLIT | (6 << 4), "routed": LX_PATH_ROUTED}
 STAGES = ["norm", "pair_h", "boys_r", "gemm1", "gemm2", "split", "digest"]
 
 
@@ -116,7 +121,7 @@ def load(build_if_missing: bool = True):
         lib.lx_hermite_R.restype = ctypes.c_int
         lib.lx_hermite_H.argtypes = [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_i32, c_i32, c_vp, c_i64, c_vp]
         lib.lx_hermite_H.restype = ctypes.c_int
-        lib.lx_split_gemm.argtypes = [c_i32, c_i32, c_i32, c_vp, c_i32, c_vp, c_i32, c_vp, c_i32, c_vp]
+        lib.lx_split_gemm.argtypes = [c_i32, c_i32, c_i32, c_vp, c_i32, c_vp, c_i32, c_vp, c_i32, c_i32, c_vp]
         lib.lx_split_gemm.restype = ctypes.c_int
         lib.lx_eri_graph_create.argtypes = [c_vp, c_i32, c_vp, c_vp, c_i32, c_vp, c_i64, c_i32, c_vp, c_vp, c_sz,
                                             ctypes.POINTER(c_vp)]
@@ -136,7 +141,7 @@ def load(build_if_missing: bool = True):
         lib.lx_tune_clear.restype = ctypes.c_int
         lib.lx_route_features.argtypes = [c_vp, c_i32, c_vp, c_i32, c_vp, c_i64, c_vp, c_vp]
         lib.lx_route_features.restype = ctypes.c_int
-        lib.lx_router_set.argtypes = [c_vp, ctypes.c_float]
+        lib.lx_router_set.argtypes = [c_vp, c_vp]
         lib.lx_router_set.restype = ctypes.c_int
         lib.lx_mlp_forward.argtypes = [c_vp, c_vp, c_i64, c_vp, c_vp]
         lib.lx_mlp_forward.restype = ctypes.c_int
@@ -522,10 +527,12 @@ def eri(basis: dict, quartets, solid: bool = True, device="cuda", workspace_limi
     return out[: b.out_size], b.quartets["out_offset"].copy()
 
 
-def router_set(params_f16, tau: float):
+def router_set(params_f16, tau):
     """Install the routing network of path "routed" on the current device: params_f16 holds
-    the MLP_NPARAM FP16 parameters (any array or tensor; copied), tau the threshold on the
-    predicted log10 max |integral| at or above which a quartet takes the FP64 path."""
+    the MLP_NPARAM FP16 parameters (any array or tensor; copied); tau the thresholds of the
+    split tiers of 4, 5 and 6 digits on the network's output 1 (predicted log10 split error):
+    a quartet takes the first tier whose threshold lies above its prediction, else the FP64
+    path (a tier is disabled by -1e30)."""
     try:
         import torch
         if isinstance(params_f16, torch.Tensor):
@@ -535,11 +542,15 @@ def router_set(params_f16, tau: float):
     p = np.ascontiguousarray(np.asarray(params_f16, dtype=np.float16))
     if p.size != MLP_NPARAM:
         raise ValueError(f"expected {MLP_NPARAM} parameters, got {p.size}")
-    _check(load().lx_router_set(_ptr(p), ctypes.c_float(float(tau))), "lx_router_set")
+    t = np.ascontiguousarray(np.asarray(tau, dtype=np.float32).reshape(-1))
+    if t.size != len(ROUTE_TIERS):
+        raise ValueError(f"expected {len(ROUTE_TIERS)} thresholds, got {t.size}")
+    _check(load().lx_router_set(_ptr(p), _ptr(t)), "lx_router_set")
 
 
-def split_gemm(A, B, stream=None):
-    """C = A @ B.T for float64 CUDA matrices through the split path's tensor-core kernels."""
+def split_gemm(A, B, stream=None, digits: int = 6):
+    """C = A @ B.T for float64 CUDA matrices through the split path's tensor-core kernels,
+    keeping `digits` (4..6) BF16 digits per value."""
     import torch
     A = A.contiguous()
     B = B.contiguous()
@@ -547,7 +558,7 @@ def split_gemm(A, B, stream=None):
     N = B.shape[0]
     C = torch.empty((M, N), dtype=torch.float64, device=A.device)
     _check(load().lx_split_gemm(M, N, K, ctypes.c_void_p(A.data_ptr()), K, ctypes.c_void_p(B.data_ptr()), K,
-                                ctypes.c_void_p(C.data_ptr()), N, ctypes.c_void_p(_stream_ptr(stream))),
+                                ctypes.c_void_p(C.data_ptr()), N, int(digits), ctypes.c_void_p(_stream_ptr(stream))),
            "lx_split_gemm")
     return C
 
@@ -566,8 +577,9 @@ def route_features(basis: dict, quartets, device="cuda", stream=None):
 
 
 def mlp_forward(params_f16, feat, stream=None):
+    """(n, MLP_NOUT) outputs of the network for features (n, MLP_NIN)."""
     import torch
-    out = torch.empty(feat.shape[0], dtype=torch.float32, device=feat.device)
+    out = torch.empty((feat.shape[0], MLP_NOUT), dtype=torch.float32, device=feat.device)
     _check(load().lx_mlp_forward(ctypes.c_void_p(params_f16.data_ptr()), ctypes.c_void_p(feat.data_ptr()),
                                  feat.shape[0], ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream_ptr(stream))),
            "lx_mlp_forward")
@@ -575,7 +587,8 @@ def mlp_forward(params_f16, feat, stream=None):
 
 
 def mlp_grad(params, feat, target, stream=None):
-    """(loss, grad) of the mean squared error, forward with FP16-rounded params."""
+    """(loss, grad) of the mean over samples of the summed squared errors of the outputs
+    (target: (n, MLP_NOUT)), forward with FP16-rounded params."""
     import torch
     grad = torch.empty(MLP_NPARAM, dtype=torch.float32, device=params.device)
     loss = torch.empty(1, dtype=torch.float32, device=params.device)

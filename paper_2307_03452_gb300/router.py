@@ -1,11 +1,13 @@
-"""Learned routing between the FP64 path and the split path.
+"""Learned routing between the FP64 path and the split path's digit tiers.
 
-A 3-layer MLP (20 -> 64 -> 64 -> 1, FP16 weights) predicts log10 of each quartet's largest
-|integral| from cheap shell descriptors (lx_route_features).  The split path's absolute
-error grows with the magnitude of the integrals, so quartets predicted above a threshold
-tau go to the FP64 path and the rest to the split path.  Training (forward, backward,
-Adam) and inference run in the library's own kernels; this module only moves tensors.
-No part of the paper corresponds to it.
+A 3-layer MLP (20 -> 64 -> 64 -> 2, FP16 weights) predicts, from cheap shell descriptors
+(lx_route_features), log10 of each quartet's largest |integral| (output 0) and log10 of the
+split path's absolute error on it with 6 digits (output 1).  That error follows the size of
+the quartet's intermediates, which exceeds the result by orders of magnitude when the
+Hermite sums cancel, so routing uses output 1: a quartet takes the split path with the
+fewest digits (4, 5 or 6) whose threshold lies above its prediction, and the FP64 path if
+none does.  Training (forward, backward, Adam) and inference run in the library's own
+kernels; this module only moves tensors.  No part of the paper corresponds to it.
 """
 from __future__ import annotations
 
@@ -17,7 +19,7 @@ import numpy as np
 from . import lx
 
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "router_weights.json")
-FORMAT_VERSION = 1
+FORMAT_VERSION = 2
 
 
 class Router:
@@ -31,17 +33,32 @@ class Router:
         for (fan_in, n_out) in [(nin, nw), (nw, nw)]:
             p[o:o + n_out * fan_in] = rng.normal(scale=np.sqrt(2.0 / fan_in), size=n_out * fan_in)
             o += n_out * fan_in + n_out  # weights, then zero biases
-        p[o:o + nw] = rng.normal(scale=np.sqrt(1.0 / nw), size=nw)
+        p[o:o + lx.MLP_NOUT * nw] = rng.normal(scale=np.sqrt(1.0 / nw), size=lx.MLP_NOUT * nw)
         self.params = torch.tensor(p, device=device)
         self.m = torch.zeros_like(self.params)
         self.v = torch.zeros_like(self.params)
         self.p16 = self.params.half()
         self.step = 0
-        self.tau = None  # routing threshold on the predicted log10 max |integral|
+        self.tau = None  # thresholds of the 4-, 5- and 6-digit tiers on the predicted log10 split error
 
     # ---- inference
     def predict(self, feat):
+        """(n, 2): predicted log10 max |integral| and log10 split error (6 digits)."""
         return lx.mlp_forward(self.p16, feat)
+
+    def tiers(self, feat, basis=None, quartets=None, solid=True):
+        """Destination of each quartet as the library routes it: 0 = FP64 path, 4, 5, 6 = the
+        split path with that many digits (numpy int array)."""
+        err = self.predict(feat)[:, 1].cpu().numpy()
+        dest = np.zeros(len(err), dtype=np.int64)
+        undecided = np.ones(len(err), dtype=bool)
+        for d, t in zip(lx.ROUTE_TIERS, self.tau):
+            take = undecided & (err < t)
+            dest[take] = d
+            undecided &= ~take
+        if basis is not None:
+            dest[transform_flops(basis, quartets, solid) < ROUTE_SPLIT_MIN_FLOP] = 0
+        return dest
 
     # ---- training on the GPU (lx_mlp_grad + lx_mlp_adam)
     def train(self, feat, target, steps=2000, batch=4096, lr=3e-3, seed=0, log_every=0):
@@ -67,8 +84,8 @@ class Router:
 
     # ---- persistence (versioned JSON: weights, threshold, provenance)
     def save(self, path=WEIGHTS, meta=None):
-        d = {"format": FORMAT_VERSION, "nin": lx.MLP_NIN, "width": lx.MLP_WIDTH,
-             "params": self.params.cpu().numpy().astype(float).tolist(), "tau": self.tau, "meta": meta or {}}
+        d = {"format": FORMAT_VERSION, "nin": lx.MLP_NIN, "width": lx.MLP_WIDTH, "nout": lx.MLP_NOUT,
+             "params": self.params.cpu().numpy().astype(float).tolist(), "tau": list(self.tau), "meta": meta or {}}
         with open(path, "w") as f:
             json.dump(d, f)
 
@@ -77,7 +94,8 @@ class Router:
         import torch
         with open(path) as f:
             d = json.load(f)
-        if d.get("format") != FORMAT_VERSION or d["nin"] != lx.MLP_NIN or d["width"] != lx.MLP_WIDTH:
+        if (d.get("format") != FORMAT_VERSION or d["nin"] != lx.MLP_NIN or d["width"] != lx.MLP_WIDTH
+                or d.get("nout") != lx.MLP_NOUT):
             raise ValueError(f"incompatible router weights file {path}")
         r = cls(device=device)
         r.params = torch.tensor(np.asarray(d["params"], dtype=np.float32), device=device)
@@ -90,37 +108,37 @@ class Router:
 def block_log10_max(out, off, sizes, floor=1e-300):
     """log10 of the largest |integral| of each quartet block (CUDA tensors in, CUDA tensor out)."""
     import torch
-    off_t = torch.as_tensor(np.asarray(off), device=out.device)
-    sz_t = torch.as_tensor(np.asarray(sizes), device=out.device)
-    seg = torch.repeat_interleave(torch.arange(len(off_t), device=out.device), sz_t)
+    return torch.log10(block_max_abs(out, off, sizes).clamp_min(floor)).float()
+
+
+def block_max_abs(x, off, sizes):
+    """Largest |x| of each quartet block (CUDA tensors in, CUDA tensor out)."""
+    import torch
+    off_t = torch.as_tensor(np.asarray(off), device=x.device)
+    sz_t = torch.as_tensor(np.asarray(sizes), device=x.device)
+    seg = torch.repeat_interleave(torch.arange(len(off_t), device=x.device), sz_t)
     idx = torch.repeat_interleave(off_t - torch.cumsum(sz_t, 0) + sz_t, sz_t) + torch.arange(int(sz_t.sum()),
-                                                                                            device=out.device)
-    vals = out[idx].abs()
-    mx = torch.zeros(len(off_t), dtype=out.dtype, device=out.device).scatter_reduce(0, seg, vals, "amax")
-    return torch.log10(mx.clamp_min(floor)).float()
-
-
-def labels(basis, quartets, solid=True):
-    """Training targets: log10 max |integral| per quartet from the FP64 path."""
-    out, off = lx.eri(basis, quartets, solid=solid, path="fp64")
-    b = lx.Batch(basis, quartets, solid)
-    return block_log10_max(out, off, b.sizes), out, off
+                                                                                            device=x.device)
+    return torch.zeros(len(off_t), dtype=x.dtype, device=x.device).scatter_reduce(0, seg, x[idx].abs(), "amax")
 
 
 def routed_eri(basis, quartets, router: Router, solid=True, tau=None, device="cuda",
-               workspace_limit: int = 16 << 30, return_mask: bool = True):
+               workspace_limit: int = 16 << 30, return_tiers: bool = True):
     """Evaluate with per-quartet routing in one library call (path "routed", after installing
-    this network); returns (out, offsets, route mask: True = FP64) or (out, offsets) when
-    return_mask is False.  The batch is chunked to fit workspace_limit bytes of scratch (or
-    the smallest workspace that holds its largest quartet, if that is more).  The mask is
-    recomputed here from the same features and network, for reporting."""
+    this network and its thresholds); returns (out, offsets, destination per quartet: 0 =
+    FP64, else the digits of its split tier) or (out, offsets) when return_tiers is False.
+    The batch is chunked to fit workspace_limit bytes of scratch (or the smallest workspace
+    that holds its largest quartet, if that is more).  The destinations are recomputed here
+    from the same features, network and thresholds, for reporting."""
     tau = router.tau if tau is None else tau
     lx.router_set(router.p16, tau)
     out, off = lx.eri(basis, quartets, solid=solid, device=device, workspace_limit=workspace_limit, path="routed")
-    if not return_mask:
+    if not return_tiers:
         return out, off
-    to_fp64 = (router.predict(lx.route_features(basis, quartets, device=device)) >= tau).cpu().numpy()
-    return out, off, to_fp64 | (transform_flops(basis, quartets, solid) < ROUTE_SPLIT_MIN_FLOP)
+    saved, router.tau = router.tau, tau
+    dest = router.tiers(lx.route_features(basis, quartets, device=device), basis, quartets, solid)
+    router.tau = saved
+    return out, off, dest
 
 
 #: quartets whose two transforms take fewer FLOPs than this go to the FP64 path (as in the library)

@@ -26,30 +26,39 @@ def _device():
 SHAPES = [(1, 1, 1), (128, 96, 32), (129, 97, 33), (300, 200, 455), (455, 169, 455), (64, 16, 1000), (7, 250, 70)]
 
 
+@pytest.mark.parametrize("digits", [4, 5, 6])
 @pytest.mark.parametrize("M,N,K", SHAPES)
-def test_split_gemm_exact_on_integer_rows(M, N, K):
-    # rows: integers |x| < 2^12 times a per-row power of two -> the 48-bit split is exact and every
-    # partial sum stays exact, so C must equal the FP64 product exactly
+def test_split_gemm_exact_on_integer_rows(M, N, K, digits):
+    # rows: integers |x| < 2^12 times a per-row power of two -> only the top two digits of each
+    # value are nonzero, so even 4 digits (products s + t <= 3) represent every product exactly,
+    # every partial sum stays exact, and C must equal the FP64 product exactly
     rng = np.random.default_rng(M * 1000 + N + K)
     A = rng.integers(-4095, 4096, (M, K)).astype(np.float64) * np.exp2(rng.integers(-20, 20, (M, 1)))
     B = rng.integers(-4095, 4096, (N, K)).astype(np.float64) * np.exp2(rng.integers(-20, 20, (N, 1)))
     ref = A @ B.T
-    C = lx.split_gemm(torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda")).cpu().numpy()
+    C = lx.split_gemm(torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda"), digits=digits).cpu().numpy()
     assert np.array_equal(C, ref)
 
 
+@pytest.mark.parametrize("digits", [4, 5, 6])
 @pytest.mark.parametrize("M,N,K", SHAPES)
-def test_split_gemm_random_within_bound(M, N, K):
-    # 48-bit operands (x = q 2^(e-48), |x| < 2^e <= 2|x|max) and the dropped digit products
-    # (s + t >= 6) cost at most ~2.3 units of 2^(eA+eB-48) per k:
-    # |C - AB^T| <= K * 2^-43 * max_k|A_ik| * max_k|B_jk| with room to spare
+def test_split_gemm_random_within_bound(M, N, K, digits):
+    # operands of 8 d bits (x = q 2^(e-48) truncated to d digits, |x| < 2^e <= 2|x|max) and the
+    # dropped digit products (s + t >= d) cost at most a few units of 2^(eA+eB-8d) per k:
+    # |C - AB^T| <= K * 2^(5-8d) * max_k|A_ik| * max_k|B_jk| (2^-43 for d = 6) with room to spare;
+    # and one digit fewer must cost more than 2^6 of the error at the typical element
     rng = np.random.default_rng(7 + M + N + K)
     A = rng.normal(size=(M, K)) * np.exp(rng.uniform(-5, 5, (M, 1)))
     B = rng.normal(size=(N, K)) * np.exp(rng.uniform(-5, 5, (N, 1)))
     ref = A @ B.T
-    C = lx.split_gemm(torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda")).cpu().numpy()
-    bound = K * 2.0 ** -43 * np.outer(np.abs(A).max(1), np.abs(B).max(1))
+    At, Bt = torch.tensor(A, device="cuda"), torch.tensor(B, device="cuda")
+    C = lx.split_gemm(At, Bt, digits=digits).cpu().numpy()
+    scale = np.outer(np.abs(A).max(1), np.abs(B).max(1))
+    bound = K * 2.0 ** (5 - 8 * digits) * scale
     assert np.all(np.abs(C - ref) <= bound)
+    if digits > 4 and K >= 32:
+        Cf = lx.split_gemm(At, Bt, digits=digits - 1).cpu().numpy()
+        assert np.median(np.abs(Cf - ref) / scale) > 2.0 ** 6 * np.median(np.abs(C - ref) / scale)
 
 
 @pytest.mark.parametrize("K", [300, 4096, 20000])
