@@ -78,8 +78,29 @@ def nfun(l, solid):
 
 # DRAM bytes per quartet of one launch, from single ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum) of these kernels on 256 solid (ii|ii) K = 1 quartets; a launch's
-# traffic grows with its quartet count.  Valid for that workload and these kernel builds.
-NCU_BYTES_PER_QUARTET = {"gemm1": 311.383296e6 / 256, "split_gemm1": 1186.914816e6 / 256}
+# traffic grows with its quartet count.  Each figure holds for that workload and for the
+# kernel source it was captured on, named with its sha256: once that file changes, the
+# traffic is reported as unknown (null) until it is captured again.
+NCU_TRAFFIC = {
+    "gemm1": (311.383296e6 / 256, "paper_2307_03452_gb300/csrc/lx_gemm.cu",
+              "2e31e62d4b0eb5d2d87ec27d9d5e2bf675e0e8eec6d9707d1c2f2df1cb75f841"),
+    "split_gemm1": ((957.585920e6 + 146.121728e6) / 256, "paper_2307_03452_gb300/csrc/lx_split.cu",
+                    "99ebcfd71c7c0b34327aff12254e72505253eea2f7d29e1dd00672ca3d528996"),
+}
+
+
+def ncu_traffic(kernel, nquartet):
+    """DRAM bytes of one launch of `kernel` over nquartet (ii|ii) quartets, or None when its
+    source has changed since the capture."""
+    import hashlib
+    per, path, sha = NCU_TRAFFIC[kernel]
+    try:
+        with open(os.path.join(ROOT, path), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != sha:
+                return None
+    except OSError:
+        return None
+    return per * nquartet
 
 
 def gemm_flops(basis, quartets, solid):
@@ -665,7 +686,7 @@ def main(argv=None):
     lx.load(build_if_missing=True)
     basis, quartets = inputs.iiii_fp64(args.nquartet)
     nq = len(quartets)
-    default_workload = True  # solid (ii|ii) K = 1 at any count: the class NCU_BYTES_PER_QUARTET was taken on
+    default_workload = True  # solid (ii|ii) K = 1 at any count: the class NCU_TRAFFIC was taken on
 
     checks = OracleChecks()
     peak64 = fp64_peak_tflops(torch)
@@ -702,7 +723,9 @@ def main(argv=None):
                                f"({NOMINAL_FP64_TFLOPS} / {NOMINAL_BF16_TFLOPS} TFLOP/s) = {fp64_derived:.4f} "
                                f"(of {bf16_src}) and cuBLAS DGEMM 4096^3 measured in this run = {peak64:.4f}",
                 "cublas_dgemm_tflops": peak64, "dtype": "f64",
-                "traffic": (NCU_BYTES_PER_QUARTET["gemm1"] * nq if dominant == "gemm1" and default_workload else None)}
+                "traffic": (ncu_traffic("gemm1", nq) if dominant == "gemm1" and default_workload else None),
+                "traffic_source": "ncu capture on 256 quartets scaled by quartet count; null if the kernel source "
+                                  "changed since"}
     roofline["frac"] = roofline["achieved"] / fp64_peak if roofline["achieved"] else None
     roofline["frac_of_cublas_dgemm"] = roofline["achieved"] / peak64 if roofline["achieved"] else None
     roofline["frac_le_1"] = bool(roofline["frac"] is not None and roofline["frac"] <= 1.0)
@@ -726,8 +749,9 @@ def main(argv=None):
         sroof = {"bound": "tensor", "kernel": f"split_{sdom}", "unit": "TFLOP/s",
                  "achieved": (tens / (sper * 1e-3) / 1e12) if tens else None, "peak": bf16_peak,
                  "peak_source": f"MEASURED_PEAKS.json bf16_tflops (burst), of {bf16_src}",
-                 "traffic": (NCU_BYTES_PER_QUARTET["split_gemm1"] * nq
-                             if sdom == "gemm1" and default_workload else None)}
+                 "traffic": (ncu_traffic("split_gemm1", nq) if sdom == "gemm1" and default_workload else None),
+                 "traffic_source": "ncu capture on 256 quartets scaled by quartet count; null if the kernel source "
+                                   "changed since"}
         sroof["frac"] = sroof["achieved"] / bf16_peak if sroof["achieved"] and bf16_peak else None
         split = {"quartets_per_s": world * nq * args.steps / (stot * 1e-3), "ms_per_step": stot / args.steps,
                  "fp64_equiv_tflops": world * (g1 + g2) * args.steps / (stot * 1e-3) / 1e12,

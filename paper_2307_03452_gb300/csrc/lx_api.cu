@@ -467,7 +467,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             const DPair& pr = P.pairs[p];
             const int k = pr.Kab * pr.np, tb = split_tb(pr.nrow);
             // columns scaled into (-1, 1): one pass, e = 0 per row
-            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k, pr.nrow, k, tb, split_nkb(k), -1, 1, 0});
+            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k, pr.nrow, k, tb, split_nkb(k), -1, 1, 0, nd, 0});
             P.cmd.push_back(ColMaxDesc{0, 0, k, pr.nrow, k, 0});
             for (int c = 0; c < (k + 127) / 128; ++c) P.items_cA.push_back({p, c, 0, 0});
             // digit kernels: one item per 8 consecutive rows (every row tile is a multiple of 8)
@@ -479,12 +479,13 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             SplitQuartet q{};
             q.nkb1 = split_nkb(k1);
             q.nkb2 = split_nkb(k2);
+            q.nd = nd;
             const DPair &pb = P.pairs[d.pb], &pk = P.pairs[d.pk];
             q.gidx_off = gidx_offset(sh[pb.sa].l + sh[pb.sb].l, sh[pk.sa].l + sh[pk.sb].l);
             P.sq.push_back(q);
             const int tb1 = split_tb(d.nab), tb2 = split_tb(d.ncd);
             // A2: X, one exponent per row and segment (the rows up to nab rounded to 8 are used)
-            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k2, d.nab, k2, SPLIT_TA, q.nkb2, +1, 2, split_nseg(q.nkb2)});
+            P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k2, d.nab, k2, SPLIT_TA, q.nkb2, +1, 2, split_nseg(q.nkb2), nd, 0});
             for (int row = 0; row < split_rowpad(k2, 8); row += 8) P.items_sr.push_back({i, row, 0, 0});
             // X's digit planes only after GEMM1
             for (int row = 0; row < split_rowpad(d.nab, 8); row += 8) P.items_sD.push_back({npair + i, row, 0, 0});
@@ -1705,8 +1706,8 @@ int lx_split_gemm(int32_t M, int32_t N, int32_t K, const double* A, int32_t lda,
     const int tb = split_tb(N);
     const int ra = split_rowpad(M, SPLIT_TA), rb = split_rowpad(N, tb);
     std::vector<SplitRowsDesc> rd(2);
-    rd[0] = SplitRowsDesc{0, 0, 0, -1, lda, M, K, SPLIT_TA, nkb, 0, 0, 0};
-    rd[1] = SplitRowsDesc{0, 0, 0, -1, ldb, N, K, tb, nkb, 0, 0, 0};
+    rd[0] = SplitRowsDesc{0, 0, 0, -1, lda, M, K, SPLIT_TA, nkb, 0, 0, 0, digits, 0};
+    rd[1] = SplitRowsDesc{0, 0, 0, -1, ldb, N, K, tb, nkb, 0, 0, 0, digits, 0};
     std::vector<WorkItem> ia, ib, ig;
     for (int r = 0; r < ra; r += 8) ia.push_back({0, r, 0, 0});
     for (int r = 0; r < rb; r += 8) ib.push_back({1, r, 0, 0});

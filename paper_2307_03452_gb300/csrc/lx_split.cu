@@ -213,10 +213,10 @@ __device__ inline void digits_of(long long q, uint32_t (&f)[SPLIT_NSLICE]) {
 }
 
 // Digits of 8 consecutive values (k0 .. k0+7, k0 a multiple of 8) of one row, written as one
-// 16-byte store per slice (one row of a core matrix).
+// 16-byte store per slice (one row of a core matrix), for the first nd slices.
 __device__ inline int64_t dig_index(int row, int k, int s, int T, int nkb);
 __device__ inline void store_digit_group(__nv_bfloat16* dig, int row, int k0, int T, int nkb,
-                                         const long long (&q)[8]) {
+                                         const long long (&q)[8], int nd) {
     // w[s][i]: BF16 pair of slice s, element 2i in the low half and 2i + 1 in the high half
     uint32_t w[SPLIT_NSLICE][4];
 #pragma unroll
@@ -228,8 +228,10 @@ __device__ inline void store_digit_group(__nv_bfloat16* dig, int row, int k0, in
         for (int s = 0; s < SPLIT_NSLICE; ++s) w[s][j >> 1] = __byte_perm(f0[s], f1[s], 0x7632);
     }
 #pragma unroll
-    for (int s = 0; s < SPLIT_NSLICE; ++s)
-        *reinterpret_cast<uint4*>(dig + dig_index(row, k0, s, T, nkb)) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+    for (int s = 0; s < SPLIT_NSLICE; ++s)  // slices past nd are never read
+        if (s < nd)
+            *reinterpret_cast<uint4*>(dig + dig_index(row, k0, s, T, nkb)) =
+                make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
 }
 
 // Offset (in BF16 elements) of element (row, k) of slice s inside an operand stored as
@@ -259,7 +261,7 @@ __device__ inline int row_max16(int mx) {
 // they are scaled by; zeros outside the matrix): digit planes of row tile T with nkb K blocks
 // and one int exponent per row (the modes of SplitRowsDesc::fixed).
 template <bool SEGMENTS, typename Value>
-__device__ __forceinline__ void split_8rows(int r0, int nkb, int T, int fixed, int nseg,
+__device__ __forceinline__ void split_8rows(int r0, int nkb, int T, int fixed, int nseg, int nd,
                                             __nv_bfloat16* __restrict__ dig, int* __restrict__ exps, Value value) {
     const int lane = threadIdx.x & 31, c8 = 8 * (lane & 15);
     static_assert(SPLIT_SEG_KB * SPLIT_KB == 128, "one pass of a row pair covers one segment");
@@ -283,7 +285,7 @@ __device__ __forceinline__ void split_8rows(int r0, int nkb, int T, int fixed, i
                     long long q[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) q[i] = mx > 0 ? fixed_of(v[i], sh[i], e) : 0ll;
-                    store_digit_group(dig, row, k0, T, nkb, q);
+                    store_digit_group(dig, row, k0, T, nkb, q, nd);
                 }
                 if ((lane & 15) == 0) exps[(int64_t)row * nseg + sg] = e;
             }
@@ -308,7 +310,7 @@ __device__ __forceinline__ void split_8rows(int r0, int nkb, int T, int fixed, i
             long long q[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) q[i] = mx > 0 ? fixed_of(v[i], sh[i], e) : 0ll;
-            store_digit_group(dig, row, k0, T, nkb, q);
+            store_digit_group(dig, row, k0, T, nkb, q, nd);
         }
         if ((lane & 15) == 0) exps[row] = e;
     }
@@ -322,7 +324,7 @@ __device__ __forceinline__ void split_rows_item(const SplitRowsDesc* __restrict_
     const SplitRowsDesc d = descs[it.q];
     const double* src = src_base + d.src_off;
     const int* shift = d.shift_off >= 0 ? reinterpret_cast<const int*>(ws + d.shift_off) : nullptr;
-    split_8rows<SEGMENTS>(it.a, d.nkb, d.T, d.fixed, d.nseg, reinterpret_cast<__nv_bfloat16*>(ws + d.dig_off),
+    split_8rows<SEGMENTS>(it.a, d.nkb, d.T, d.fixed, d.nseg, d.nd, reinterpret_cast<__nv_bfloat16*>(ws + d.dig_off),
                 reinterpret_cast<int*>(ws + d.exp_off), [&](int row, int k0, double (&v)[8], int (&sh)[8]) {
                     const bool live = row < d.rows;
                     const double* sr = src + (int64_t)row * d.ld;
@@ -422,7 +424,7 @@ __device__ __forceinline__ void split_r_item(const DQuartet* __restrict__ qd, co
         long long qv[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) qv[i] = mx > 0 ? fixed_of(v[i], sh[i], e) : 0ll;
-        store_digit_group(dig, row, SPLIT_KB * kb + c8, SPLIT_TA, s.nkb1, qv);
+        store_digit_group(dig, row, SPLIT_KB * kb + c8, SPLIT_TA, s.nkb1, qv, s.nd);
     }
     if ((lane & 3) == 0) reinterpret_cast<int*>(ws + s.a1_exp)[row] = e;
 }

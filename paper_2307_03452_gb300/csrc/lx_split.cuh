@@ -34,6 +34,7 @@ struct SplitRowsDesc {
     int64_t exp_off;    // bytes from the workspace base (int per padded row, times nseg if fixed = 2)
     int64_t shift_off;  // bytes from the workspace base (int per column), or -1
     int ld, rows, K, T, nkb, shift_sign, fixed, nseg;
+    int nd, pad;  // digit slices written (the first nd of the block's NSLICE)
 };
 __host__ __device__ inline int split_nseg(int nkb) { return (nkb + SPLIT_SEG_KB - 1) / SPLIT_SEG_KB; }
 
@@ -56,6 +57,7 @@ struct SplitQuartet {
     int64_t c1_off, c2_off;  // int[Kbra Np], int[Kket Nq]
     int64_t gidx_off;        // this class's block of the [p+q] index table (gidx_offset)
     int nkb1, nkb2;
+    int nd, pad;  // digit slices written (the first nd of the block's NSLICE)
 };
 
 // Index table of the [p|q] gathers: for l_bra, l_ket <= 2 LMAX, entry gidx_offset(l_bra,
