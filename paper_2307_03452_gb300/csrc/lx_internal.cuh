@@ -130,22 +130,41 @@ constexpr int GEMM_BK = 16;
 //   W[a u v t]        = sum_bx E^x_{ax bx t} Q[ay az bx u v]
 //   H[m_a m_b][t u v] = sum_a C_a[m_a][a] W[a t u v]
 // Only entries that can be nonzero (t <= ax + bx, u <= ay + by, v <= az + bz, nonzero C) are
-// kept.  Each stage's rows are sorted by length and stored in groups of 32 (one per warp):
-// entry j of row 32 g + i is ent[gptr[g] + 32 j + i], for j < (gptr[g+1] - gptr[g]) / 32, and
-// short rows are padded with null entries that multiply by an explicit zero.
+// kept.  Each stage's rows are sorted by length and taken in groups of 32 (lane i of a warp
+// owns row 32 g + i); every row of a group is padded to the group's longest row with null
+// entries that multiply by an explicit zero, and a group of empty rows gets one null entry.
+// Warp w takes groups fold_group(k, w) for k = 0, 1, ...: round k of FOLD_NWARP groups is
+// dealt to the warps in order for even k and in reverse for odd k, which evens out the warps'
+// work on groups sorted by length.  Each warp reads one stream: its groups in order, column j of a group (entry j
+// of its 32 rows) after column j - 1.  Every entry of a group's last column carries
+// FOLD_FLAG (end of those rows: store them and move to the warp's next group), and every
+// entry of a column with no real entry carries FOLD_SKIP (nothing to add).  Columns are stored
+// four at a time, lane-major: entry j of lane i's current row at stream + 128 (j / 4) + 4 i +
+// j % 4, so one 16-byte load per lane fetches four; a stream is padded to whole quads with
+// skipped null columns.  Warp w's stream of a stage is ent[ws[w] .. ws[w + 1]) (ws = wstart +
+// the stage's offset, FOLD_NWARP + 1 bounds).
 //   Q entry: coefficient index (m_b ncart(lb) + b) | E^y index << 10 | E^z index << 20
 //   W entry: E^x index | Q row << 10
-//   H entry: coefficient index (m_a ncart(la) + a) | W row << 10; h_out[row] = m_a | p << 4
-// E^d index = (i (lb+1) + j) (la+lb+1) + t for exponents (i, j) on a and b.  Short rows are
-// padded with entries that multiply by a zero: coefficient index (2lb+1) ncart(lb) in a Q
-// row, (2la+1) ncart(la) in an H row (one past each shell's coefficients), Q row maxq of the
-// (la, lb) (the row after its largest Q stage) in a W row.
+//   H entry: coefficient index (m_a ncart(la) + a) | W row << 10;
+//   h_out[row] = m_a | p << 4 | (t + u + v odd) << 30, with p = hidx(t, u, v)
+// E^d index = (i (lb+1) + j) (la+lb+1) + t for exponents (i, j) on a and b.  Null entries
+// multiply by a zero: coefficient index (2lb+1) ncart(lb) in a Q row, (2la+1) ncart(la) in
+// an H row (one past each shell's coefficients), Q row maxq of the (la, lb) (the row after
+// its largest Q stage) in a W row.
+constexpr int FOLD_NWARP = 16;              // warps of the fold kernel (one stream each)
+constexpr int FOLD_FLAG = INT32_MIN;          // bit 31: the last column of a group
+constexpr int FOLD_SKIP = 1 << 30;            // bit 30: a column of null entries only
+constexpr int FOLD_MASK = FOLD_SKIP - 1;      // the entry itself
+// Group of round k of warp w.
+__host__ __device__ inline int fold_group(int k, int w) {
+    return k * FOLD_NWARP + ((k & 1) ? FOLD_NWARP - 1 - w : w);
+}
 constexpr int FOLD_QMAX = 8191;   // bound on the Q rows of one m_b (5688 at la = lb = 7)
 constexpr int FOLD_WMAX = 16383;  // bound on the W rows of one m_b (13542 at la = lb = 7)
 constexpr int FOLD_CMAX = NSOL_MAX * NCART_MAX;  // coefficients of one shell (540 at l = 7)
 static_assert(FOLD_CMAX < 1024 && (LMAX + 1) * (LMAX + 1) * (2 * LMAX + 1) <= 1024, "fold entry fields of 10 bits");
 struct FoldSeg {
-    int q_grp0, q_nrow, w_grp0, w_nrow, h_grp0, h_row0;  // first group of each stage; h_out offset
+    int q_ws, q_nrow, w_ws, w_nrow, h_ws, h_row0;  // each stage's offset in wstart; h_out offset
 };
 struct FoldPairTab {
     int seg0;  // segments seg0 .. seg0 + 2 lb (one per m_b)
@@ -179,7 +198,7 @@ void make_tuv_table(int* tuv);              // NHERM_TOT entries: t | u << 8 | v
 #include <vector>
 namespace lx {
 struct FoldHost {
-    std::vector<int> q_gptr, q_ent, w_gptr, w_ent, h_gptr, h_ent, h_out;
+    std::vector<int> q_ent, w_ent, h_ent, h_out, wstart;
     std::vector<FoldSeg> segs;
     FoldPairTab pair[LMAX + 1][LMAX + 1];
 };

@@ -16,8 +16,6 @@ constexpr int SPLIT_TA = 128;                        // A row tile = MMA M
 constexpr int SPLIT_TB = 32;                         // largest B row tile (2 sets x 6 diagonals x 32 TMEM columns)
 constexpr int SPLIT_SEG_KB = 4;                      // K blocks accumulated in TMEM between int64 drains
 
-// One matrix whose rows are split: src at (double*)base + src_off, row stride ld.  Before
-// splitting, column k is multiplied by 2^(shift_sign * shift[k]) (exact; shift_off < 0: none).
 // Exponent of an all-zero row segment (below any real exponent; its digits are zero).
 constexpr int SPLIT_EXP_NONE = -(1 << 29);
 

@@ -14,6 +14,7 @@
 // for the top order, summed in long double, and the downward recursion
 // F_n = (2T F_{n+1} + exp(-T)) / (2n+1).
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <map>
 #include <tuple>
@@ -142,35 +143,53 @@ void make_boys_table(double* table) {
 
 namespace {
 
-// Sort rows by decreasing length (stable) and append them in groups of 32; returns the
-// position of each original row.
-std::vector<int> emit_groups(const std::vector<std::vector<int>>& rows, int null_entry, std::vector<int>& gptr,
+// Sort rows by decreasing length (stable), take them in groups of 32 and append one stream
+// per warp (the layout described with FoldSeg) to ent, and the FOLD_NWARP + 1 stream bounds
+// to wstart; returns the position of each original row.
+std::vector<int> emit_groups(const std::vector<std::vector<int>>& rows, int null_entry, std::vector<int>& wstart,
                              std::vector<int>& ent) {
-    const int n = (int)rows.size();
+    const int n = (int)rows.size(), ngroup = (n + 31) / 32;
     std::vector<int> order(n), pos(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return rows[a].size() > rows[b].size(); });
     for (int i = 0; i < n; ++i) pos[order[i]] = i;
-    for (int g = 0; g < (n + 31) / 32; ++g) {
-        size_t len = 0;
-        for (int i = 32 * g; i < std::min(n, 32 * g + 32); ++i) len = std::max(len, rows[order[i]].size());
-        for (size_t j = 0; j < len; ++j)
-            for (int i = 32 * g; i < 32 * g + 32; ++i)
-                ent.push_back(i < n && j < rows[order[i]].size() ? rows[order[i]][j] : null_entry);
-        gptr.push_back((int)ent.size());
+    for (int w = 0; w < FOLD_NWARP; ++w) {
+        wstart.push_back((int)ent.size());
+        std::vector<std::array<int, 32>> cols;  // the warp's columns in stream order
+        for (int k = 0, g; (g = fold_group(k, w)) < ngroup; ++k) {
+            size_t len = 1;  // a group of empty rows still ends with one (null) column
+            for (int i = 32 * g; i < std::min(n, 32 * g + 32); ++i) len = std::max(len, rows[order[i]].size());
+            for (size_t j = 0; j < len; ++j) {
+                std::array<int, 32> c;
+                bool any = false;
+                for (int i = 0; i < 32; ++i) {
+                    const int r = 32 * g + i;
+                    const bool real = r < n && j < rows[order[r]].size();
+                    c[i] = real ? rows[order[r]][j] : null_entry;
+                    any = any || real;
+                }
+                for (int i = 0; i < 32; ++i) c[i] |= (any ? 0 : FOLD_SKIP) | (j + 1 == len ? FOLD_FLAG : 0);
+                cols.push_back(c);
+            }
+        }
+        std::array<int, 32> pad;
+        pad.fill(null_entry | FOLD_SKIP);
+        while (cols.size() % 4) cols.push_back(pad);
+        for (size_t q = 0; q < cols.size(); q += 4)
+            for (int i = 0; i < 32; ++i)
+                for (int k = 0; k < 4; ++k) ent.push_back(cols[q + k][i]);
     }
+    wstart.push_back((int)ent.size());
     return pos;
 }
 
 }  // namespace
 
-constexpr int W_PLACEHOLDER = -1;  // never a real W entry (those are non-negative)
+constexpr int W_PLACEHOLDER = FOLD_MASK;  // never a real W entry
 
 bool make_fold_lists(const double* coefs, FoldHost& F) {
-    F.q_gptr.assign(1, 0);
-    F.w_gptr.assign(1, 0);
-    F.h_gptr.assign(1, 0);
+    F.wstart.clear();
     F.q_ent.clear();
     F.w_ent.clear();
     F.h_ent.clear();
@@ -190,6 +209,9 @@ bool make_fold_lists(const double* coefs, FoldHost& F) {
                 }
             for (int i = 0, k = 0; i <= lb; ++i)
                 for (int j = 0; j <= i; ++j, ++k) bidx[(lb - i) * (lb + 1) + (i - j)] = k;  // (bx, by) -> b
+            std::vector<int> lsum(np);  // t + u + v of Hermite index p
+            for (int L = 0; L <= la + lb; ++L)
+                for (int p = L ? pyr(L - 1) : 0; p < pyr(L); ++p) lsum[p] = L;
             const double* Ca = coefs + solid_offset(la);
             const double* Cb = coefs + solid_offset(lb);
             // distinct (ay, az) of shell a, in component order
@@ -203,9 +225,6 @@ bool make_fold_lists(const double* coefs, FoldHost& F) {
             const size_t w_first = F.w_ent.size();
             for (int mb = 0; mb < nsb; ++mb) {
                 FoldSeg sg{};
-                sg.q_grp0 = (int)F.q_gptr.size() - 1;
-                sg.w_grp0 = (int)F.w_gptr.size() - 1;
-                sg.h_grp0 = (int)F.h_gptr.size() - 1;
                 sg.h_row0 = (int)F.h_out.size();
                 // Q rows, keyed (ay, az, bx, u, v)
                 std::vector<std::tuple<int, int, int, int, int>> qkey;
@@ -228,7 +247,8 @@ bool make_fold_lists(const double* coefs, FoldHost& F) {
                 sg.q_nrow = (int)qkey.size();
                 if (sg.q_nrow > FOLD_QMAX) return false;
                 // padding entries take the zero stored after C_b (coefficient index nsb ncb)
-                const std::vector<int> qpos = emit_groups(qrows, nsb * ncb, F.q_gptr, F.q_ent);
+                sg.q_ws = (int)F.wstart.size();
+                const std::vector<int> qpos = emit_groups(qrows, nsb * ncb, F.wstart, F.q_ent);
                 // W rows, keyed (a, p)
                 std::vector<std::vector<int>> wrows;
                 std::vector<int> wrow((size_t)nca * np, -1);
@@ -249,7 +269,8 @@ bool make_fold_lists(const double* coefs, FoldHost& F) {
                 sg.w_nrow = (int)wrows.size();
                 if (sg.w_nrow > FOLD_WMAX) return false;
                 // padding entries point at the zero Q row, known once every m_b is built
-                const std::vector<int> wpos = emit_groups(wrows, W_PLACEHOLDER, F.w_gptr, F.w_ent);
+                sg.w_ws = (int)F.wstart.size();
+                const std::vector<int> wpos = emit_groups(wrows, W_PLACEHOLDER, F.wstart, F.w_ent);
                 // H rows (m_a, p); the output position travels with the row
                 std::vector<std::vector<int>> hrows;
                 std::vector<int> hkey;
@@ -262,10 +283,11 @@ bool make_fold_lists(const double* coefs, FoldHost& F) {
                             row.push_back((ma * nca + a) | (wpos[w] << 10));
                         }
                         hrows.push_back(std::move(row));
-                        hkey.push_back(ma | (p << 4));
+                        hkey.push_back(ma | (p << 4) | ((lsum[p] & 1) << 30));
                     }
                 // padding entries take the zero stored after C_a (coefficient index nsa nca)
-                const std::vector<int> hpos = emit_groups(hrows, nsa * nca, F.h_gptr, F.h_ent);
+                sg.h_ws = (int)F.wstart.size();
+                const std::vector<int> hpos = emit_groups(hrows, nsa * nca, F.wstart, F.h_ent);
                 std::vector<int> out(hrows.size());
                 for (size_t i = 0; i < hrows.size(); ++i) out[hpos[i]] = hkey[i];
                 F.h_out.insert(F.h_out.end(), out.begin(), out.end());
@@ -273,8 +295,8 @@ bool make_fold_lists(const double* coefs, FoldHost& F) {
                 tab.maxw = std::max(tab.maxw, sg.w_nrow);
                 F.segs.push_back(sg);
             }
-            for (size_t i = w_first; i < F.w_ent.size(); ++i)
-                if (F.w_ent[i] == W_PLACEHOLDER) F.w_ent[i] = tab.maxq << 10;  // E^x[0] times the zero row
+            for (size_t i = w_first; i < F.w_ent.size(); ++i)  // E^x[0] times the zero row, flags kept
+                if ((F.w_ent[i] & FOLD_MASK) == W_PLACEHOLDER) F.w_ent[i] = (F.w_ent[i] & ~FOLD_MASK) | (tab.maxq << 10);
         }
     return ok;
 }
