@@ -243,9 +243,9 @@ size_t pair_bytes(const lx_shell* sh, int sa, int sb, int flags) {
     if (split) {
         // H's digit planes (rows padded to at most SPLIT_TB), row exponents, column scales
         const int rp = split_rowpad((int)rows, SPLIT_TB);
-        bytes += sizeof(SplitRowsDesc) + sizeof(ColMaxDesc) + (size_t)split_dig_bytes((int)rows, (int)k, SPLIT_TB);
+        bytes += sizeof(SplitRowsDesc) + (size_t)split_dig_bytes((int)rows, (int)k, SPLIT_TB);
         bytes += 4 * (size_t)(rp + k) + 3 * 256;
-        bytes += sizeof(WorkItem) * (size_t)(rp / 8 + (k + 127) / 128);
+        bytes += sizeof(WorkItem) * (size_t)(rp / 8);
     }
     return bytes;
 }
@@ -304,15 +304,14 @@ struct ChunkPlan {
     size_t off_pairs = 0, off_quartets = 0, off_h = 0, off_br = 0, off_g1 = 0, off_g2 = 0, off_data = 0;
     int g1_counts[GEMM_NVARIANT] = {0, 0, 0, 0}, g2_counts[GEMM_NVARIANT] = {0, 0, 0, 0};
     size_t off_counters = 0;  // 2 x GEMM_NVARIANT work counters, uploaded as zeros with the blob
-    // split path: one split-row and one column-scale desc per pair (H), one split-row desc per
-    // quartet (X)
+    // split path: one split-row desc per pair (H) and per quartet (X); the column scales of H
+    // come from the pair kernels
     std::vector<SplitRowsDesc> srd;
-    std::vector<ColMaxDesc> cmd;
     std::vector<SplitQuartet> sq;
     std::vector<SplitGemmDesc> sg1, sg2;
-    std::vector<WorkItem> items_cA, items_sr, items_sB, items_sg1, items_sD, items_sg2;
-    size_t off_srd = 0, off_cmd = 0, off_sq = 0, off_sg1 = 0, off_sg2 = 0;
-    size_t off_icA = 0, off_isr = 0, off_isB = 0, off_isg1 = 0, off_isD = 0, off_isg2 = 0;
+    std::vector<WorkItem> items_sr, items_sB, items_sg1, items_sD, items_sg2;
+    size_t off_srd = 0, off_sq = 0, off_sg1 = 0, off_sg2 = 0;
+    size_t off_isr = 0, off_isB = 0, off_isg1 = 0, off_isD = 0, off_isg2 = 0;
     size_t total = 0;         // bytes from the chunk base
     std::vector<char> blob;   // descriptor bytes [0, off_data)
 };
@@ -333,11 +332,10 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     P.items_g1.clear();
     P.items_g2.clear();
     P.srd.clear();
-    P.cmd.clear();
     P.sq.clear();
     P.sg1.clear();
     P.sg2.clear();
-    for (auto* v : {&P.items_cA, &P.items_sr, &P.items_sB, &P.items_sg1, &P.items_sD, &P.items_sg2})
+    for (auto* v : {&P.items_sr, &P.items_sB, &P.items_sg1, &P.items_sD, &P.items_sg2})
         v->clear();
     std::unordered_map<PairKey, int, PairKeyHash> pid;
     auto get_pair = [&](int sa, int sb, int side) {
@@ -345,6 +343,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
         auto f = pid.find(k);
         if (f != pid.end()) return f->second;
         DPair p{};
+        p.cs_off = -1;  // set with the data layout on the split path
         p.sa = sa;
         p.sb = sb;
         p.Kab = sh[sa].nprim * sh[sb].nprim;
@@ -468,8 +467,6 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             const int k = pr.Kab * pr.np, tb = split_tb(pr.nrow);
             // columns scaled into (-1, 1): one pass, e = 0 per row
             P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k, pr.nrow, k, tb, split_nkb(k), -1, 1, 0, nd, 0});
-            P.cmd.push_back(ColMaxDesc{0, 0, k, pr.nrow, k, 0});
-            for (int c = 0; c < (k + 127) / 128; ++c) P.items_cA.push_back({p, c, 0, 0});
             // digit kernels: one item per 8 consecutive rows (every row tile is a multiple of 8)
             for (int row = 0; row < split_rowpad(pr.nrow, tb); row += 8) P.items_sB.push_back({p, row, 0, 0});
         }
@@ -516,11 +513,9 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     region(P.off_g2, sizeof(WorkItem) * P.items_g2.size());
     region(P.off_counters, sizeof(int) * 2 * GEMM_NVARIANT);
     region(P.off_srd, sizeof(SplitRowsDesc) * P.srd.size());
-    region(P.off_cmd, sizeof(ColMaxDesc) * P.cmd.size());
     region(P.off_sq, sizeof(SplitQuartet) * P.sq.size());
     region(P.off_sg1, sizeof(SplitGemmDesc) * P.sq.size());
     region(P.off_sg2, sizeof(SplitGemmDesc) * P.sq.size());
-    region(P.off_icA, sizeof(WorkItem) * P.items_cA.size());
     region(P.off_isr, sizeof(WorkItem) * P.items_sr.size());
     region(P.off_isB, sizeof(WorkItem) * P.items_sB.size());
     region(P.off_isg1, sizeof(WorkItem) * P.items_sg1.size());
@@ -553,8 +548,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             r.dig_off = take_bytes(split_dig_bytes(pr.nrow, k, tb));
             r.exp_off = take_bytes(4 * (int64_t)split_rowpad(pr.nrow, tb));
             r.shift_off = take_bytes(4 * (int64_t)k);
-            P.cmd[p].src_off = pr.h_off;
-            P.cmd[p].out_off = r.shift_off;
+            P.pairs[p].cs_off = r.shift_off;  // written by the pair's H kernel
         }
         for (size_t i = 0; i < P.quartets.size(); ++i) {
             const DQuartet& d = P.quartets[i];
@@ -620,11 +614,9 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     put(P.off_g1, P.items_g1.data(), sizeof(WorkItem) * P.items_g1.size());
     put(P.off_g2, P.items_g2.data(), sizeof(WorkItem) * P.items_g2.size());
     put(P.off_srd, P.srd.data(), sizeof(SplitRowsDesc) * P.srd.size());
-    put(P.off_cmd, P.cmd.data(), sizeof(ColMaxDesc) * P.cmd.size());
     put(P.off_sq, P.sq.data(), sizeof(SplitQuartet) * P.sq.size());
     put(P.off_sg1, P.sg1.data(), sizeof(SplitGemmDesc) * P.sg1.size());
     put(P.off_sg2, P.sg2.data(), sizeof(SplitGemmDesc) * P.sg2.size());
-    put(P.off_icA, P.items_cA.data(), sizeof(WorkItem) * P.items_cA.size());
     put(P.off_isr, P.items_sr.data(), sizeof(WorkItem) * P.items_sr.size());
     put(P.off_isB, P.items_sB.data(), sizeof(WorkItem) * P.items_sB.size());
     put(P.off_isg1, P.items_sg1.data(), sizeof(WorkItem) * P.items_sg1.size());
@@ -755,7 +747,7 @@ int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector
         const WorkItem* d_ig1 = reinterpret_cast<const WorkItem*>(base + P.off_g1);
         const WorkItem* d_ig2 = reinterpret_cast<const WorkItem*>(base + P.off_g2);
         if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
-        if ((e = launch_pair_h(d_pairs, d_ih, (int)P.items_h.size(), d_sh, d_exps, d_ncoef, ws, ws, solid,
+        if ((e = launch_pair_h(d_pairs, d_ih, (int)P.items_h.size(), d_sh, d_exps, d_ncoef, ws, ws, solid, split,
                                P.fold_lcap, P.fold_qcap, P.fold_wcap, status, st)) != cudaSuccess)
             return cuda_fail(e);
         if ((e = tm.end(LX_STAGE_PAIR, 1)) != cudaSuccess) return cuda_fail(e);
@@ -767,19 +759,17 @@ int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector
         if (split) {
             auto at = [&](size_t off) { return base + off; };
             const SplitRowsDesc* d_srd = reinterpret_cast<const SplitRowsDesc*>(at(P.off_srd));
-            const ColMaxDesc* d_cmd = reinterpret_cast<const ColMaxDesc*>(at(P.off_cmd));
             const SplitQuartet* d_sq = reinterpret_cast<const SplitQuartet*>(at(P.off_sq));
             const SplitGemmDesc* d_sg1 = reinterpret_cast<const SplitGemmDesc*>(at(P.off_sg1));
             const SplitGemmDesc* d_sg2 = reinterpret_cast<const SplitGemmDesc*>(at(P.off_sg2));
             auto items = [&](size_t off) { return reinterpret_cast<const WorkItem*>(at(off)); };
-            // operands of GEMM1: column scales of H_bra and H_ket, then digit planes of [p|q]^T
-            // and H_bra
+            // operands of GEMM1 and the H operand of GEMM2: digit planes of [p|q]^T and of each
+            // pair's H (H's column scales were written by the pair kernels)
             if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
-            if ((e = launch_colmax(d_cmd, items(P.off_icA), (int)P.items_cA.size(), ws, wsb, st)) != cudaSuccess ||
-                (e = launch_split_operands(d_q, d_sq, items(P.off_isr), (int)P.items_sr.size(), d_srd,
+            if ((e = launch_split_operands(d_q, d_sq, items(P.off_isr), (int)P.items_sr.size(), d_srd,
                                            items(P.off_isB), (int)P.items_sB.size(), ws, wsb, st)) != cudaSuccess)
                 return cuda_fail(e);
-            if ((e = tm.end(LX_STAGE_SPLIT, 2)) != cudaSuccess) return cuda_fail(e);
+            if ((e = tm.end(LX_STAGE_SPLIT, 1)) != cudaSuccess) return cuda_fail(e);
             if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
             if ((e = launch_split_gemm(d_sg1, items(P.off_isg1), (int)P.items_sg1.size(), wsb, ws, status, st,
                                        false, P.digits)) != cudaSuccess)
@@ -1642,6 +1632,7 @@ int lx_hermite_H(const lx_shell* shells, int32_t nshell, const double* exps, con
         p.np = pyr(shells[sa].l + shells[sb].l);
         p.sign = side;
         p.solid = solid ? 1 : 0;
+        p.cs_off = -1;
         p.info_off = info_total;
         info_total += 4 * (int64_t)p.Kab;
         for (int kp = 0; kp < p.Kab; ++kp) items.push_back({k, kp, 0, 0});
@@ -1686,7 +1677,8 @@ int lx_hermite_H(const lx_shell* shells, int32_t nshell, const double* exps, con
         }
     if ((e = launch_pair_h(reinterpret_cast<const DPair*>(scratch + o_pairs),
                            reinterpret_cast<const WorkItem*>(scratch + o_items), (int)items.size(), d_sh, d_exps,
-                           d_ncoef, H, reinterpret_cast<double*>(scratch + o_info), solid, lcap, qcap, wcap, status, st)) !=
+                           d_ncoef, H, reinterpret_cast<double*>(scratch + o_info), solid, false, lcap, qcap, wcap, status,
+                           st)) !=
         cudaSuccess)
         return cuda_fail(e);
     if ((e = cudaFreeAsync(scratch, st)) != cudaSuccess) return cuda_fail(e);

@@ -12,6 +12,7 @@ constexpr int LTOT = 4 * LMAX;                      // largest total L of a quar
 constexpr int NCART_MAX = (LMAX + 1) * (LMAX + 2) / 2;  // 36
 constexpr int NSOL_MAX = 2 * LMAX + 1;              // 15
 constexpr int NHERM_TOT = (LTOT + 1) * (LTOT + 2) * (LTOT + 3) / 6;  // pyr(28) = 4495
+constexpr int NHERM_PAIR = (2 * LMAX + 1) * (2 * LMAX + 2) * (2 * LMAX + 3) / 6;  // pyr(14) = 680: Hermite indices of one pair
 
 // Boys table: F_n(T_k), n = 0..BOYS_NROW-1, T_k = k * BOYS_DT for k = 0..BOYS_NPT-1.
 // Taylor expansion of order BOYS_ORDER-1 around the nearest grid point covers T < BOYS_TMAX.
@@ -51,6 +52,10 @@ struct DPair {  // one shell pair on one side of the quartet
     int pad;
     int64_t h_off;     // H block (doubles): [nrow][Kab*np]
     int64_t info_off;  // pair scalars (doubles): [Kab][4] = zeta_p, P
+    // split path: column scales of H, int[Kab*np] at this many bytes from the workspace base
+    // (c_k with |H[.][k]| < 2^c_k over the column, 0 for a zero column), written by the pair's
+    // H kernel; -1: none
+    int64_t cs_off;
 };
 
 struct DQuartet {
@@ -80,8 +85,8 @@ cudaError_t launch_norm(const DShell* sh, int nshell, const double* exps, const 
 // H blocks at ws + h_off, pair scalars at ws_info + info_off.
 cudaError_t launch_pair_h(const DPair* pairs, const WorkItem* items, int nitems, const DShell* sh,
                           const double* exps, const double* ncoef, double* ws, double* ws_info, bool solid,
-                          int fold_lcap, int fold_qcap, int fold_wcap, unsigned* status,
-                          cudaStream_t st);  // solid fold: largest l of the pairs, Q and W rows
+                          bool scales, int fold_lcap, int fold_qcap, int fold_wcap, unsigned* status,
+                          cudaStream_t st);  // scales: pairs carry cs_off; solid fold: largest l, Q and W rows
 // J/K digestion of the blocks at ws + out_off, one CTA per quartet (lx_jk.cu).  J or K may
 // be null.
 cudaError_t launch_jk_digest(const DQuartet* qd, const DPair* pairs, const DShell* sh, int nquartet,

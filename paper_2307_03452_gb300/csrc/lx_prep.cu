@@ -76,9 +76,11 @@ __host__ __device__ constexpr int etab_of(int l) { return (l + 1) * (l + 1) * (2
 __host__ __device__ constexpr int ncoef_of(int l) { return (2 * l + 1) * (l + 1) * (l + 2) / 2; }
 constexpr int ETAB = etab_of(LMAX);  // 960 per direction
 // shared memory of pair_h_solid_kernel for pairs with la, lb <= lcap and fold capacities qcap
-// (Q rows incl. the zero row) and wcap: E[3][etab], C_a and C_b (each with a trailing zero), Q, W
+// (Q rows incl. the zero row) and wcap: E[3][etab], C_a and C_b (each with a trailing zero), Q, W,
+// then one int per Hermite index of the pair (column exponents)
 inline size_t fold_smem_bytes(int lcap, int qcap, int wcap) {
-    return sizeof(double) * (size_t)(3 * etab_of(lcap) + 2 * (ncoef_of(lcap) + 1) + qcap + wcap);
+    return sizeof(double) * (size_t)(3 * etab_of(lcap) + 2 * (ncoef_of(lcap) + 1) + qcap + wcap) +
+           sizeof(int) * (size_t)pyr(2 * lcap);
 }
 
 // Hermite expansion coefficients of primitive pair kp into E[3][etab] (zero beyond t <= i+j),
@@ -148,8 +150,17 @@ __device__ __forceinline__ void pair_setup(const DPair& pr, int kp, const DShell
     __syncthreads();
 }
 
+// Largest exponent field of the values stored in each column (shared-memory maxima), turned
+// into the column scales c_k (|x| < 2^c_k over the column, 0 for a zero column) of the split
+// path.
+__device__ inline int exp_field_of(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF); }
+__device__ inline void write_col_scales(const int* cexp, int np, int* out) {
+    for (int p = threadIdx.x; p < np; p += blockDim.x) out[p] = cexp[p] > 0 ? cexp[p] - 1022 : 0;
+}
+
 // One CTA per primitive pair (item.q = pair id, item.a = primitive pair kp), Cartesian rows.
-// Writes pair scalars (zeta_p, P) and the H block columns of this primitive pair.
+// Writes pair scalars (zeta_p, P) and the H block columns of this primitive pair (and, on the
+// split path, their column scales).
 __global__ void __launch_bounds__(PAIR_THREADS) pair_h_kernel(const DPair* __restrict__ pairs,
                                                                const WorkItem* __restrict__ items,
                                                                const DShell* __restrict__ sh,
@@ -159,10 +170,13 @@ __global__ void __launch_bounds__(PAIR_THREADS) pair_h_kernel(const DPair* __res
                                                                unsigned* status) {
     __shared__ double E[3][ETAB];
     __shared__ double s_pref;
+    __shared__ int cexp[NHERM_PAIR];
     const WorkItem it = items[blockIdx.x];
     const DPair pr = pairs[it.q];
     const int la = sh[pr.sa].l, lb = sh[pr.sb].l, nt = la + lb + 1;
     const int kp = it.a;
+    const bool scales = pr.cs_off >= 0;
+    for (int p = threadIdx.x; p < pr.np; p += blockDim.x) cexp[p] = 0;  // ordered by pair_setup's barriers
     pair_setup(pr, kp, sh, exps, ncoef, ws_info, &E[0][0], ETAB, &s_pref);
 
     const int np = pr.np;
@@ -187,7 +201,13 @@ __global__ void __launch_bounds__(PAIR_THREADS) pair_h_kernel(const DPair* __res
         const int px = tuv & 255, py = (tuv >> 8) & 255, pz = tuv >> 16;
         double v = Ex[(ax * sb1 + bx) * nt + px] * Ey[(ay * sb1 + by) * nt + py] * Ez[(az * sb1 + bz) * nt + pz];
         if (pr.sign && ((px + py + pz) & 1)) v = -v;
-        H[(int64_t)ab * ldh + p] = pref * v;
+        const double h = pref * v;
+        H[(int64_t)ab * ldh + p] = h;
+        if (scales) atomicMax(&cexp[p], exp_field_of(h));
+    }
+    if (scales) {
+        __syncthreads();
+        write_col_scales(cexp, np, reinterpret_cast<int*>(reinterpret_cast<char*>(ws) + pr.cs_off) + (int64_t)kp * np);
     }
 }
 
@@ -238,21 +258,27 @@ __device__ __forceinline__ void fold_stage(int ws, int nrow, const int* __restri
 // by the factorised fold (one Cartesian index at a time, structural zeros skipped; the row
 // groups are built on the host).  Per m_b: the Q stage, a barrier, the W stage, a barrier,
 // then the H stage of m_b together with the Q stage of m_b + 1 (which touch disjoint
-// arrays), a barrier.
+// arrays), a barrier.  On the split path the H stage also keeps each column's largest
+// exponent, and the column scales are written at the end.
+template <bool SCALES>  // the split path: pairs carry column scales (cs_off >= 0)
 __global__ void __launch_bounds__(PAIR_SOLID_THREADS, 2) pair_h_solid_kernel(
     const DPair* __restrict__ pairs, const WorkItem* __restrict__ items, const DShell* __restrict__ sh,
     const double* __restrict__ exps, const double* __restrict__ ncoef, double* __restrict__ ws,
-    double* __restrict__ ws_info, int lcap, int qcap, unsigned* status) {
+    double* __restrict__ ws_info, int lcap, int qcap, int wcap, unsigned* status) {
     extern __shared__ double fold_smem[];
     const int etab = etab_of(lcap), ccap = ncoef_of(lcap) + 1;
     double* E = fold_smem;        // 3 etab
     double* Csa = E + 3 * etab;   // ccap: C_a, then a zero at ncoef(la)
     double* Csb = Csa + ccap;     // ccap: C_b, then a zero at ncoef(lb)
     double* Q = Csb + ccap;       // qcap (>= maxq + 1 of this pair's tables); Q[maxq] zero
-    double* W = Q + qcap;
+    double* W = Q + qcap;         // wcap
+    int* cexp = reinterpret_cast<int*>(W + wcap);  // pyr(2 lcap): largest exponent field per column
     __shared__ double s_pref;
     const WorkItem it = items[blockIdx.x];
     const DPair pr = pairs[it.q];
+    const bool scales = SCALES && pr.cs_off >= 0;
+    if (SCALES)
+        for (int p = threadIdx.x; p < pr.np; p += blockDim.x) cexp[p] = 0;  // ordered by pair_setup's barriers
     const int la = sh[pr.sa].l, lb = sh[pr.sb].l;
     const int kp = it.a;
     const int nca = ncart(la), ncb = ncart(lb), nsb = 2 * lb + 1;
@@ -297,6 +323,7 @@ __global__ void __launch_bounds__(PAIR_SOLID_THREADS, 2) pair_h_solid_kernel(
                    [=](int, int o, double v) {
                        const int ma = o & 15, p = (o >> 4) & 0xffff;
                        const bool neg = sign && ((o >> 30) & 1);
+                       if (scales) atomicMax(&cexp[p], exp_field_of(v));
                        // the sign as a bit flip, off the FP64 pipe
                        H[(int64_t)(ma * nsb + mb) * ldh + p] =
                            __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
@@ -304,6 +331,8 @@ __global__ void __launch_bounds__(PAIR_SOLID_THREADS, 2) pair_h_solid_kernel(
         if (mb + 1 < nsb) fold_stage(sg[1].q_ws, sg[1].q_nrow, c_fold.q_ent, q_term, no_pre, q_store);
         __syncthreads();
     }
+    if (scales)
+        write_col_scales(cexp, np, reinterpret_cast<int*>(reinterpret_cast<char*>(ws) + pr.cs_off) + (int64_t)kp * np);
 }
 
 }  // namespace
@@ -345,9 +374,10 @@ cudaError_t init_prep_tables(const double* host_coefs, const int* host_tuv, cons
             qmax = std::max(qmax, F.pair[a][b].maxq + 1);
             wmax = std::max(wmax, F.pair[a][b].maxw);
         }
-    if ((e = cudaFuncSetAttribute(pair_h_solid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)fold_smem_bytes(LMAX, qmax, wmax))) != cudaSuccess)
-        return e;
+    for (const void* k : {(const void*)pair_h_solid_kernel<false>, (const void*)pair_h_solid_kernel<true>})
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)fold_smem_bytes(LMAX, qmax, wmax))) != cudaSuccess)
+            return e;
     return cudaMemcpyToSymbol(g_tuv_prep, host_tuv, sizeof(int) * NHERM_TOT);
 }
 
@@ -359,13 +389,18 @@ cudaError_t launch_norm(const DShell* sh, int nshell, const double* exps, const 
 }
 
 cudaError_t launch_pair_h(const DPair* pairs, const WorkItem* items, int nitems, const DShell* sh,
-                          const double* exps, const double* ncoef, double* ws, double* ws_info, bool solid,
+                          const double* exps, const double* ncoef, double* ws, double* ws_info, bool solid, bool scales,
                           int fold_lcap, int fold_qcap, int fold_wcap, unsigned* status, cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
     if (solid) {
         if (fold_lcap < 0 || fold_lcap > LMAX) return cudaErrorInvalidValue;
-        pair_h_solid_kernel<<<nitems, PAIR_SOLID_THREADS, fold_smem_bytes(fold_lcap, fold_qcap, fold_wcap), st>>>(
-            pairs, items, sh, exps, ncoef, ws, ws_info, fold_lcap, fold_qcap, status);
+        const size_t smem = fold_smem_bytes(fold_lcap, fold_qcap, fold_wcap);
+        if (scales)
+            pair_h_solid_kernel<true><<<nitems, PAIR_SOLID_THREADS, smem, st>>>(
+                pairs, items, sh, exps, ncoef, ws, ws_info, fold_lcap, fold_qcap, fold_wcap, status);
+        else
+            pair_h_solid_kernel<false><<<nitems, PAIR_SOLID_THREADS, smem, st>>>(
+                pairs, items, sh, exps, ncoef, ws, ws_info, fold_lcap, fold_qcap, fold_wcap, status);
     } else
         pair_h_kernel<<<nitems, PAIR_THREADS, 0, st>>>(pairs, items, sh, exps, ncoef, ws, ws_info, status);
     return cudaGetLastError();

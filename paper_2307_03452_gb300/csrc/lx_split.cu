@@ -17,7 +17,6 @@
 //   split_operands_kernel  rows q of the [p|q] operand gathered from [r]^(0), and the H
 //                      rows, -> digit planes + row exponents (GEMM1 operands, H_ket)
 //   split_rows_kernel  FP64 row-major matrix rows ([ab|q]) -> digit planes + row exponents
-//   colmax_kernel      column scales of the H matrices (powers of two along K)
 //   split_gemm_kernel  D = A B^T on tcgen05 (M tile 128, N tile <= 32, K blocks of 32),
 //                      persistent, operand blocks streamed by bulk TMA copies into a
 //                      3-stage mbarrier ring, one thread issuing the MMAs, two TMEM
@@ -456,20 +455,6 @@ __global__ void __launch_bounds__(256) split_operands_kernel(const DQuartet* __r
     }
 }
 
-// One thread per column k: c_k with |x| < 2^c_k over the column (from the largest exponent
-// field; 0 for a column of zeros).  item = (desc, chunk of 128 columns).
-__global__ void colmax_kernel(const ColMaxDesc* __restrict__ descs, const WorkItem* __restrict__ items,
-                              const double* __restrict__ src_base, char* __restrict__ ws) {
-    const WorkItem it = items[blockIdx.x];
-    const ColMaxDesc d = descs[it.q];
-    const int k = it.a * 128 + threadIdx.x;
-    if (k >= d.K) return;
-    const double* src = src_base + d.src_off + k;
-    int mx = 0;
-    for (int r = 0; r < d.rows; ++r) mx = max(mx, exp_field(src[(int64_t)r * d.ld]));
-    reinterpret_cast<int*>(ws + d.out_off)[k] = mx > 0 ? mx - 1022 : 0;
-}
-
 // ------------------------------------------------------------------ tcgen05 GEMM
 
 constexpr int STAGES = 3;
@@ -784,13 +769,6 @@ cudaError_t launch_split_operands(const DQuartet* qd, const SplitQuartet* sq, co
     const int nb = (n_r + 7) / 8 + (n_w + 7) / 8;
     if (nb <= 0) return cudaSuccess;
     split_operands_kernel<<<nb, 256, 0, st>>>(qd, sq, items_r, n_r, descs, items_w, n_w, wsd, ws);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_colmax(const ColMaxDesc* descs, const WorkItem* items, int nitems, const double* src_base,
-                          char* ws, cudaStream_t st) {
-    if (nitems <= 0) return cudaSuccess;
-    colmax_kernel<<<nitems, 128, 0, st>>>(descs, items, src_base, ws);
     return cudaGetLastError();
 }
 

@@ -36,14 +36,6 @@ struct SplitRowsDesc {
 };
 __host__ __device__ inline int split_nseg(int nkb) { return (nkb + SPLIT_SEG_KB - 1) / SPLIT_SEG_KB; }
 
-// out[k] = c_k with |x| < 2^c_k over column k of a row-major matrix (0 for a zero column):
-// the column scale of an H matrix.
-struct ColMaxDesc {
-    int64_t src_off;  // doubles
-    int64_t out_off;  // bytes (int per column)
-    int ld, rows, K, pad;
-};
-
 // Per-quartet split operands of the two GEMMs.  Column k of H_bra is scaled by 2^-c1[k] into
 // (-1, 1) and column k of [p|q]^T by 2^c1[k] (the product is unchanged); likewise H_ket and
 // [ab|q] with c2.  Every operand carries one exponent per row.
@@ -111,9 +103,6 @@ cudaError_t launch_split_rows(const SplitRowsDesc* descs, const WorkItem* items,
 cudaError_t launch_split_operands(const DQuartet* qd, const SplitQuartet* sq, const WorkItem* items_r, int n_r,
                                   const SplitRowsDesc* descs, const WorkItem* items_w, int n_w, const double* wsd,
                                   char* ws, cudaStream_t st);
-// item = (desc, chunk of 128 columns)
-cudaError_t launch_colmax(const ColMaxDesc* descs, const WorkItem* items, int nitems, const double* src_base,
-                          char* ws, cudaStream_t st);
 // The bounded-wait timeout path on purpose (a wait of `limit` tries, <= the kernels' own
 // limit, on an mbarrier nothing arrives on): sets the status word's timeout bit.
 cudaError_t launch_wait_selftest(unsigned* status, unsigned long long limit, cudaStream_t st);
