@@ -80,10 +80,10 @@ def calibrate(pred_err, errs, margin):
 def main(argv=None):
     import torch
     ap = argparse.ArgumentParser(description=__doc__)
-    ap.add_argument("--train", type=int, default=48000, help="training quartets like the routed workload")
+    ap.add_argument("--train", type=int, default=200000, help="training quartets like the routed workload")
     ap.add_argument("--mixed", type=int, default=0, help="training quartets like the mixed-class workload")
-    ap.add_argument("--val", type=int, default=4000, help="validation quartets of each kind")
-    ap.add_argument("--steps", type=int, default=8000)
+    ap.add_argument("--val", type=int, default=16000, help="validation quartets of each kind")
+    ap.add_argument("--steps", type=int, default=24000)
     ap.add_argument("--err-floor", type=float, default=-17.0, help="log10 floor of the error target")
     ap.add_argument("--oversample", type=int, default=8,
                     help="copies in the training set of quartets whose 4-digit error passes 1/20 of the target")
