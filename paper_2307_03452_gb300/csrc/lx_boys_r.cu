@@ -12,6 +12,8 @@
 // In the batch kernel each CTA is that one warp, with shared memory for the chunk's
 // largest L, so that as many quartets as shared memory allows run side by side.
 #include <cmath>
+#include <cstring>
+#include <vector>
 
 #include "lx_internal.cuh"
 
@@ -20,9 +22,13 @@ namespace lx {
 namespace {
 
 __device__ double g_boys[BOYS_NROW * BOYS_NPT];
-// Within-total position s -> (i, v) with s = i(i+1)/2 + v, packed i | v << 8, s < (LTOT+1)(LTOT+2)/2.
-constexpr int NPOS = (LTOT + 1) * (LTOT + 2) / 2;
-__device__ int g_pos[NPOS];
+// One step of Eq. md1 for every Hermite position h = hidx(t, u, v) with t + u + v >= 1,
+// lowering the first nonzero direction d of (t, u, v):
+//   [r]^(m) = X_d [r - 1_d]^(m+1) + (r_d - 1) [r - 2_d]^(m+1)
+// x = hidx(r - 1_d) | hidx(r - 2_d) << 13 | d << 26 (the second position 0 when r_d = 1),
+// (z, w) = the FP64 bits of r_d - 1 (low, high word), so that the step is one multiply and one
+// FMA with no branch and no integer conversion.
+__device__ int4 g_rec[NHERM_TOT];
 
 constexpr double PI = 3.141592653589793238462643383279502884;
 
@@ -67,13 +73,6 @@ __device__ inline void scale_base(int L, double rho, double pref, double* B, int
     }
 }
 
-// Within-total position s (0 <= s < (n+1)(n+2)/2) -> (i, v) with s = i(i+1)/2 + v.
-__device__ inline void split_pos(int s, int& i, int& v) {
-    const int w = __ldg(&g_pos[s]);
-    i = w & 255;
-    v = w >> 8;
-}
-
 // In-place Eq. md1 on R[pyr(L)] (shared memory), by one warp.  B[m] = [0]^(m), m = 0..L.
 // On return R holds [r]^(0).
 __device__ void hermite_r_warp(int L, double X, double Y, double Z, const double* B, double* R, int lane) {
@@ -84,23 +83,10 @@ __device__ void hermite_r_warp(int L, double X, double Y, double Z, const double
             const int base = n * (n + 1) * (n + 2) / 6;  // pyr(n-1)
             const int cnt = (n + 1) * (n + 2) / 2;
             for (int s = lane; s < cnt; s += 32) {
-                int i, v;
-                split_pos(s, i, v);
-                const int u = i - v, t = n - i;
-                double val;
-                // [r + 1_d]^(m) = r_d [r - 1_d]^(m+1) + X_d [r]^(m+1), lowering the first
-                // nonzero direction of the target triplet
-                if (t > 0) {
-                    val = X * R[hidx(t - 1, u, v)];
-                    if (t > 1) val += (t - 1) * R[hidx(t - 2, u, v)];
-                } else if (u > 0) {
-                    val = Y * R[hidx(0, u - 1, v)];
-                    if (u > 1) val += (u - 1) * R[hidx(0, u - 2, v)];
-                } else {
-                    val = Z * R[hidx(0, 0, v - 1)];
-                    if (v > 1) val += (v - 1) * R[hidx(0, 0, v - 2)];
-                }
-                R[base + s] = val;
+                const int4 e = __ldg(&g_rec[base + s]);
+                const int d = e.x >> 26;
+                const double xd = d == 0 ? X : (d == 1 ? Y : Z);
+                R[base + s] = fma(__hiloint2double(e.w, e.z), R[(e.x >> 13) & 0x1FFF], xd * R[e.x & 0x1FFF]);
             }
             __syncwarp();
         }
@@ -183,10 +169,22 @@ size_t br_smem(int L) { return sizeof(double) * BR_WARPS * (size_t)(pyr(L) + LTO
 cudaError_t init_boys_table(const double* host_table) {
     cudaError_t e = cudaMemcpyToSymbol(g_boys, host_table, sizeof(double) * BOYS_NROW * BOYS_NPT);
     if (e != cudaSuccess) return e;
-    int pos[NPOS];
-    for (int i = 0, s = 0; s < NPOS; ++i)
-        for (int v = 0; v <= i && s < NPOS; ++v, ++s) pos[s] = i | (v << 8);
-    if ((e = cudaMemcpyToSymbol(g_pos, pos, sizeof(pos))) != cudaSuccess) return e;
+    static_assert(NHERM_TOT <= 8192, "Hermite positions fit 13 bits");
+    std::vector<int4> rec(NHERM_TOT, make_int4(0, 0, 0, 0));
+    for (int n = 1; n <= LTOT; ++n)
+        for (int i = 0; i <= n; ++i)
+            for (int v = 0; v <= i; ++v) {
+                const int u = i - v, t = n - i;
+                const int d = t > 0 ? 0 : (u > 0 ? 1 : 2), rd = d == 0 ? t : (d == 1 ? u : v);
+                const int dt = d == 0, du = d == 1, dv = d == 2;
+                const int h1 = hidx(t - dt, u - du, v - dv);
+                const int h2 = rd > 1 ? hidx(t - 2 * dt, u - 2 * du, v - 2 * dv) : 0;
+                const double c = rd - 1;
+                long long bits;
+                std::memcpy(&bits, &c, sizeof(bits));
+                rec[hidx(t, u, v)] = make_int4(h1 | (h2 << 13) | (d << 26), 0, (int)(bits & 0xFFFFFFFFll), (int)(bits >> 32));
+            }
+    if ((e = cudaMemcpyToSymbol(g_rec, rec.data(), sizeof(int4) * NHERM_TOT)) != cudaSuccess) return e;
     e = cudaFuncSetAttribute(boys_r_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(double) * (pyr(LTOT) + LTOT + 1)));
     if (e != cudaSuccess) return e;
