@@ -467,8 +467,10 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             const int k = pr.Kab * pr.np, tb = split_tb(pr.nrow);
             // columns scaled into (-1, 1): one pass, e = 0 per row
             P.srd.push_back(SplitRowsDesc{0, 0, 0, 0, k, pr.nrow, k, tb, split_nkb(k), -1, 1, 0, nd, 0});
-            // digit kernels: one item per 8 consecutive rows (every row tile is a multiple of 8)
-            for (int row = 0; row < split_rowpad(pr.nrow, tb); row += 8) P.items_sB.push_back({p, row, 0, 0});
+            // digit kernels: one item per 8 consecutive rows, up to nrow rounded to 8 (the GEMMs
+            // drop the output columns of B rows past nrow, so the rest of the last row tile is
+            // never written)
+            for (int row = 0; row < split_rowpad(pr.nrow, 8); row += 8) P.items_sB.push_back({p, row, 0, 0});
         }
         for (int i = 0; i < (int)P.quartets.size(); ++i) {
             const DQuartet& d = P.quartets[i];

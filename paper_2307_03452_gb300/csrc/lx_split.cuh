@@ -71,8 +71,10 @@ static_assert(NHERM_TOT < 65536, "[r]^(0) positions fit 16 bits");
 // with nkb K blocks; D written to (double*)C + c_off with row stride ldc (transpose: D[m][n] ->
 // C[n][m]).  B carries one exponent per row; A one per row (a_nseg = 1) or one per row and
 // segment of SPLIT_SEG_KB K blocks (a_nseg = split_nseg(nkb), int[row][a_nseg]).  The A operand
-// is read only up to M rows rounded to 8 (the last row tile is loaded that far).  Only the
-// first nd (4..6) digit slices of each operand are used: the products with s + t < nd.
+// is read only up to M rows rounded to 8 (the last row tile is loaded that far).  B rows past
+// N (in its last row tile) may hold anything: they reach only output columns >= N, which are
+// dropped.  Only the first nd (4..6) digit slices of each operand are used: the products with
+// s + t < nd.
 struct SplitGemmDesc {
     int64_t a_dig, a_exp, b_dig, b_exp;
     int64_t c_off;
