@@ -298,7 +298,7 @@ struct ChunkPlan {
     std::vector<WorkItem> items_h, items_br, items_g1, items_g2;
     int br_lmax = 0;  // largest L of the chunk's quartets
     int digits = 6;   // split path: BF16 digits kept per value (one count per batch)
-    int fold_lcap = 0, fold_qcap = 0, fold_wcap = 0;  // solid fold: largest l, Q and W rows of the chunk's pairs
+    int fold_lcap = 0, fold_qcap = 0, fold_wcap = 0, fold_gcap = 0;  // solid fold: largest l, Q, W and G of the chunk's pairs
     int jkd_qc = 0;          // J/K on the FP64 path: chunk width of jk_direct_kernel
     size_t jkd_smem = 0;     // and its shared memory
     size_t off_pairs = 0, off_quartets = 0, off_h = 0, off_br = 0, off_g1 = 0, off_g2 = 0, off_data = 0;
@@ -326,7 +326,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
     P.items_h.clear();
     P.items_br.clear();
     P.br_lmax = 0;
-    P.fold_lcap = P.fold_qcap = P.fold_wcap = 0;
+    P.fold_lcap = P.fold_qcap = P.fold_wcap = P.fold_gcap = 0;
     P.jkd_qc = 0;
     P.jkd_smem = 0;
     P.items_g1.clear();
@@ -382,6 +382,7 @@ void build_chunk(const lx_shell* sh, const lx_quartet* qs, const Chunk& ch, int 
             P.fold_lcap = std::max(P.fold_lcap, std::max(sh[pr.sa].l, sh[pr.sb].l));
             P.fold_qcap = std::max(P.fold_qcap, t.maxq + 1);
             P.fold_wcap = std::max(P.fold_wcap, t.maxw);
+            P.fold_gcap = std::max(P.fold_gcap, t.maxg + 1);
         }
     std::vector<int64_t> cost1, cost2;
     {
@@ -750,7 +751,7 @@ int enqueue_batch(const PlannedBatch& B, const char* head_src, const std::vector
         const WorkItem* d_ig2 = reinterpret_cast<const WorkItem*>(base + P.off_g2);
         if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
         if ((e = launch_pair_h(d_pairs, d_ih, (int)P.items_h.size(), d_sh, d_exps, d_ncoef, ws, ws, solid, split,
-                               P.fold_lcap, P.fold_qcap, P.fold_wcap, status, st)) != cudaSuccess)
+                               P.fold_lcap, P.fold_qcap, P.fold_wcap, P.fold_gcap, status, st)) != cudaSuccess)
             return cuda_fail(e);
         if ((e = tm.end(LX_STAGE_PAIR, 1)) != cudaSuccess) return cuda_fail(e);
         if ((e = tm.begin()) != cudaSuccess) return cuda_fail(e);
@@ -1669,17 +1670,18 @@ int lx_hermite_H(const lx_shell* shells, int32_t nshell, const double* exps, con
     const double* d_coefs = reinterpret_cast<const double*>(scratch + o_coefs);
     double* d_ncoef = reinterpret_cast<double*>(scratch + o_ncoef);
     if ((e = launch_norm(d_sh, nshell, d_exps, d_coefs, d_ncoef, status, st)) != cudaSuccess) return cuda_fail(e);
-    int lcap = 0, qcap = 0, wcap = 0;
+    int lcap = 0, qcap = 0, wcap = 0, gcap = 0;
     if (solid)
         for (const DPair& pr : dp) {
             const FoldPairTab& t = g_fold.pair[shells[pr.sa].l][shells[pr.sb].l];
             lcap = std::max(lcap, std::max(shells[pr.sa].l, shells[pr.sb].l));
             qcap = std::max(qcap, t.maxq + 1);
             wcap = std::max(wcap, t.maxw);
+            gcap = std::max(gcap, t.maxg + 1);
         }
     if ((e = launch_pair_h(reinterpret_cast<const DPair*>(scratch + o_pairs),
                            reinterpret_cast<const WorkItem*>(scratch + o_items), (int)items.size(), d_sh, d_exps,
-                           d_ncoef, H, reinterpret_cast<double*>(scratch + o_info), solid, false, lcap, qcap, wcap, status,
+                           d_ncoef, H, reinterpret_cast<double*>(scratch + o_info), solid, false, lcap, qcap, wcap, gcap, status,
                            st)) !=
         cudaSuccess)
         return cuda_fail(e);

@@ -85,8 +85,9 @@ cudaError_t launch_norm(const DShell* sh, int nshell, const double* exps, const 
 // H blocks at ws + h_off, pair scalars at ws_info + info_off.
 cudaError_t launch_pair_h(const DPair* pairs, const WorkItem* items, int nitems, const DShell* sh,
                           const double* exps, const double* ncoef, double* ws, double* ws_info, bool solid,
-                          bool scales, int fold_lcap, int fold_qcap, int fold_wcap, unsigned* status,
-                          cudaStream_t st);  // scales: pairs carry cs_off; solid fold: largest l, Q and W rows
+                          bool scales, int fold_lcap, int fold_qcap, int fold_wcap, int fold_gcap,
+                          unsigned* status, cudaStream_t st);  // scales: pairs carry cs_off; solid fold:
+                                                               // largest l, Q, W and G capacities
 // J/K digestion of the blocks at ws + out_off, one CTA per quartet (lx_jk.cu).  J or K may
 // be null.
 cudaError_t launch_jk_digest(const DQuartet* qd, const DPair* pairs, const DShell* sh, int nquartet,
@@ -131,7 +132,8 @@ constexpr int GEMM_BK = 16;
 // shell is block diagonal over the (at most 4) parity classes of its Cartesian components.
 
 // Factorised solid fold of one primitive pair (la, lb), per solid function m_b of b:
-//   Q[ay az bx u v]   = sum_by C_b[m_b][bx by bz] E^y_{ay by u} E^z_{az bz v}   (bz = lb - bx - by)
+//   G[b az v]         = C_b[m_b][bx by bz] E^z_{az bz v}                          (nonzero C_b only)
+//   Q[ay az bx u v]   = sum_by G[b az v] E^y_{ay by u}                             (bz = lb - bx - by)
 //   W[a u v t]        = sum_bx E^x_{ax bx t} Q[ay az bx u v]
 //   H[m_a m_b][t u v] = sum_a C_a[m_a][a] W[a t u v]
 // Only entries that can be nonzero (t <= ax + bx, u <= ay + by, v <= az + bz, nonzero C) are
@@ -148,14 +150,15 @@ constexpr int GEMM_BK = 16;
 // j % 4, so one 16-byte load per lane fetches four; a stream is padded to whole quads with
 // skipped null columns.  Warp w's stream of a stage is ent[ws[w] .. ws[w + 1]) (ws = wstart +
 // the stage's offset, FOLD_NWARP + 1 bounds).
-//   Q entry: coefficient index (m_b ncart(lb) + b) | E^y index << 10 | E^z index << 20
+//   G recipe (g_rec[g_off + g]): coefficient index (m_b ncart(lb) + b) | E^z index << 10
+//   Q entry: G index | E^y index << 10
 //   W entry: E^x index | Q row << 10
 //   H entry: coefficient index (m_a ncart(la) + a) | W row << 10;
 //   h_out[row] = m_a | p << 4 | (t + u + v odd) << 30, with p = hidx(t, u, v)
 // E^d index = (i (lb+1) + j) (la+lb+1) + t for exponents (i, j) on a and b.  Null entries
-// multiply by a zero: coefficient index (2lb+1) ncart(lb) in a Q row, (2la+1) ncart(la) in
-// an H row (one past each shell's coefficients), Q row maxq of the (la, lb) (the row after
-// its largest Q stage) in a W row.
+// multiply by a zero: G index g_n in a Q row (the zero after the m_b's G entries), coefficient
+// index (2la+1) ncart(la) in an H row (one past the shell's coefficients), Q row maxq of the
+// (la, lb) (the row after its largest Q stage) in a W row.
 constexpr int FOLD_NWARP = 16;              // warps of the fold kernel (one stream each)
 constexpr int FOLD_FLAG = INT32_MIN;          // bit 31: the last column of a group
 constexpr int FOLD_SKIP = 1 << 30;            // bit 30: a column of null entries only
@@ -166,14 +169,17 @@ __host__ __device__ inline int fold_group(int k, int w) {
 }
 constexpr int FOLD_QMAX = 8191;   // bound on the Q rows of one m_b (5688 at la = lb = 7)
 constexpr int FOLD_WMAX = 16383;  // bound on the W rows of one m_b (13542 at la = lb = 7)
+constexpr int FOLD_GMAX = 1023;   // bound on the G entries of one m_b (600 at la = lb = 7)
 constexpr int FOLD_CMAX = NSOL_MAX * NCART_MAX;  // coefficients of one shell (540 at l = 7)
 static_assert(FOLD_CMAX < 1024 && (LMAX + 1) * (LMAX + 1) * (2 * LMAX + 1) <= 1024, "fold entry fields of 10 bits");
 struct FoldSeg {
     int q_ws, q_nrow, w_ws, w_nrow, h_ws, h_row0;  // each stage's offset in wstart; h_out offset
+    int g_off, g_n;                                 // the m_b's G recipes in g_rec
 };
 struct FoldPairTab {
     int seg0;  // segments seg0 .. seg0 + 2 lb (one per m_b)
     int maxq, maxw;  // largest Q and W row counts over the m_b (Q row maxq is the zero row)
+    int maxg;        // largest G count over the m_b
 };
 constexpr int NSOLID_PACKED = [] {
     int n = 0;
@@ -203,7 +209,7 @@ void make_tuv_table(int* tuv);              // NHERM_TOT entries: t | u << 8 | v
 #include <vector>
 namespace lx {
 struct FoldHost {
-    std::vector<int> q_ent, w_ent, h_ent, h_out, wstart;
+    std::vector<int> q_ent, w_ent, h_ent, h_out, wstart, g_rec;
     std::vector<FoldSeg> segs;
     FoldPairTab pair[LMAX + 1][LMAX + 1];
 };

@@ -15,7 +15,7 @@ __constant__ int c_solid_off[LMAX + 2];
 __device__ int g_tuv_prep[NHERM_TOT];
 
 struct FoldDev {
-    const int *q_ent, *w_ent, *h_ent, *h_out, *wstart;
+    const int *q_ent, *w_ent, *h_ent, *h_out, *wstart, *g_rec;
     const FoldSeg* segs;
     FoldPairTab pair[LMAX + 1][LMAX + 1];
 };
@@ -76,10 +76,11 @@ __host__ __device__ constexpr int etab_of(int l) { return (l + 1) * (l + 1) * (2
 __host__ __device__ constexpr int ncoef_of(int l) { return (2 * l + 1) * (l + 1) * (l + 2) / 2; }
 constexpr int ETAB = etab_of(LMAX);  // 960 per direction
 // shared memory of pair_h_solid_kernel for pairs with la, lb <= lcap and fold capacities qcap
-// (Q rows incl. the zero row) and wcap: E[3][etab], C_a and C_b (each with a trailing zero), Q, W,
-// then one int per Hermite index of the pair (column exponents)
-inline size_t fold_smem_bytes(int lcap, int qcap, int wcap) {
-    return sizeof(double) * (size_t)(3 * etab_of(lcap) + 2 * (ncoef_of(lcap) + 1) + qcap + wcap) +
+// (Q rows incl. the zero row), wcap and gcap (G entries incl. the zero): E[3][etab], C_a and
+// C_b (each with a trailing zero), Q, W, G, then one int per Hermite index of the pair (column
+// exponents)
+inline size_t fold_smem_bytes(int lcap, int qcap, int wcap, int gcap) {
+    return sizeof(double) * (size_t)(3 * etab_of(lcap) + 2 * (ncoef_of(lcap) + 1) + qcap + wcap + gcap) +
            sizeof(int) * (size_t)pyr(2 * lcap);
 }
 
@@ -264,7 +265,7 @@ template <bool SCALES>  // the split path: pairs carry column scales (cs_off >= 
 __global__ void __launch_bounds__(PAIR_SOLID_THREADS, 2) pair_h_solid_kernel(
     const DPair* __restrict__ pairs, const WorkItem* __restrict__ items, const DShell* __restrict__ sh,
     const double* __restrict__ exps, const double* __restrict__ ncoef, double* __restrict__ ws,
-    double* __restrict__ ws_info, int lcap, int qcap, int wcap, unsigned* status) {
+    double* __restrict__ ws_info, int lcap, int qcap, int wcap, int gcap, unsigned* status) {
     extern __shared__ double fold_smem[];
     const int etab = etab_of(lcap), ccap = ncoef_of(lcap) + 1;
     double* E = fold_smem;        // 3 etab
@@ -272,7 +273,8 @@ __global__ void __launch_bounds__(PAIR_SOLID_THREADS, 2) pair_h_solid_kernel(
     double* Csb = Csa + ccap;     // ccap: C_b, then a zero at ncoef(lb)
     double* Q = Csb + ccap;       // qcap (>= maxq + 1 of this pair's tables); Q[maxq] zero
     double* W = Q + qcap;         // wcap
-    int* cexp = reinterpret_cast<int*>(W + wcap);  // pyr(2 lcap): largest exponent field per column
+    double* G = W + wcap;         // gcap (>= maxg + 1): the m_b's C_b E^z products, then a zero
+    int* cexp = reinterpret_cast<int*>(G + gcap);  // pyr(2 lcap): largest exponent field per column
     __shared__ double s_pref;
     const WorkItem it = items[blockIdx.x];
     const DPair pr = pairs[it.q];
@@ -307,15 +309,27 @@ __global__ void __launch_bounds__(PAIR_SOLID_THREADS, 2) pair_h_solid_kernel(
     const int hrows = (2 * la + 1) * np;
     const bool sign = pr.sign;
 
-    auto q_term = [=](int x) { return Csb[x & 1023] * Ey[(x >> 10) & 1023] * Ez[x >> 20]; };
+    // G of one m_b: C_b[m_b][b] E^z_{az bz v} once per (b, az, v), so that a Q entry is one FMA
+    auto g_build = [=](const FoldSeg* sg) {
+        const int* rec = c_fold.g_rec + sg->g_off;
+        for (int g = threadIdx.x; g < sg->g_n; g += blockDim.x) {
+            const int r = __ldg(&rec[g]);
+            G[g] = Csb[r & 1023] * Ez[r >> 10];
+        }
+        if (threadIdx.x == 0) G[sg->g_n] = 0.0;
+    };
+    auto q_term = [=](int x) { return G[x & 1023] * Ey[x >> 10]; };
     auto no_pre = [](int) { return 0; };
     auto q_store = [=](int r, int, double v) { Q[r] = v; };
+    g_build(segs);
+    __syncthreads();
     fold_stage(segs[0].q_ws, segs[0].q_nrow, c_fold.q_ent, q_term, no_pre, q_store);
     __syncthreads();
     for (int mb = 0; mb < nsb; ++mb) {
         const FoldSeg* sg = segs + mb;
         fold_stage(sg->w_ws, sg->w_nrow, c_fold.w_ent, [=](int x) { return Ex[x & 1023] * Q[x >> 10]; }, no_pre,
                    [=](int r, int, double v) { W[r] = v; });
+        if (mb + 1 < nsb) g_build(sg + 1);  // G of m_b is done with: the next Q stage follows the barrier
         __syncthreads();
         const int h_row0 = sg->h_row0;
         fold_stage(sg->h_ws, hrows, c_fold.h_ent, [=](int x) { return Csa[x & 1023] * W[x >> 10]; },
@@ -349,9 +363,9 @@ cudaError_t init_prep_tables(const double* host_coefs, const int* host_tuv, cons
     // fold lists: device copies held for the life of the process (one set per device)
     const FoldHost& F = *static_cast<const FoldHost*>(host_fold);
     FoldDev d{};
-    const std::vector<int>* src[5] = {&F.q_ent, &F.w_ent, &F.h_ent, &F.h_out, &F.wstart};
-    const int** dst[5] = {&d.q_ent, &d.w_ent, &d.h_ent, &d.h_out, &d.wstart};
-    for (int k = 0; k < 5; ++k) {
+    const std::vector<int>* src[6] = {&F.q_ent, &F.w_ent, &F.h_ent, &F.h_out, &F.wstart, &F.g_rec};
+    const int** dst[6] = {&d.q_ent, &d.w_ent, &d.h_ent, &d.h_out, &d.wstart, &d.g_rec};
+    for (int k = 0; k < 6; ++k) {
         int* p = nullptr;
         const size_t bytes = sizeof(int) * (src[k]->size() + 1);
         if ((e = cudaMalloc(&p, bytes)) != cudaSuccess) return e;
@@ -368,15 +382,16 @@ cudaError_t init_prep_tables(const double* host_coefs, const int* host_tuv, cons
     for (int a = 0; a <= LMAX; ++a)
         for (int b = 0; b <= LMAX; ++b) d.pair[a][b] = F.pair[a][b];
     if ((e = cudaMemcpyToSymbol(c_fold, &d, sizeof(d))) != cudaSuccess) return e;
-    int qmax = 0, wmax = 0;
+    int qmax = 0, wmax = 0, gmax = 0;
     for (int a = 0; a <= LMAX; ++a)
         for (int b = 0; b <= LMAX; ++b) {
             qmax = std::max(qmax, F.pair[a][b].maxq + 1);
             wmax = std::max(wmax, F.pair[a][b].maxw);
+            gmax = std::max(gmax, F.pair[a][b].maxg + 1);
         }
     for (const void* k : {(const void*)pair_h_solid_kernel<false>, (const void*)pair_h_solid_kernel<true>})
         if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)fold_smem_bytes(LMAX, qmax, wmax))) != cudaSuccess)
+                                      (int)fold_smem_bytes(LMAX, qmax, wmax, gmax))) != cudaSuccess)
             return e;
     return cudaMemcpyToSymbol(g_tuv_prep, host_tuv, sizeof(int) * NHERM_TOT);
 }
@@ -390,17 +405,18 @@ cudaError_t launch_norm(const DShell* sh, int nshell, const double* exps, const 
 
 cudaError_t launch_pair_h(const DPair* pairs, const WorkItem* items, int nitems, const DShell* sh,
                           const double* exps, const double* ncoef, double* ws, double* ws_info, bool solid, bool scales,
-                          int fold_lcap, int fold_qcap, int fold_wcap, unsigned* status, cudaStream_t st) {
+                          int fold_lcap, int fold_qcap, int fold_wcap, int fold_gcap, unsigned* status,
+                          cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
     if (solid) {
         if (fold_lcap < 0 || fold_lcap > LMAX) return cudaErrorInvalidValue;
-        const size_t smem = fold_smem_bytes(fold_lcap, fold_qcap, fold_wcap);
+        const size_t smem = fold_smem_bytes(fold_lcap, fold_qcap, fold_wcap, fold_gcap);
         if (scales)
             pair_h_solid_kernel<true><<<nitems, PAIR_SOLID_THREADS, smem, st>>>(
-                pairs, items, sh, exps, ncoef, ws, ws_info, fold_lcap, fold_qcap, fold_wcap, status);
+                pairs, items, sh, exps, ncoef, ws, ws_info, fold_lcap, fold_qcap, fold_wcap, fold_gcap, status);
         else
             pair_h_solid_kernel<false><<<nitems, PAIR_SOLID_THREADS, smem, st>>>(
-                pairs, items, sh, exps, ncoef, ws, ws_info, fold_lcap, fold_qcap, fold_wcap, status);
+                pairs, items, sh, exps, ncoef, ws, ws_info, fold_lcap, fold_qcap, fold_wcap, fold_gcap, status);
     } else
         pair_h_kernel<<<nitems, PAIR_THREADS, 0, st>>>(pairs, items, sh, exps, ncoef, ws, ws_info, status);
     return cudaGetLastError();

@@ -190,6 +190,7 @@ constexpr int W_PLACEHOLDER = FOLD_MASK;  // never a real W entry
 
 bool make_fold_lists(const double* coefs, FoldHost& F) {
     F.wstart.clear();
+    F.g_rec.clear();
     F.q_ent.clear();
     F.w_ent.clear();
     F.h_ent.clear();
@@ -221,14 +222,17 @@ bool make_fold_lists(const double* coefs, FoldHost& F) {
                     yz.emplace_back(ay[k], az[k]);
             FoldPairTab& tab = F.pair[la][lb];
             tab.seg0 = (int)F.segs.size();
-            tab.maxq = tab.maxw = 0;
+            tab.maxq = tab.maxw = tab.maxg = 0;
             const size_t w_first = F.w_ent.size();
             for (int mb = 0; mb < nsb; ++mb) {
                 FoldSeg sg{};
                 sg.h_row0 = (int)F.h_out.size();
-                // Q rows, keyed (ay, az, bx, u, v)
+                // Q rows, keyed (ay, az, bx, u, v); their G entries C_b[m_b][b] E^z_{az bz v},
+                // numbered in order of first use
                 std::vector<std::tuple<int, int, int, int, int>> qkey;
                 std::vector<std::vector<int>> qrows;
+                std::map<int, int> gidx_of;  // (coefficient index | E^z index << 10) -> G index
+                std::vector<int> grec;
                 for (const auto& [y, z] : yz)
                     for (int bx = 0; bx <= lb; ++bx)
                         for (int u = 0; u <= y + lb - bx; ++u)
@@ -237,8 +241,13 @@ bool make_fold_lists(const double* coefs, FoldHost& F) {
                                 for (int by = 0; by <= lb - bx; ++by) {
                                     const int bz = lb - bx - by, b = bidx[bx * (lb + 1) + by];
                                     if (std::fabs(Cb[mb * ncb + b]) <= 1e-14 || u > y + by || v > z + bz) continue;
-                                    row.push_back((mb * ncb + b) | (((y * sb1 + by) * nt + u) << 10) |
-                                                  (((z * sb1 + bz) * nt + v) << 20));
+                                    const int rec = (mb * ncb + b) | (((z * sb1 + bz) * nt + v) << 10);
+                                    auto gi = gidx_of.find(rec);
+                                    if (gi == gidx_of.end()) {
+                                        gi = gidx_of.emplace(rec, (int)grec.size()).first;
+                                        grec.push_back(rec);
+                                    }
+                                    row.push_back(gi->second | (((y * sb1 + by) * nt + u) << 10));
                                 }
                                 if (row.empty()) continue;
                                 qkey.emplace_back(y, z, bx, u, v);
@@ -246,9 +255,13 @@ bool make_fold_lists(const double* coefs, FoldHost& F) {
                             }
                 sg.q_nrow = (int)qkey.size();
                 if (sg.q_nrow > FOLD_QMAX) return false;
-                // padding entries take the zero stored after C_b (coefficient index nsb ncb)
+                sg.g_n = (int)grec.size();
+                if (sg.g_n > FOLD_GMAX) return false;
+                sg.g_off = (int)F.g_rec.size();
+                F.g_rec.insert(F.g_rec.end(), grec.begin(), grec.end());
+                // padding entries take the zero stored after the G entries (G index g_n)
                 sg.q_ws = (int)F.wstart.size();
-                const std::vector<int> qpos = emit_groups(qrows, nsb * ncb, F.wstart, F.q_ent);
+                const std::vector<int> qpos = emit_groups(qrows, sg.g_n, F.wstart, F.q_ent);
                 // W rows, keyed (a, p)
                 std::vector<std::vector<int>> wrows;
                 std::vector<int> wrow((size_t)nca * np, -1);
@@ -292,6 +305,7 @@ bool make_fold_lists(const double* coefs, FoldHost& F) {
                 for (size_t i = 0; i < hrows.size(); ++i) out[hpos[i]] = hkey[i];
                 F.h_out.insert(F.h_out.end(), out.begin(), out.end());
                 tab.maxq = std::max(tab.maxq, sg.q_nrow);
+                tab.maxg = std::max(tab.maxg, sg.g_n);
                 tab.maxw = std::max(tab.maxw, sg.w_nrow);
                 F.segs.push_back(sg);
             }
