@@ -84,8 +84,8 @@ def nfun(l, solid):
 NCU_TRAFFIC = {
     "gemm1": (311.383296e6 / 256, "paper_2307_03452_gb300/csrc/lx_gemm.cu",
               "2e31e62d4b0eb5d2d87ec27d9d5e2bf675e0e8eec6d9707d1c2f2df1cb75f841"),
-    "split_gemm1": ((957.062400e6 + 145.941248e6) / 256, "paper_2307_03452_gb300/csrc/lx_split.cu",
-                    "c1f5968d582d9dedbdfcc9ebdee672e9d4afe5bf7a37895514853c766ad0d1df"),
+    "split_gemm1": ((957.045504e6 + 145.702656e6) / 256, "paper_2307_03452_gb300/csrc/lx_split.cu",
+                    "559aa480485e877e1e889fde8c826245b58238bb6559e839d3fb8fb2230d99a4"),
 }
 
 

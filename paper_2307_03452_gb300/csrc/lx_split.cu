@@ -680,7 +680,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                     } else {
                         sv = E - es;  // a zero segment (es = SPLIT_EXP_NONE) contributes nothing
                     }
+                    // the running sum's shift is the same for every column: applied here, once
+                    if (sa > 0) {
+#pragma unroll
+                        for (int j = 0; j < DCOLS; ++j) acc[j] = shr_round(acc[j], sa);
+                    }
                 }
+                // this segment's shift and its rounding half (sv >= 62: nothing left of it)
+                const bool seg_live = sv < 62;
+                const long long seg_half = sv > 0 && seg_live ? (1ll << (sv - 1)) : 0ll;
                 const bool got = mbar_wait(&seg_full[buf], (sgc >> 1) & 1, status);
                 ok = __all_sync(0xffffffffu, got) && !*(volatile int*)&abort_sh;
                 if (!ok) break;
@@ -714,10 +722,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                             }
                             if (xs) v = (v + (1ll << (xs - 1))) >> xs;
                             const int j = HC * h + jj;
-                            if (segs)
-                                acc[j] = shr_round(acc[j], sa) + shr_round(v, sv);
-                            else
+                            if (segs) {
+                                if (seg_live) acc[j] += (v + seg_half) >> sv;
+                            } else {
                                 acc[j] += v;
+                            }
                         }
                     }
                 }
