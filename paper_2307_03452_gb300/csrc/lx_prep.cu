@@ -257,10 +257,11 @@ __device__ __forceinline__ void fold_stage(int ws, int nrow, const int* __restri
 // One CTA per primitive pair, solid-harmonic rows:
 //   H[m_a m_b][p] = sign(p) * sum_a (pref C_a[m_a][a]) sum_b C_b[m_b][b] E_ab^p
 // by the factorised fold (one Cartesian index at a time, structural zeros skipped; the row
-// groups are built on the host).  Per m_b: the Q stage, a barrier, the W stage, a barrier,
-// then the H stage of m_b together with the Q stage of m_b + 1 (which touch disjoint
-// arrays), a barrier.  On the split path the H stage also keeps each column's largest
-// exponent, and the column scales are written at the end.
+// streams and the G recipes are built on the host).  G of m_b = 0 is made first; then per
+// m_b: the Q stage (one FMA per entry from G), a barrier, the W stage and G of m_b + 1 (G of
+// m_b is no longer read), a barrier, then the H stage of m_b together with the Q stage of
+// m_b + 1 (which touch disjoint arrays), a barrier.  On the split path the H stage also keeps
+// each column's largest exponent, and the column scales are written at the end.
 template <bool SCALES>  // the split path: pairs carry column scales (cs_off >= 0)
 __global__ void __launch_bounds__(PAIR_SOLID_THREADS, 2) pair_h_solid_kernel(
     const DPair* __restrict__ pairs, const WorkItem* __restrict__ items, const DShell* __restrict__ sh,
